@@ -1,0 +1,104 @@
+"""Seeded synthetic workloads (inputs only).
+
+This module draws the random inputs and states the recipes of the benchmark workloads:
+lattice size, physical parameters, the initial orientation noise and the positions of the
+ring nodes.  It holds none of the method's arithmetic, so that the CUDA path and the FP64
+oracle can both consume exactly the same arrays.  Every random number comes from numpy's
+PCG64 generator seeded per workload.
+
+Recipe of the default physics (lattice units, dx = dt = 1):
+  * D2Q9 BGK, tau = 0.8, rho0 = 1, periodic in x and y, fluid at rest.
+  * K^x = G0 (2, 1, 1, 1) for (K1111, K1122, K2222, K1212), G0 = 1e-3: the ratios of the
+    paper's Table IV.
+  * relaxation time lambda in steps (turned into eta_p by each consumer).
+  * Beris-Edwards parameters of the paper's Table III: xi = 1.1, alpha = -0.9, beta = 1,
+    kappa = 0.001, Gamma = 1.
+  * P = P_eq (cos theta_d, sin theta_d) + noise, noise uniform in [-0.05, 0.05] per component.
+  * sigma = 0.
+  * rings: N nodes on a circle of radius r, node a at angle 2 pi a / N; l_eq = the initial
+    chord; constant pull force split equally over the nodes.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+DEFAULT_PHYSICS = dict(tau=0.8, rho0=1.0, K=(2e-3, 1e-3, 1e-3, 1e-3), lambda_steps=50.0,
+                       Dp=0.05, alpha=-0.9, beta=1.0, xi=1.1, Gamma=1.0, kappa=0.001,
+                       P_cap=0.99, ericksen=1, director_angle=0.0)
+
+
+def ring(n_nodes: int, radius: float, centre, k_spring=0.1, eps_angle=0.01, pull_force=1e-3,
+         pull_angle=0.0, phase=0.0) -> dict:
+    """A closed ring of n_nodes points on a circle (node a at angle phase + 2 pi a / N)."""
+    a = phase + 2.0 * np.pi * np.arange(n_nodes) / n_nodes
+    X = np.stack([centre[0] + radius * np.cos(a), centre[1] + radius * np.sin(a)], axis=1)
+    l_eq = float(np.hypot(*(X[1] - X[0])))
+    return dict(X=X, k_spring=k_spring, eps_angle=eps_angle, l_eq=l_eq, pull_force=pull_force,
+                pull_angle=pull_angle, radius=radius, centre=tuple(centre))
+
+
+def make(nx: int, ny: int, rings=(), seed: int = 1, noise_amp: float = 0.05, steps: int = 100,
+         every: int = 10, **physics) -> dict:
+    """A workload: physics + seeded orientation noise [2, ny, nx] + rings."""
+    w = dict(DEFAULT_PHYSICS)
+    w.update(physics)
+    w.update(nx=nx, ny=ny, seed=seed, steps=steps, every=every, rings=list(rings))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if noise_amp > 0:
+        w["noise"] = rng.uniform(-noise_amp, noise_amp, size=(2, ny, nx))
+    else:
+        w["noise"] = None
+    w["noise_amp"] = noise_amp
+    return w
+
+
+def cfg1(seed: int = 1) -> dict:
+    """Plain method, 64x64 periodic; one ring of 32 nodes, radius 6, pulled along x with
+    1e-3; relaxation 50 steps, D_p = 0.05; 2000 steps, restoring force every 10 steps."""
+    return make(64, 64, rings=[ring(32, 6.0, (32.0, 32.0), pull_force=1e-3, pull_angle=0.0)],
+                seed=seed, steps=2000, every=10, lambda_steps=50.0, Dp=0.05)
+
+
+def cfg2(seed: int = 2) -> dict:
+    """Plain method at scale, 1024x1024 periodic; one ring of 256 nodes, radius 24, pulled at
+    30 degrees to the director (x) with 5e-4; relaxation 200 steps, D_p = 0.1; 20000 steps."""
+    return make(1024, 1024,
+                rings=[ring(256, 24.0, (512.0, 512.0), pull_force=5e-4, pull_angle=math.radians(30))],
+                seed=seed, steps=20000, every=10, lambda_steps=200.0, Dp=0.1)
+
+
+def cfg3(seed: int = 3, side: int = 4096, n_rings: int = 16) -> dict:
+    """Precision-form workload: side x side periodic, n_rings rings of 128 nodes, radius 12,
+    at seeded positions (centre separation >= 2r + 8, on the torus) with seeded pull angles in
+    [0, 90] degrees, force 5e-4 each; relaxation 200 steps, D_p = 0.1; 10000 steps."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    r, sep = 12.0, 2 * 12.0 + 8.0
+    centres = []
+    while len(centres) < n_rings:
+        c = rng.uniform(0, side, size=2)
+        ok = True
+        for d in centres:
+            dx = abs(c[0] - d[0]); dx = min(dx, side - dx)
+            dy = abs(c[1] - d[1]); dy = min(dy, side - dy)
+            if math.hypot(dx, dy) < sep:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    angles = rng.uniform(0.0, math.pi / 2, size=n_rings)
+    rings = [ring(128, r, tuple(c), pull_force=5e-4, pull_angle=float(a))
+             for c, a in zip(centres, angles)]
+    return make(side, side, rings=rings, seed=seed, steps=10000, every=10, lambda_steps=200.0,
+                Dp=0.1)
+
+
+def small(nx: int, ny: int, seed: int = 7, n_nodes: int = 24, radius: float = 5.0, centre=None,
+          pull_angle: float = 0.3, steps: int = 50, **physics) -> dict:
+    """Small parity case with an arbitrary (possibly ragged) lattice and one ring."""
+    if centre is None:
+        centre = (nx / 2 + 0.37, ny / 2 - 0.21)
+    rings = [ring(n_nodes, radius, centre, pull_force=1e-3, pull_angle=pull_angle, phase=0.1)] \
+        if n_nodes > 0 else []
+    return make(nx, ny, rings=rings, seed=seed, steps=steps, every=10, **physics)

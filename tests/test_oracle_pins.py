@@ -1,0 +1,576 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test names the part of the oracle it checks and the independent fact it uses: the
+paper's definitions (App. B integral, Eq. rotate), printed limits and table values, closed
+forms of special cases (Taylor-Green, Kolmogorov, Poiseuille, exponential relaxation,
+diffusion of a Fourier mode, logistic P relaxation), library routines (scipy Bessel
+functions) and invariants (conservation, partition of unity, adjointness, symmetry).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import iv
+
+import oracle as O
+from paper_2209_14889_gb300 import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+KX = (2e-3, 1e-3, 1e-3, 1e-3)
+
+
+def _p(nx=8, ny=8, **kw):
+    base = dict(K1111=KX[0], K1122=KX[1], K2222=KX[2], K1212=KX[3], eta_p=0.1)
+    base.update(kw)
+    return O.Params(nx=nx, ny=ny, **base)
+
+
+# ----------------------------------------------------------------------------------------
+# Bessel functions and the P <-> k map (Eq. Pk)
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [0, 1, 2, 4])
+def test_bessel_series_matches_library(n):
+    for k in [1e-8, 1e-3, 0.1, 0.7, 1.0, 3.3, 10.0, 25.0, 50.254, 60.0]:
+        ref = iv(n, k)
+        assert abs(O.bessel_i(n, k) - ref) <= 1e-13 * abs(ref) + 1e-300, (n, k)
+
+
+def test_bessel_matches_integral_representation():
+    # I_n(k) = (1/pi) int_0^pi exp(k cos t) cos(n t) dt (trapezoid rule is spectral here)
+    t = np.linspace(0, np.pi, 4001)
+    for n in [0, 1, 2, 4]:
+        for k in [0.5, 2.0, 9.0]:
+            f = np.exp(k * np.cos(t)) * np.cos(n * t)
+            val = (f.sum() - 0.5 * (f[0] + f[-1])) * (t[1] - t[0]) / np.pi
+            assert abs(O.bessel_i(n, k) - val) < 1e-12 * val
+
+
+def test_P_of_k_is_first_moment_of_von_mises():
+    # Eq. Pk: P = int g(theta; k) cos(theta) dtheta with g = e^{k cos} / (2 pi I0)
+    th = np.linspace(0, 2 * np.pi, 8001)[:-1]
+    for k in [0.2, 1.5, 7.0, 30.0]:
+        g = np.exp(k * np.cos(th)) / (2 * np.pi * iv(0, k))
+        P = (g * np.cos(th)).sum() * (th[1] - th[0])
+        assert abs(O.k_of_P(P) - k) < 1e-9 * k
+
+
+def test_k_of_P_round_trip_and_cap_value():
+    for k in [1e-6, 1e-3, 0.3, 2.0, 11.0, 45.0]:
+        P = iv(1, k) / iv(0, k)
+        assert abs(O.k_of_P(P) - k) <= 1e-10 * k
+    assert O.k_of_P(0.0) == 0.0
+    # the cap P = 0.99 of Sec. II C 3 corresponds to k = 50.2538...
+    k99 = O.k_of_P(0.99)
+    assert abs(iv(1, k99) / iv(0, k99) - 0.99) < 1e-14
+
+
+def test_printed_bracket_equals_I4():
+    # App. B writes (k(k^2+24) I0 - 8(k^2+6) I1) / k^3; it is identically I4(k).
+    for k in [2.0, 5.0, 12.0, 30.0, 50.0]:
+        br = (k * (k * k + 24) * O.bessel_i(0, k) - 8 * (k * k + 6) * O.bessel_i(1, k)) / k ** 3
+        assert abs(br - O.bessel_i(4, k)) < 1e-9 * O.bessel_i(4, k)
+
+
+# ----------------------------------------------------------------------------------------
+# Stiffness tensor (App. B, Eq. Cdef1, Eq. qmatrix, Eq. Kmatrix, Eq. rotate)
+# ----------------------------------------------------------------------------------------
+
+def _Qt(th):
+    c, s = np.cos(th), np.sin(th)
+    return np.array([[c * c, s * s, -2 * s * c], [s * s, c * c, 2 * s * c],
+                     [s * c, -s * c, c * c - s * s]])
+
+
+def _quad_mandel(K, k, thP, M=4096):
+    """App. B definition: int g(theta - theta_P; k) Q~(theta) K~x Q~(theta)^-1 dtheta with the
+    printed Q~ (Eq. qmatrix) and K~x (Eq. Kmatrix)."""
+    K11, K12, K22, K66 = K
+    Kx = np.array([[K11, K12, 0], [K12, K22, 0], [0, 0, 2 * K66]])
+    th = 2 * np.pi * np.arange(M) / M
+    C = np.zeros((3, 3))
+    for t in th:
+        g = np.exp(k * np.cos(t - thP)) / (2 * np.pi * iv(0, k))
+        Q = _Qt(t)
+        C += g * Q @ Kx @ np.linalg.inv(Q)
+    return C * 2 * np.pi / M
+
+
+def _quad_tensor(K, k, thP, M=2048):
+    """Eq. rotate: K_ijkl(n) = Q_iI Q_jJ Q_kK Q_lL K^x_IJKL with the transversely isotropic
+    K^x, averaged over g; returned in the plain basis s = (s11, s22, s12) acting on
+    (e11, e22, e12): [[C1111, C1122, 2 C1112], [C2211, C2222, 2 C2212], [C1211, C1222, 2 C1212]]."""
+    K11, K12, K22, K66 = K
+    Kx = np.zeros((2, 2, 2, 2))
+    Kx[0, 0, 0, 0] = K11; Kx[1, 1, 1, 1] = K22
+    Kx[0, 0, 1, 1] = Kx[1, 1, 0, 0] = K12
+    for (i, j, k_, l) in [(0, 1, 0, 1), (0, 1, 1, 0), (1, 0, 0, 1), (1, 0, 1, 0)]:
+        Kx[i, j, k_, l] = K66
+    C4 = np.zeros((2, 2, 2, 2))
+    for t in 2 * np.pi * np.arange(M) / M:
+        g = np.exp(k * np.cos(t - thP)) / (2 * np.pi * iv(0, k))
+        R = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+        C4 += g * np.einsum("iI,jJ,kK,lL,IJKL->ijkl", R, R, R, R, Kx)
+    C4 *= 2 * np.pi / M
+    return np.array([[C4[0, 0, 0, 0], C4[0, 0, 1, 1], 2 * C4[0, 0, 0, 1]],
+                     [C4[1, 1, 0, 0], C4[1, 1, 1, 1], 2 * C4[1, 1, 0, 1]],
+                     [C4[0, 1, 0, 0], C4[0, 1, 1, 1], 2 * C4[0, 1, 0, 1]]])
+
+
+@pytest.mark.parametrize("K", [KX, (0.01, 0.005, 0.005, 0.005), (1.0, 0.3, 0.7, 0.2),
+                               (0.4, -0.1, 1.3, 0.9)])
+def test_stiffness_closed_form_matches_definition(K):
+    rng = np.random.default_rng(11)
+    p = _p(K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3])
+    for _ in range(4):
+        k = rng.uniform(0.05, 40.0)
+        thP = rng.uniform(-np.pi, np.pi)
+        P = iv(1, k) / iv(0, k)
+        C = O.stiffness(p, P * np.cos(thP), P * np.sin(thP))
+        Cq = _quad_mandel(K, k, thP, M=1024)
+        scale = np.abs(Cq).max()
+        assert np.abs(C - Cq).max() < 1e-11 * scale, (K, k, thP)
+
+
+def test_stiffness_basis_matches_fourth_order_rotation():
+    K = (1.0, 0.3, 0.7, 0.2)
+    p = _p(K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3])
+    for k, thP in [(0.8, 0.3), (6.0, -2.1), (25.0, 1.2)]:
+        P = iv(1, k) / iv(0, k)
+        C = O.stiffness(p, P * np.cos(thP), P * np.sin(thP))
+        Ct = _quad_tensor(K, k, thP, M=512)
+        assert np.abs(C - Ct).max() < 1e-11 * np.abs(Ct).max()
+
+
+def test_isotropic_limit_is_the_printed_one():
+    gi = GOLD["isotropic_limit"]
+    for K in [KX, (0.01, 0.005, 0.005, 0.005), (0.4, -0.1, 1.3, 0.9)]:
+        p = _p(K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3])
+        C = O.stiffness(p, 0.0, 0.0)
+        C11 = np.dot(gi["coeff_C11"], K) / 8
+        C12 = np.dot(gi["coeff_C12"], K) / 8
+        ref = np.array([[C11, C12, 0], [C12, C11, 0], [0, 0, C11 - C12]])
+        assert np.abs(C - ref).max() < 1e-15
+        # and k -> 0 continuously
+        C2 = O.stiffness(p, 1e-7, 2e-7)
+        assert np.abs(C2 - ref).max() < 1e-12
+
+
+def test_stiffness_period_pi_and_mirror():
+    p = _p(K1111=1.0, K1122=0.3, K2222=0.7, K1212=0.2)
+    M = np.diag([1.0, 1.0, -1.0])
+    for P, th in [(0.5, 0.4), (0.93, 2.2), (0.2, -1.0)]:
+        C = O.stiffness(p, P * np.cos(th), P * np.sin(th))
+        Cpi = O.stiffness(p, P * np.cos(th + np.pi), P * np.sin(th + np.pi))
+        assert np.abs(C - Cpi).max() < 1e-13
+        Cm = O.stiffness(p, P * np.cos(-th), P * np.sin(-th))
+        assert np.abs(Cm - M @ C @ M).max() < 1e-13
+
+
+def test_stiffness_caps_P():
+    p = _p(K1111=1.0, K1122=0.3, K2222=0.7, K1212=0.2)
+    th = 0.77
+    a = O.stiffness(p, 0.99 * np.cos(th), 0.99 * np.sin(th))
+    b = O.stiffness(p, 1.3 * np.cos(th), 1.3 * np.sin(th))
+    assert np.abs(a - b).max() < 1e-15
+
+
+def test_scalar_limit():
+    # Sec. II C 3: with C12 = 0 at k = 0 the tensor is C11 * I and Eq. StiffCons is Eq. MaxDiff.
+    K = (1.0, 0.0, 1.0, 0.5)           # K1111 + 6 K1122 - 4 K1212 + K2222 = 0
+    p = _p(K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3], eta_p=2.0)
+    C = O.stiffness(p, 0.0, 0.0)
+    assert np.abs(C - C[0, 0] * np.eye(3)).max() < 1e-15
+    n = 6
+    p.nx = p.ny = n
+    rng = np.random.default_rng(3)
+    sig = np.broadcast_to(rng.normal(size=(3, 1, 1)), (3, n, n)).copy()
+    psi = np.broadcast_to(rng.normal(size=(3, 1, 1)), (3, n, n)).copy()
+    ds, _ = O.rhs(p, sig, np.zeros((2, n, n)), np.zeros((2, n, n)), psi, np.zeros((n, n)))
+    ref = C[0, 0] * psi - C[0, 0] / p.eta_p * sig
+    assert np.abs(ds - ref).max() < 1e-14
+
+
+# ----------------------------------------------------------------------------------------
+# Immersed boundary (App. A)
+# ----------------------------------------------------------------------------------------
+
+def test_phi_partition_of_unity_and_support():
+    for r in np.linspace(0, 1, 17):
+        s = sum(O.phi(r + j) for j in range(-3, 4))
+        assert abs(s - 1.0) < 1e-15
+    assert O.phi(2.0) == 0.0 and O.phi(-2.5) == 0.0
+    assert abs(O.phi(0.0) - 0.5) < 1e-16
+
+
+def test_spread_total_equals_lagrangian_force_and_adjoint():
+    p = _p(nx=20, ny=13)
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-3, 25, size=(9, 2))          # includes images across the periodic seams
+    X[0] = (0.0, 12.999)
+    f = rng.normal(size=(9, 2))
+    fib = O.spread(p, X, f)
+    assert np.allclose(fib.sum(axis=(1, 2)), f.sum(0), atol=1e-14, rtol=0)
+    u = rng.normal(size=(2, 13, 20))
+    V = O.interp(p, u, X)
+    assert abs((u * fib).sum() - (V * f).sum()) < 1e-13
+    Vc = O.interp(p, np.stack([np.full((13, 20), 0.3), np.full((13, 20), -1.7)]), X)
+    assert np.allclose(Vc, [[0.3, -1.7]] * 9, atol=1e-15)
+
+
+def test_node_forces_are_minus_gradient_of_energy():
+    rng = np.random.default_rng(9)
+    w = W.ring(12, 3.0, (5.0, 6.0))
+    X = w["X"] + rng.normal(scale=0.2, size=w["X"].shape)
+    ring = O.Ring(12, k_spring=0.1, eps_angle=0.01, l_eq=w["l_eq"], pull_x=1e-3, pull_y=-2e-3)
+    f = O.node_forces(ring, X)
+    h = 1e-5
+    for a in range(12):
+        for c in range(2):
+            Xp = X.copy(); Xp[a, c] += h
+            Xm = X.copy(); Xm[a, c] -= h
+            g = (O.ring_energy(ring, Xp) - O.ring_energy(ring, Xm)) / (2 * h)
+            assert abs(f[a, c] + g) < 1e-7 * max(1e-3, abs(g)), (a, c)
+    # internal forces sum to the pull only
+    assert np.allclose(f.sum(0), [1e-3, -2e-3], atol=1e-15)
+
+
+# ----------------------------------------------------------------------------------------
+# Lattice Boltzmann hydrodynamics (Sec. II A)
+# ----------------------------------------------------------------------------------------
+
+def _fluid_only(nx, ny, tau, **kw):
+    return O.Params(nx=nx, ny=ny, tau=tau, ericksen=0, **kw)
+
+
+def _tg_error(N, tau, U0=1e-4):
+    p = _fluid_only(N, N, tau)
+    k = 2 * np.pi / N
+    y, x = np.mgrid[0:N, 0:N].astype(float)
+    u = np.stack([-U0 * np.cos(k * x) * np.sin(k * y), U0 * np.sin(k * x) * np.cos(k * y)])
+    prs = -0.25 * U0 ** 2 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    h = O.equilibrium(1.0 + 3 * prs, u)
+    s = O.Sim(p, [], h, np.zeros((3, N, N)), np.zeros((2, N, N)), np.zeros((0, 2)))
+    nu = (tau - 0.5) / 3
+    n = int(round(0.5 / (nu * k * k)))           # ~ e^-1 decay
+    s.step(n)
+    f = s.fields()
+    decay = np.exp(-2 * nu * k * k * n)
+    return np.abs(f["ux"] - u[0] * decay).max() / (U0 * decay)
+
+
+def test_taylor_green_decay_second_order():
+    e16, e32 = _tg_error(16, 0.8), _tg_error(32, 0.8)
+    assert e32 < 0.02
+    assert 3.0 < e16 / e32 < 5.5                   # second order in dx
+
+
+def test_viscosity_of_table_I_tau():
+    # Table I: tau = 1.25 with eta_s / rho_s, dx, dt gives nu_lu = 0.25 = c_s^2 (tau - 1/2);
+    # the decay rate of a shear wave in the oracle at that tau measures the same nu.
+    t1 = GOLD["table_I"]
+    nu_lu = t1["eta_s_Pa_s"] / t1["rho_s_kg_m3"] * t1["dt_s"] / t1["dx_m"] ** 2
+    assert abs(nu_lu - 0.25) < 1e-12
+    N = 32
+    p = _fluid_only(4, N, t1["tau"])
+    k = 2 * np.pi / N
+    y = np.arange(N, dtype=float)[:, None] * np.ones((1, 4))
+    u = np.stack([1e-5 * np.sin(k * y), np.zeros_like(y)])
+    s = O.Sim(p, [], O.equilibrium(np.ones((N, 4)), u), np.zeros((3, N, 4)), np.zeros((2, N, 4)),
+              np.zeros((0, 2)))
+    s.step(20)
+    a0 = (s.fields()["ux"][:, 0] * np.sin(k * y[:, 0])).sum()
+    s.step(200)
+    a1 = (s.fields()["ux"][:, 0] * np.sin(k * y[:, 0])).sum()
+    nu_meas = -np.log(a1 / a0) / (200 * k * k)
+    assert abs(nu_meas - nu_lu) < 0.01 * nu_lu
+
+
+def _kolmogorov_error(N, tau=0.8, F0=1e-7):
+    p = _fluid_only(4, N, tau)
+    k = 2 * np.pi / N
+    y = np.arange(N, dtype=float)[:, None] * np.ones((1, 4))
+    fext = np.stack([F0 * np.sin(k * y), np.zeros_like(y)])
+    s = O.Sim(p, [], O.equilibrium(np.ones((N, 4)), np.zeros((2, N, 4))), np.zeros((3, N, 4)),
+              np.zeros((2, N, 4)), np.zeros((0, 2)), fext=fext)
+    nu = (tau - 0.5) / 3
+    s.step(int(12 / (nu * k * k)))
+    ux = s.fields()["ux"][:, 0]
+    ref = F0 / (nu * k * k) * np.sin(k * y[:, 0])
+    return np.abs(ux - ref).max() / np.abs(ref).max()
+
+
+def test_kolmogorov_flow_with_guo_forcing_second_order():
+    e8, e16 = _kolmogorov_error(8), _kolmogorov_error(16)
+    assert e16 < 0.02
+    assert 3.5 < e8 / e16 < 4.5
+
+
+def test_poiseuille_bounce_back_exact_at_magic_tau():
+    # Half-way bounce-back + Guo forcing reproduce the parabola exactly at
+    # tau = 1/2 + sqrt(3/16) (a known BGK property), and to O(dx^2) otherwise.
+    for tau, tol in [(0.5 + math.sqrt(3 / 16), 1e-9), (0.8, 5e-3)]:
+        ny, nx, g = 16, 2, 1e-6
+        p = _fluid_only(nx, ny, tau, walls_y=1)
+        fext = np.zeros((2, ny, nx)); fext[0] = g
+        s = O.Sim(p, [], O.equilibrium(np.ones((ny, nx)), np.zeros((2, ny, nx))),
+                  np.zeros((3, ny, nx)), np.zeros((2, ny, nx)), np.zeros((0, 2)), fext=fext)
+        nu = (tau - 0.5) / 3
+        s.step(int(25 * ny * ny / nu))
+        y = np.arange(ny)
+        ref = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+        err = np.abs(s.fields()["ux"][:, 0] - ref).max() / ref.max()
+        assert err < tol, (tau, err)
+
+
+# ----------------------------------------------------------------------------------------
+# Polymer stress and orientation dynamics (Eq. StiffCons, Eq. BE)
+# ----------------------------------------------------------------------------------------
+
+def test_uniform_stress_decay():
+    # u = 0, uniform P = P_eq, uniform sigma: the fluid stays at rest and sigma_n = M^n sigma_0
+    # with M = I - Z + Z^2/2 (Heun), Z = C~(P)/eta_p; and sigma ~ exp(-Z t) to O(Z^3) per step.
+    n = 8
+    p = _p(nx=n, ny=n, eta_p=0.09375, alpha=-0.9, beta=1.0, xi=1.1, Gamma=1.0, kappa=1e-3)
+    Peq = math.sqrt(0.9)
+    th = 0.6
+    P = np.zeros((2, n, n)); P[0] = Peq * math.cos(th); P[1] = Peq * math.sin(th)
+    s0 = np.array([1e-4, -3e-5, 5e-5])
+    sig = np.broadcast_to(s0[:, None, None], (3, n, n)).copy()
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))), sig, P,
+                np.zeros((0, 2)))
+    steps = 40
+    sim.step(steps)
+    Z = O.stiffness(p, P[0, 0, 0], P[1, 0, 0]) / p.eta_p
+    M = np.eye(3) - Z + Z @ Z / 2
+    ref = np.linalg.matrix_power(M, steps) @ s0
+    assert np.abs(sim.sigma[:, 0, 0] - ref).max() < 1e-13 * np.abs(s0).max()
+    assert np.abs(sim.sigma - sim.sigma[:, :1, :1]).max() < 1e-18
+    from scipy.linalg import expm
+    cont = expm(-Z * steps) @ s0
+    bound = steps * np.linalg.norm(Z, 2) ** 3 / 6 * np.abs(s0).max() * 2
+    assert np.abs(sim.sigma[:, 0, 0] - cont).max() < bound
+
+
+def test_scalar_relaxation_time():
+    # scalar model (Eq. MaxLine): sigma decays as exp(-t/lambda), lambda = eta_p / C.
+    n, lam = 6, 50.0
+    K = (1.0e-3, 0.0, 1.0e-3, 0.5e-3)
+    C11 = (3 * K[0] + 2 * K[1] + 4 * K[3] + 3 * K[2]) / 8
+    p = O.Params(nx=n, ny=n, tau=0.8, K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3],
+                 eta_p=lam * C11, ericksen=0)
+    sig = np.zeros((3, n, n)); sig[0] = 1e-4
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))), sig,
+                np.zeros((2, n, n)), np.zeros((0, 2)))
+    sim.step(100)
+    assert abs(sim.sigma[0, 0, 0] / 1e-4 - math.exp(-100 / lam)) < 100 * (1 / lam) ** 3
+
+
+def _airy_mode(n, kx, ky):
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    phi = np.cos(kx * x + 0.3) * np.cos(ky * y - 0.2)
+    Dx = lambda f: 0.5 * (np.roll(f, -1, 1) - np.roll(f, 1, 1))
+    Dy = lambda f: 0.5 * (np.roll(f, -1, 0) - np.roll(f, 1, 0))
+    return np.stack([Dy(Dy(phi)), Dx(Dx(phi)), -Dx(Dy(phi))])
+
+
+def test_stress_mode_diffusion_exact():
+    # C = 0, no flow: a divergence-free (Airy) stress mode decays by (1 - z + z^2/2)^n with
+    # z = D_p (4 sin^2(kx/2) + 4 sin^2(ky/2)), the 5-point Laplacian eigenvalue under Heun.
+    n, D = 16, 0.2
+    kx, ky = 2 * np.pi * 2 / n, 2 * np.pi * 3 / n
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, Dp=D, ericksen=0)
+    sig0 = 1e-3 * _airy_mode(n, kx, ky)
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))), sig0.copy(),
+                np.zeros((2, n, n)), np.zeros((0, 2)))
+    steps = 25
+    sim.step(steps)
+    z = D * (4 * math.sin(kx / 2) ** 2 + 4 * math.sin(ky / 2) ** 2)
+    ref = (1 - z + z * z / 2) ** steps * sig0
+    assert np.abs(sim.sigma - ref).max() < 1e-12 * np.abs(sig0).max()
+
+
+def test_stress_pulse_second_moment_grows_4Dt():
+    # Heun + 5-point Laplacian: sum x^2 s grows by exactly 4 D sum s per step (2D).
+    n, D = 48, 0.1
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, Dp=D, ericksen=0)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r2 = (x - 24) ** 2 + (y - 24) ** 2
+    sig0 = np.zeros((3, n, n)); sig0[2] = 1e-9 * np.exp(-r2 / (2 * 2.0 ** 2))
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))), sig0.copy(),
+                np.zeros((2, n, n)), np.zeros((0, 2)))
+    steps = 30
+    sim.step(steps)
+    m0 = sig0[2].sum()
+    m2a = (r2 * sig0[2]).sum()
+    m2b = (r2 * sim.sigma[2]).sum()
+    assert abs(sim.sigma[2].sum() - m0) < 1e-12 * m0
+    assert abs((m2b - m2a) - 4 * D * steps * m0) < 1e-6 * (4 * D * steps * m0)
+
+
+def _P_relax(Gamma, steps, p0=0.3, alpha=-0.9, beta=1.0):
+    n = 4
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, alpha=alpha, beta=beta, xi=1.1, Gamma=Gamma,
+                 kappa=1e-3)
+    th = 0.4
+    P = np.zeros((2, n, n)); P[0] = p0 * math.cos(th); P[1] = p0 * math.sin(th)
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))),
+                np.zeros((3, n, n)), P, np.zeros((0, 2)))
+    sim.step(steps)
+    Pm = np.hypot(sim.P[0], sim.P[1])
+    assert np.abs(Pm - Pm[0, 0]).max() < 1e-15
+    ang = np.arctan2(sim.P[1, 0, 0], sim.P[0, 0, 0])
+    assert abs(ang - th) < 1e-14
+    return Pm[0, 0]
+
+
+def test_P_relaxation_logistic_second_order():
+    # Eq. BE with uniform P and no flow: y = |P|^2 obeys dy/dt = 2 Gamma |alpha| y (1 - y/y_eq)
+    alpha, beta, p0, T = -0.9, 1.0, 0.3, 3.0
+    yeq = -alpha / beta
+    errs = []
+    for G, n in [(0.1, 30), (0.05, 60), (0.025, 120)]:
+        pm = _P_relax(G, n, p0, alpha, beta)
+        y = yeq / (1 + (yeq / p0 ** 2 - 1) * math.exp(-2 * abs(alpha) * G * n))
+        errs.append(abs(pm - math.sqrt(y)))
+    assert errs[2] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_P_equilibrium_matches_printed_value():
+    g = GOLD["P_eq_text"]
+    pm = _P_relax(1.0, 200, 0.3, g["alpha"], g["beta"])
+    assert round(pm, g["decimals"]) == g["P_eq_approx"]
+    assert abs(pm - math.sqrt(-g["alpha"] / g["beta"])) < 1e-14
+
+
+def test_objectivity_rigid_rotation():
+    # With u a rigid rotation (Psi = 0, omega = w0), Eq. StiffCons (C = 0) and Eq. BE reduce to
+    # the co-rotation of a uniform tensor and vector: d sigma/dt = W sigma - sigma W, dP/dt = W P
+    # with W the rotation generator.
+    n, w0 = 6, 0.013
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, alpha=-0.9, beta=1.0, xi=1.1, Gamma=1.0,
+                 kappa=1e-3)
+    Peq = math.sqrt(0.9)
+    Pv = np.array([Peq * math.cos(0.5), Peq * math.sin(0.5)])
+    S = np.array([[2e-4, 7e-5], [7e-5, -1e-4]])
+    sig = np.broadcast_to(np.array([S[0, 0], S[1, 1], S[0, 1]])[:, None, None], (3, n, n)).copy()
+    P = np.broadcast_to(Pv[:, None, None], (2, n, n)).copy()
+    ds, dP = O.rhs(p, sig, P, np.zeros((2, n, n)), np.zeros((3, n, n)), np.full((n, n), w0))
+    # generator of the rigid rotation R(w0 t): dR/dt at t = 0
+    Wg = np.array([[0.0, -w0], [w0, 0.0]])
+    dS = Wg @ S - S @ Wg
+    dPv = Wg @ Pv
+    assert np.allclose(ds[:, 0, 0], [dS[0, 0], dS[1, 1], dS[0, 1]], atol=1e-18, rtol=0)
+    # Gamma h(P_eq) is zero up to the rounding of alpha + beta P_eq^2
+    assert np.allclose(dP[:, 0, 0], dPv, atol=1e-15, rtol=0)
+
+
+# ----------------------------------------------------------------------------------------
+# Whole coupled step: conservation and mirror symmetry
+# ----------------------------------------------------------------------------------------
+
+def test_conservation_coupled_step():
+    w = W.small(24, 20, steps=0)
+    sim = O.Sim.from_workload(w)
+    sim.step(31, every=1)
+    s = np.array(sim.series)
+    N = 24 * 20
+    assert np.abs(s[:, 1]).max() < 1e-13 * N                    # mass
+    pull = np.array([1e-3 * math.cos(0.3), 1e-3 * math.sin(0.3)])
+    assert np.abs(s[:, 4:6] - pull).max() < 1e-15               # total force = pull
+    dmom = np.diff(s[:, 2:4], axis=0)
+    assert np.abs(dmom - s[:-1, 4:6]).max() < 1e-14             # d(momentum) = F
+
+
+def test_mirror_symmetry_parallel_pull():
+    # Director along x, no noise, ring symmetric about y = 16, pull along x (Sec. III B):
+    # fields are mirror symmetric and the restoring force has no y component.
+    w = W.make(32, 32, rings=[W.ring(20, 5.0, (16.0, 16.0), pull_force=1e-3, pull_angle=0.0)],
+               noise_amp=0.0, lambda_steps=50.0, Dp=0.05)
+    sim = O.Sim.from_workload(w)
+    sim.step(41, every=10)
+    f = sim.fields()
+    m = lambda a: np.roll(a[::-1], 1, axis=0)                 # y -> 32 - y
+    for k, sgn in [("drho", 1), ("ux", 1), ("uy", -1), ("sxx", 1), ("syy", 1), ("sxy", -1),
+                   ("Px", 1), ("Py", -1)]:
+        a = f[k]
+        # rho = rho0 + drho carries rounding of O(1e-16) (the scale of rho0)
+        assert np.abs(a - sgn * m(a)).max() <= 1e-11 * np.abs(a).max() + 1e-14, k
+    s = np.array(sim.series)
+    assert np.abs(s[:, 7]).max() < 1e-12 * np.abs(s[:, 6]).max()
+
+
+def test_advection_sign_and_discrete_speed():
+    # -(u.grad) sigma with central differences: for sigma = cos(k x) and uniform u = U x^,
+    # d sigma/dt = U sin(k) sin(k x) (the mode moves towards +x).
+    n, U = 16, 0.03
+    k = 2 * np.pi * 3 / n
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, ericksen=0)
+    x = np.arange(n, dtype=float)[None, :] * np.ones((n, 1))
+    sig = np.stack([np.cos(k * x), np.zeros((n, n)), np.zeros((n, n))])
+    u = np.stack([np.full((n, n), U), np.zeros((n, n))])
+    ds, _ = O.rhs(p, sig, np.zeros((2, n, n)), u, np.zeros((3, n, n)), np.zeros((n, n)))
+    assert np.abs(ds[0] - U * np.sin(k) * np.sin(k * x)).max() < 1e-16
+
+
+def test_flow_aligning_angle():
+    # Eq. BE in simple shear u = (g y, 0): the director angle obeys
+    # d theta/dt = -g/2 + (xi g / 2) cos 2 theta, steady at cos 2 theta = 1/xi (|xi| > 1).
+    n, g, xi = 4, 1e-3, 1.1
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, alpha=-0.9, beta=1.0, xi=xi, Gamma=1.0,
+                 kappa=1e-3)
+    psi = np.zeros((3, n, n)); psi[2] = g / 2
+    om = np.full((n, n), -g / 2)
+    Peq = math.sqrt(0.9)
+    for th in [0.5 * math.acos(1 / xi), -0.5 * math.acos(1 / xi), 0.0, 1.0]:
+        P = np.zeros((2, n, n)); P[0] = Peq * math.cos(th); P[1] = Peq * math.sin(th)
+        _, dP = O.rhs(p, np.zeros((3, n, n)), P, np.zeros((2, n, n)), psi, om)
+        rate = (P[0] * dP[1] - P[1] * dP[0]) / Peq ** 2
+        ref = -g / 2 + xi * g / 2 * math.cos(2 * th)
+        assert np.abs(rate - ref).max() < 1e-15
+
+
+def _smooth(rng, x, y, kmax=2, amp=0.1):
+    f = np.zeros_like(x)
+    for kx in range(-kmax, kmax + 1):
+        for ky in range(-kmax, kmax + 1):
+            if kx or ky:
+                f += amp * rng.normal() * np.cos(kx * x + ky * y + rng.uniform(0, 2 * np.pi))
+    return f
+
+
+def _ericksen_power_residual(N, kappa_phys=0.1):
+    # the same smooth fields on [0, 2 pi)^2 sampled with N cells (dx = 2 pi / N)
+    rng = np.random.default_rng(4)
+    dx = 2 * np.pi / N
+    y, x = np.mgrid[0:N, 0:N] * dx
+    P = np.stack([0.7 + _smooth(rng, x, y), 0.3 + _smooth(rng, x, y)])
+    D_x = lambda f: 0.5 * (np.roll(f, -1, 1) - np.roll(f, 1, 1))
+    D_y = lambda f: 0.5 * (np.roll(f, -1, 0) - np.roll(f, 1, 0))
+    lap = lambda f: np.roll(f, 1, 0) + np.roll(f, -1, 0) + np.roll(f, 1, 1) + np.roll(f, -1, 1) - 4 * f
+    stream = 1e-3 * _smooth(rng, x, y, amp=1.0) / dx
+    v = np.stack([D_y(stream), -D_x(stream)])               # discretely divergence-free
+    kap = kappa_phys / dx ** 2
+    p = O.Params(nx=N, ny=N, tau=0.8, eta_p=1.0, alpha=-0.9, beta=1.0, xi=1.1, Gamma=0.0,
+                 kappa=kap, ericksen=1)
+    q = (P ** 2).sum(0)
+    h = np.stack([(p.alpha + p.beta * q) * P[c] - kap * lap(P[c]) for c in range(2)])
+    psi = np.stack([D_x(v[0]), D_y(v[1]), 0.5 * (D_x(v[1]) + D_y(v[0]))])
+    om = 0.5 * (D_x(v[1]) - D_y(v[0]))
+    _, dP = O.rhs(p, np.zeros((3, N, N)), P, v, psi, om)     # reactive part (Gamma = 0)
+    F, _ = O.forces(p, [], np.zeros((3, N, N)), P, np.zeros((0, 2)))
+    A = (h * dP).sum()                                        # dF/dt from Eq. BE
+    B = (v * F).sum()                                         # power of f^E on the flow
+    return abs(A + B) / abs(B)
+
+
+def test_ericksen_stress_balances_beris_edwards_power():
+    # For a divergence-free flow the reactive terms of Eq. BE change the free energy at the
+    # rate that f^E = div sigma^E does work on the fluid (a consistency check of the printed
+    # signs of sigma^E against Eq. BE; kappa restored per the reading of the last term).
+    r32, r64 = _ericksen_power_residual(32), _ericksen_power_residual(64)
+    assert r64 < 3e-3
+    assert 3.5 < r32 / r64 < 4.5                              # second order in dx
