@@ -1,0 +1,310 @@
+"""Throughput of the fused viscoelastic IB-LB step on GB300 (one JSON line on rank 0).
+
+Workload: the 1024 x 1024 periodic lattice with one 256-node ring of radius 24 pulled at 30
+degrees to the director with 5e-4, D_p = 0.1, relaxation time 200 steps (Tables III-IV
+ratios, synthetic seeded input).  One bench step = lb_step(10): ten LB time steps, i.e. one
+readout period (restoring force, mass, momentum, total force recorded once).  Every rank runs
+its own independent lattice (the path does not shard; replicas only, weak scaling).
+
+value     MLUPS = cells x LB steps / device time, inputs resident in HBM, L2 flushed (256 MB
+          write) between timed steps, each timed step bracketed by CUDA events.
+roofline  fused lattice kernel: algorithmic bytes (112 B/cell: 14 FP32 fields read + written)
+          x cells / mean launch duration (CUDA events around each launch inside the timed
+          steps), against the measured HBM copy bandwidth.
+e2e       the same metric through the C ABI with host buffers: per step the whole state is
+          uploaded from pinned host memory, ten steps run, and the readout row is copied back.
+--impl reference   the FP64 CPU oracle on the host cores, on a bounded sample (512 x 512 with
+          the same physics and ring), one LB time step per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS of fused viscoelastic LB step + % HBM roofline; restoring-force err vs FP64"
+LB_STEPS_PER_STEP = 10
+WORKLOAD = ("1024x1024 periodic D2Q9, tau 0.8; one ring of 256 nodes, radius 24, pulled with "
+            "5e-4 at 30 deg to the director; D_p 0.1, relaxation 200 steps; FP32 state")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), \
+        int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "fused_step_1024x1024.txt")
+    src = os.path.join(ROOT, "paper_2209_14889_gb300", "csrc", "lb_fused.cu")
+    if not os.path.exists(path):
+        return None
+    info = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            info[k.strip()] = v.strip()
+    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if info.get("kernel_source_sha1") != sha or "dram_bytes_per_launch" not in info:
+        return None
+    return float(info["dram_bytes_per_launch"])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = "/tmp/vlb_clocks_%d.csv" % os.getpid()
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def frest_error_check():
+    """Restoring-force error of the GPU path vs the FP64 oracle on the 64 x 64 workload for 200
+    steps (20 readouts): relative L2 over the series."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2209_14889_gb300 import lb, workloads as W
+    w = W.cfg1()
+    s = lb.Solver.from_workload(w)
+    s.step(200)
+    s.sync()
+    g = s.series()[:, 6:8]
+    s.close()
+    sim = O.Sim.from_workload(w)
+    sim.step(200, every=10)
+    r = np.array(sim.series)[:, 6:8]
+    return float(np.linalg.norm(g - r) / np.linalg.norm(r))
+
+
+def run_reference(args, rank, world):
+    """FP64 oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    from paper_2209_14889_gb300 import workloads as W
+    w = W.make(512, 512, rings=[W.ring(256, 24.0, (256.0, 256.0), pull_force=5e-4,
+                                       pull_angle=math.radians(30))],
+               seed=2, lambda_steps=200.0, Dp=0.1)
+    sim = O.Sim.from_workload(w)
+    cells = 512 * 512
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(1, every=10)
+    dt = time.perf_counter() - t0
+    v = cells * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "512x512 lattice, same physics and ring, "
+                       "one LB time step per bench step", "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "512x512, 1 LB step per bench step, %d steps" % args.steps},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on one host core, on a bounded sample of the workload: one LB
+    time step of the 1024 x 1024 lattice."""
+    import oracle as O
+    from paper_2209_14889_gb300 import workloads as W
+    w = W.cfg2()
+    sim = O.Sim.from_workload(w)
+    t0 = time.perf_counter()
+    sim.step(1)
+    dt = time.perf_counter() - t0
+    return {"value": 1024 * 1024 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "1 LB time step of the 1024x1024 workload (%.1f s)" % dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2209_14889_gb300 import lb, workloads as W
+
+    w = W.cfg2(seed=2 + rank)
+    cells = w["nx"] * w["ny"]
+    s = lb.Solver.from_workload(w)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush.zero_()
+        s.step(LB_STEPS_PER_STEP)
+    s.sync()
+
+    # timed steps (device time), fused-kernel events inside
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    s.timing(True)
+    with Clocks(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            s.step(LB_STEPS_PER_STEP)
+            ev[k][1].record(stream)
+        barrier()
+    s.sync()
+    kt = s.kernel_time()
+    s.timing(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cells = cells * LB_STEPS_PER_STEP * args.steps * world
+    value = total_cells / (ms * 1e-3) / 1e6
+
+    # roofline of the fused lattice kernel
+    peaks, peak_kind = measured_peaks()
+    fused_avg_s = kt["fused_ms"] * 1e-3 / max(kt["fused_launches"], 1)
+    bytes_launch = s.bytes_per_cell * cells
+    achieved = bytes_launch / fused_avg_s / 1e9
+    traffic = ncu_traffic()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "k_fused (fused lattice step)", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "mean_launch_us": fused_avg_s * 1e6,
+            "node_kernel_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1)}
+
+    # end to end through the C ABI with host buffers
+    host = {}
+    names = ["pop%d" % n for n in range(9)] + ["sxx", "syy", "sxy", "Px", "Py"]
+    for nm in names:
+        host[nm] = s.readout(nm, device=False)
+    pinned = {nm: torch.from_numpy(host[nm]).pin_memory() for nm in names}
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        for nm in names:
+            s.write_field(nm, pinned[nm])
+        s.step(LB_STEPS_PER_STEP)
+        row = s.series()[-1:]
+        d2h = row.nbytes
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    h2d = sum(pinned[nm].numel() * 4 for nm in names)
+    e2e = {"value": cells * LB_STEPS_PER_STEP * e2e_steps * world / e2e_dt / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h),
+           "steps": e2e_steps}
+
+    rc = lb.lib().lb_sync(s.h)
+    s.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    frest_err = frest_error_check()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_sample()
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": [w["nx"], w["ny"]],
+                       "lb_steps_per_step": LB_STEPS_PER_STEP,
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "gpu_launches": 2 * LB_STEPS_PER_STEP * args.steps,
+            "frest_err_vs_fp64": {"value": frest_err, "workload": "64x64, 200 steps, 20 readouts"},
+            "status": int(rc)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

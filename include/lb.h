@@ -1,0 +1,165 @@
+/*
+ * lb.h -- C ABI of the GB300 (sm_103a) immersed-boundary / lattice-Boltzmann solver for a
+ * tensorial viscoelastic fluid (Floyd, Vaikuntanathan, Dinner, arXiv 2209.14889).
+ *
+ * One time step (Fig. 2; every field is updated from the state at t):
+ *   node forces f_a = -grad U (App. A, Eq. Const, with a constant pull in place of the trap),
+ *   spreading f_IB = sum_a f_a K(R_a - r) (App. A), polymer force f^p = div sigma^p (Sec. II B),
+ *   Ericksen force f^E = div sigma^E (Sec. II C 1), D2Q9 BGK collide + stream with the Guo
+ *   body force (Sec. II A, Eq. LB, Eq. BGK), predictor-corrector updates of sigma^p
+ *   (Eq. StiffCons with C~(P) of App. B) and of P (Eq. BE), and overdamped advection of the
+ *   nodes by the interpolated velocity (App. A).
+ *
+ * Units: lattice units (dx = dt = 1, c_s^2 = 1/3).  Periodic lattice in x and y.
+ * Fields are [y][x] planes, x fastest, FP32 on the device.
+ *
+ * Ownership: the handle owns every device buffer it allocates (cudaMalloc in lb_create and
+ * lb_set_body) and frees them in lb_destroy.  Pointers passed in are only read or written
+ * during the call.  Every launch and copy goes on the stream given to lb_create; calls that
+ * return data to the host synchronise that stream.  A handle is not thread-safe.
+ *
+ * Errors: every int-returning call returns LB_OK (0) or a negative LB_E* code;
+ * lb_last_error() describes the last failure.  Numerical trouble detected on the device
+ * (non-finite readouts, a ring leaving its work box, node displacement >= 1 cell per step)
+ * is reported by lb_sync().
+ */
+#ifndef VLB_LB_H
+#define VLB_LB_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_EINVAL (-1)      /* bad argument or parameter                                */
+#define LB_ENOMEM (-2)      /* device allocation failed                                 */
+#define LB_ECUDA (-3)       /* CUDA runtime error (message in lb_last_error)             */
+#define LB_ENONFINITE (-4)  /* a readout (mass, momentum, force, node) became NaN/Inf    */
+#define LB_EUNSTABLE (-5)   /* parameters outside the explicit stability bounds          */
+#define LB_EBODY (-6)       /* a ring left its work box or moved >= 1 cell in one step   */
+#define LB_ESTATE (-7)      /* call out of order (e.g. lb_step before lb_init_fields)    */
+
+/* Storage precision of the lattice state. */
+#define LB_FP32 0
+
+/* Field identifiers for lb_readout / lb_write_field. */
+#define LB_FIELD_DRHO 0     /* rho - rho0 of the current state (readout only)           */
+#define LB_FIELD_UX 1       /* u_x = (sum c h + F/2)_x / rho (readout only)              */
+#define LB_FIELD_UY 2
+#define LB_FIELD_SXX 3      /* polymer stress sigma^p_xx                                 */
+#define LB_FIELD_SYY 4
+#define LB_FIELD_SXY 5
+#define LB_FIELD_PX 6       /* polarisation P_x                                          */
+#define LB_FIELD_PY 7
+#define LB_FIELD_POP0 8     /* LB_FIELD_POP0 + n: h_n - w_n rho0 (stored form), n = 0..8 */
+#define LB_FIELD_NODES 17   /* node positions, FP64 [n_total][2], wrapped into the box   */
+
+typedef struct lb_params {
+    int32_t nx, ny;                 /* lattice size, each >= 8                                */
+    double tau, rho0;               /* BGK relaxation time (Eq. BGK), rest density            */
+    double K1111, K1122, K2222, K1212; /* K^x of Eq. Kmatrix (prefactor absorbed, App. B)    */
+    double eta_p;                   /* polymer viscosity (Eq. StiffCons); if <= 0, taken as   */
+    double lambda_steps;            /*   lambda_steps * C~11(k = 0) (relaxation time in steps)*/
+    double Dp;                      /* stress diffusion D_p (Eq. MaxDiff)                      */
+    double alpha, beta, xi, Gamma, kappa; /* Beris-Edwards (Eq. BE, Eq. Ffunctional)          */
+    double P_cap;                   /* cap on |P| when solving Eq. Pk (0.99)                  */
+    double director_angle;          /* initial director angle theta_d (radians)               */
+    int32_t ericksen;               /* 1: include f^E in the body force                        */
+    int32_t precision;              /* LB_FP32                                                 */
+    int32_t readout_every;          /* record readouts when t % readout_every == 0 (10)       */
+    int32_t max_samples;            /* capacity of the readout ring buffer (rows)             */
+} lb_params;
+
+typedef struct lb_ring {
+    int32_t n_nodes;                /* 3 <= n_nodes <= 1024                                    */
+    int32_t pad_;
+    double k_spring, eps_angle;     /* Eq. Const: spring and angle stiffness                   */
+    double l_eq;                    /* spring rest length                                      */
+    double pull_force, pull_angle;  /* constant total pull on the ring, split over its nodes  */
+} lb_ring;
+
+typedef struct lb_handle lb_handle;
+
+/*
+ * Create a solver.  Validates the parameters (stability: 0.5 < tau, 8 D_p <= 2 for the Heun
+ * step of the diffusion term, Gamma*|alpha| linear rate <= 2, else LB_EUNSTABLE), allocates
+ * the double-buffered state (2 x 14 FP32 planes of nx*ny) and builds the C~(P) table on the
+ * host (FP64, Eq. Pk inverted numerically, App. B).  stream: a cudaStream_t (NULL = default).
+ */
+int lb_create(const lb_params* p, void* stream, lb_handle** out);
+
+/*
+ * Initial state: h_n = w_n rho0 (fluid at rest), sigma^p = 0,
+ * P = P_eq (cos theta_d, sin theta_d) + noise with P_eq = sqrt(-alpha/beta) (Sec. III B)
+ * (0 if alpha >= 0).  noise: host FP64 [2][ny][nx] added to P, or NULL.
+ * Resets the step counter to 0 and clears the readout series.
+ */
+int lb_init_fields(lb_handle* h, const double* noise);
+
+/*
+ * Immersed rings (App. A).  xy: host FP64 positions [n_total][2], ring after ring, in lattice
+ * coordinates (cell (i, j) sits at (i, j)); copied.  Replaces any previous rings and computes
+ * the forces of the initial configuration.  Each ring must fit in a box of
+ * min(nx, ny) - 8 cells.
+ */
+int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const double* xy);
+
+/* Advance n time steps, asynchronously on the handle's stream. */
+int lb_step(lb_handle* h, int64_t n);
+
+/* Synchronise the stream and return LB_OK or the first device-side error (LB_ENONFINITE,
+ * LB_EBODY) raised since the last lb_sync. */
+int lb_sync(lb_handle* h);
+
+/* Current step counter t (host copy). */
+int64_t lb_time(const lb_handle* h);
+
+/*
+ * Copy one field of the current state to dst (FP32 [ny][nx], or FP64 [n_total][2] for
+ * LB_FIELD_NODES).  bytes must equal the field size.  dst_is_device: 1 if dst is device
+ * memory, 0 for host memory.  DRHO/UX/UY run the force + moment part of the step on the
+ * current state.  Synchronises the stream.
+ */
+int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
+
+/* Overwrite one stored field (SXX..PY, POP0..POP8) of the current state from FP32 [ny][nx]. */
+int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, int32_t src_is_device);
+
+/*
+ * Readout series, one row per recorded step, oldest first:
+ *   [t, sum(rho - rho0), sum c h (x, y), sum F (x, y),
+ *    then per ring: F_rest (x, y), centre of mass (x, y)]
+ * F_rest = sum_a sum_r f^p(r) K(R_a - r), the polymer force density (div sigma^p, called the
+ * restoring force in Sec. III A) interpolated to the nodes and summed over the ring.
+ * Sums are FP64 over FP32 values in a fixed order.  Row length: 6 + 4 n_rings.
+ * dst: host FP64 [max_rows][row length].  *rows_written gets the number of rows copied.
+ */
+int lb_series(lb_handle* h, double* dst, int32_t max_rows, int32_t* rows_written);
+int32_t lb_series_row_len(const lb_handle* h);
+
+/* Restoring force of ring `ring` for the recorded rows: host FP64 [max_k][2]. */
+int lb_restoring_force(lb_handle* h, int32_t ring, double* dst, int32_t max_k, int32_t* k_written);
+
+/*
+ * Kernel timing for throughput and roofline reports.  enable = 1 brackets every launch of
+ * the fused lattice kernel with CUDA events on the handle's stream; lb_kernel_time returns
+ * the summed device time (ms) and the launch count since timing was enabled.
+ */
+int lb_timing(lb_handle* h, int32_t enable);
+int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, double* node_ms,
+                   int64_t* node_launches);
+
+/* Number of kernels launched per lb_step(1) call (2: fused lattice + node kernel). */
+int32_t lb_launches_per_step(const lb_handle* h);
+
+/* Bytes of lattice state per cell moved by one step (read + write, the algorithmic minimum). */
+double lb_bytes_per_cell(const lb_handle* h);
+
+const char* lb_last_error(const lb_handle* h);
+void lb_destroy(lb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,537 @@
+// lb_api.cu -- the C ABI declared in include/lb.h: handle, validation, device buffers, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+using namespace vlb;
+
+struct lb_handle {
+    lb_params p;
+    cudaStream_t stream = nullptr;
+    Phys ph;
+    double eta_p = 0.0;
+    long long plane = 0;
+    float* state[2] = {nullptr, nullptr};   // N_PLANES planes each
+    int cur = 0;
+    float2* lut = nullptr;
+    Ctl* ctl = nullptr;
+    double* partials = nullptr;
+    int n_partials = 0;
+    double* series = nullptr;
+    int series_cap = 0;
+    int row_len = 6;
+    float* moments = nullptr;               // 3 planes, allocated on first use
+    // rings
+    int n_rings = 0, n_total = 0;
+    RingDev* rings = nullptr;
+    double2* X = nullptr;
+    int2* node_cell = nullptr;
+    float2* node_frac = nullptr;
+    float2* node_force = nullptr;
+    float* ubox = nullptr;
+    float* fpbox = nullptr;
+    long long box_floats = 0;
+    bool fields_ready = false;
+    long long t = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_fused, ev_nodes;
+    size_t ev_fused_used = 0, ev_nodes_used = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_err;
+
+int fail(lb_handle* h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_err = buf;
+    return code;
+}
+
+int cuda_fail(lb_handle* h, cudaError_t e, const char* what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                         \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+template <class T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void free_rings(lb_handle* h)
+{
+    dfree(h->rings);
+    dfree(h->X);
+    dfree(h->node_cell);
+    dfree(h->node_frac);
+    dfree(h->node_force);
+    dfree(h->ubox);
+    dfree(h->fpbox);
+    h->n_rings = h->n_total = 0;
+    h->row_len = 6;
+}
+
+cudaEvent_t ev_get(std::vector<cudaEvent_t>& pool, size_t& used)
+{
+    if (used == pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+    }
+    return pool[used++];
+}
+
+FusedArgs fused_args(lb_handle* h)
+{
+    FusedArgs a;
+    a.src = h->state[h->cur];
+    a.dst = h->state[h->cur ^ 1];
+    a.plane = h->plane;
+    a.nx = h->p.nx;
+    a.ny = h->p.ny;
+    a.ph = h->ph;
+    a.lut = h->lut;
+    a.n_rings = h->n_rings;
+    a.rings = h->rings;
+    a.node_cell = h->node_cell;
+    a.node_frac = h->node_frac;
+    a.node_force = h->node_force;
+    a.ubox = h->ubox;
+    a.fpbox = h->fpbox;
+    a.partials = h->partials;
+    a.ctl = h->ctl;
+    a.every = h->p.readout_every;
+    a.moments_out = h->moments;
+    return a;
+}
+
+NodeArgs node_args(lb_handle* h, int advance)
+{
+    NodeArgs a;
+    a.n_rings = h->n_rings;
+    a.rings = h->rings;
+    a.X = h->X;
+    a.node_cell = h->node_cell;
+    a.node_frac = h->node_frac;
+    a.node_force = h->node_force;
+    a.ubox = h->ubox;
+    a.fpbox = h->fpbox;
+    a.partials = h->partials;
+    a.n_partials = h->n_partials;
+    a.series = h->series;
+    a.series_cap = h->series_cap;
+    a.row_len = h->row_len;
+    a.ctl = h->ctl;
+    a.every = h->p.readout_every;
+    a.nx = h->p.nx;
+    a.ny = h->p.ny;
+    a.advance = advance;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_create(const lb_params* pin, void* stream, lb_handle** out)
+{
+    if (!pin || !out) return fail(nullptr, LB_EINVAL, "null argument");
+    *out = nullptr;
+    const lb_params& p = *pin;
+    if (p.nx < 8 || p.ny < 8) return fail(nullptr, LB_EINVAL, "nx, ny must be >= 8");
+    if ((long long)p.nx * p.ny > (1LL << 31)) return fail(nullptr, LB_EINVAL, "lattice too large");
+    if (p.precision != LB_FP32) return fail(nullptr, LB_EINVAL, "unsupported precision %d", p.precision);
+    if (!(p.tau > 0.5) || !(p.rho0 > 0.0)) return fail(nullptr, LB_EINVAL, "need tau > 1/2, rho0 > 0");
+    if (!(p.P_cap > 0.0 && p.P_cap < 1.0)) return fail(nullptr, LB_EINVAL, "need 0 < P_cap < 1");
+    if (p.readout_every < 1 || p.max_samples < 1) return fail(nullptr, LB_EINVAL, "bad readout settings");
+    const double S8 = (3 * p.K1111 + 2 * p.K1122 + 4 * p.K1212 + 3 * p.K2222) / 8.0;
+    double eta = p.eta_p;
+    if (!(eta > 0.0)) eta = p.lambda_steps * S8;
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(nullptr, LB_EINVAL, "need eta_p > 0 or lambda_steps > 0");
+    // explicit stability bounds of the Heun steps (|z| <= 2 on the negative real axis)
+    if (p.Dp < 0.0 || 8.0 * p.Dp > 2.0)
+        return fail(nullptr, LB_EUNSTABLE, "D_p = %g outside [0, 0.25] (Heun + 5-point Laplacian)", p.Dp);
+    const double be_rate = p.Gamma * (2.0 * std::fabs(p.alpha) + 8.0 * p.kappa);
+    if (p.Gamma < 0.0 || p.kappa < 0.0 || be_rate > 2.0)
+        return fail(nullptr, LB_EUNSTABLE, "Gamma (2|alpha| + 8 kappa) = %g > 2", be_rate);
+    const double c_rate = (std::fabs(S8) + std::fabs(p.K1111 - p.K2222) +
+                           std::fabs(p.K1111 - 2 * p.K1122 - 4 * p.K1212 + p.K2222)) / eta;
+    if (c_rate > 2.0) return fail(nullptr, LB_EUNSTABLE, "stress relaxation rate %g > 2", c_rate);
+
+    lb_handle* h = new lb_handle();
+    h->p = p;
+    h->stream = (cudaStream_t)stream;
+    h->eta_p = eta;
+    h->plane = (long long)p.nx * p.ny;
+    Phys& ph = h->ph;
+    ph.omega = (float)(1.0 / p.tau);
+    ph.guo = (float)(1.0 - 0.5 / p.tau);
+    ph.rho0 = (float)p.rho0;
+    ph.alpha = (float)p.alpha;
+    ph.beta = (float)p.beta;
+    ph.xi = (float)p.xi;
+    ph.Gamma = (float)p.Gamma;
+    ph.kappa = (float)p.kappa;
+    ph.Dp = (float)p.Dp;
+    ph.inv_eta = (float)(1.0 / eta);
+    ph.kS8 = (float)S8;
+    ph.kC12 = (float)((p.K1111 + 6 * p.K1122 - 4 * p.K1212 + p.K2222) / 8.0);
+    ph.kC33 = (float)((p.K1111 - 2 * p.K1122 + 4 * p.K1212 + p.K2222) / 4.0);
+    ph.dK = (float)(p.K1111 - p.K2222);
+    ph.kX = (float)(p.K1111 - 2 * p.K1122 - 4 * p.K1212 + p.K2222);
+    ph.q_cap = (float)(p.P_cap * p.P_cap);
+    ph.lut_scale = (float)(LUT_N / (p.P_cap * p.P_cap));
+    ph.ericksen = p.ericksen ? 1 : 0;
+
+    int rc = LB_OK;
+    auto bail = [&](int code) {
+        lb_destroy(h);
+        return code;
+    };
+    const size_t state_bytes = sizeof(float) * N_PLANES * (size_t)h->plane;
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = cudaMalloc(&h->state[b], state_bytes);
+        if (e != cudaSuccess) { rc = cuda_fail(nullptr, e, "cudaMalloc(state)"); return bail(rc); }
+    }
+    std::vector<float> lut(2 * (LUT_N + 1));
+    build_lut(p.P_cap, lut.data());
+    h->n_partials = fused_ctas(p.nx, p.ny);
+    h->series_cap = p.max_samples;
+    cudaError_t e;
+    if ((e = cudaMalloc(&h->lut, sizeof(float) * lut.size())) != cudaSuccess ||
+        (e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess ||
+        (e = cudaMalloc(&h->partials, sizeof(double) * 5 * (size_t)h->n_partials)) != cudaSuccess) {
+        rc = cuda_fail(nullptr, e, "cudaMalloc");
+        return bail(rc);
+    }
+    if ((e = cudaMemcpy(h->lut, lut.data(), sizeof(float) * lut.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(h->ctl, 0, sizeof(Ctl))) != cudaSuccess) {
+        rc = cuda_fail(nullptr, e, "upload");
+        return bail(rc);
+    }
+    if ((e = cudaMalloc(&h->series, sizeof(double) * (size_t)h->series_cap * 6)) != cudaSuccess) {
+        rc = cuda_fail(nullptr, e, "cudaMalloc(series)");
+        return bail(rc);
+    }
+    *out = h;
+    return LB_OK;
+}
+
+int lb_init_fields(lb_handle* h, const double* noise)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    const lb_params& p = h->p;
+    const size_t N = (size_t)h->plane;
+    std::vector<float> buf(N);
+    float* S = h->state[h->cur];
+    // populations at rest (shifted form: zero) and sigma = 0
+    CK(h, cudaMemsetAsync(S, 0, sizeof(float) * (PL_PY + 1) * N, h->stream));
+    const double Peq = (p.alpha < 0.0 && p.beta > 0.0) ? std::sqrt(-p.alpha / p.beta) : 0.0;
+    for (int c = 0; c < 2; ++c) {
+        const double base = Peq * (c == 0 ? std::cos(p.director_angle) : std::sin(p.director_angle));
+        for (size_t i = 0; i < N; ++i) buf[i] = (float)(base + (noise ? noise[c * N + i] : 0.0));
+        CK(h, cudaMemcpyAsync(S + (PL_PX + c) * N, buf.data(), sizeof(float) * N, cudaMemcpyHostToDevice,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
+    h->t = 0;
+    h->fields_ready = true;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const double* xy)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (n_rings < 0 || (n_rings > 0 && (!rings || !xy))) return fail(h, LB_EINVAL, "bad rings");
+    CK(h, cudaStreamSynchronize(h->stream));
+    free_rings(h);
+    const int nx = h->p.nx, ny = h->p.ny;
+    std::vector<RingDev> rd(n_rings);
+    std::vector<double2> X;
+    long long box_off = 0;
+    int off = 0;
+    for (int r = 0; r < n_rings; ++r) {
+        const lb_ring& g = rings[r];
+        if (g.n_nodes < 3 || g.n_nodes > 1024) return fail(h, LB_EINVAL, "ring %d: 3 <= n_nodes <= 1024", r);
+        if (!(g.l_eq > 0.0) || g.k_spring < 0.0) return fail(h, LB_EINVAL, "ring %d: bad spring", r);
+        double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+        const double* P = xy + 2 * (size_t)off;
+        for (int k = 0; k < g.n_nodes; ++k) {
+            double dx = P[2 * k] - P[0], dy = P[2 * k + 1] - P[1];
+            dx -= nx * std::floor(dx / nx + 0.5);
+            dy -= ny * std::floor(dy / ny + 0.5);
+            mnx = std::fmin(mnx, dx); mxx = std::fmax(mxx, dx);
+            mny = std::fmin(mny, dy); mxy = std::fmax(mxy, dy);
+            if (!std::isfinite(P[2 * k]) || !std::isfinite(P[2 * k + 1]))
+                return fail(h, LB_EINVAL, "ring %d: non-finite node", r);
+            double xw = std::fmod(P[2 * k], (double)nx); if (xw < 0) xw += nx; if (xw >= nx) xw -= nx;
+            double yw = std::fmod(P[2 * k + 1], (double)ny); if (yw < 0) yw += ny; if (yw >= ny) yw -= ny;
+            X.push_back(make_double2(xw, yw));
+        }
+        // box capacity: the initial extent + supports + a margin for motion and deformation
+        const int lim = std::min(nx, ny) - 8;
+        int cw = (int)std::ceil(mxx - mnx) + 8, chh = (int)std::ceil(mxy - mny) + 8;
+        if (cw > lim || chh > lim) return fail(h, LB_EINVAL, "ring %d does not fit the lattice", r);
+        cw = std::min(cw + 2 * std::max(16, cw / 2), lim);
+        chh = std::min(chh + 2 * std::max(16, chh / 2), lim);
+        RingDev& d = rd[r];
+        d.n_nodes = g.n_nodes;
+        d.node_off = off;
+        d.k_spring = g.k_spring;
+        d.eps_angle = g.eps_angle;
+        d.l_eq = g.l_eq;
+        d.pull_x = g.pull_force * std::cos(g.pull_angle) / g.n_nodes;
+        d.pull_y = g.pull_force * std::sin(g.pull_angle) / g.n_nodes;
+        d.box_x0 = d.box_y0 = 0;
+        d.box_w = d.box_h = 0;
+        d.cap_w = cw;
+        d.cap_h = chh;
+        d.box_off = box_off;
+        box_off += 2LL * cw * chh;
+        off += g.n_nodes;
+    }
+    h->n_rings = n_rings;
+    h->n_total = off;
+    h->row_len = 6 + 4 * n_rings;
+    h->box_floats = box_off;
+    if (n_rings > 0) {
+        CK(h, cudaMalloc(&h->rings, sizeof(RingDev) * n_rings));
+        CK(h, cudaMalloc(&h->X, sizeof(double2) * off));
+        CK(h, cudaMalloc(&h->node_cell, sizeof(int2) * off));
+        CK(h, cudaMalloc(&h->node_frac, sizeof(float2) * off));
+        CK(h, cudaMalloc(&h->node_force, sizeof(float2) * off));
+        CK(h, cudaMalloc(&h->ubox, sizeof(float) * box_off));
+        CK(h, cudaMalloc(&h->fpbox, sizeof(float) * box_off));
+        CK(h, cudaMemcpy(h->rings, rd.data(), sizeof(RingDev) * n_rings, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->X, X.data(), sizeof(double2) * off, cudaMemcpyHostToDevice));
+        CK(h, cudaMemset(h->ubox, 0, sizeof(float) * box_off));
+        CK(h, cudaMemset(h->fpbox, 0, sizeof(float) * box_off));
+    }
+    dfree(h->series);
+    CK(h, cudaMalloc(&h->series, sizeof(double) * (size_t)h->series_cap * h->row_len));
+    CK(h, cudaMemset(h->series, 0, sizeof(double) * (size_t)h->series_cap * h->row_len));
+    if (n_rings > 0) {
+        CK(h, launch_nodes(node_args(h, 0), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return LB_OK;
+}
+
+int lb_step(lb_handle* h, int64_t n)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (n < 0) return fail(h, LB_EINVAL, "n < 0");
+    if (!h->fields_ready) return fail(h, LB_ESTATE, "lb_init_fields not called");
+    for (int64_t k = 0; k < n; ++k) {
+        FusedArgs fa = fused_args(h);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->timing) {
+            e0 = ev_get(h->ev_fused, h->ev_fused_used);
+            e1 = ev_get(h->ev_fused, h->ev_fused_used);
+            if (e0) cudaEventRecord(e0, h->stream);
+        }
+        CK(h, launch_fused(fa, MODE_STEP, h->stream, nullptr));
+        if (h->timing && e1) cudaEventRecord(e1, h->stream);
+        if (h->timing) {
+            e0 = ev_get(h->ev_nodes, h->ev_nodes_used);
+            e1 = ev_get(h->ev_nodes, h->ev_nodes_used);
+            if (e0) cudaEventRecord(e0, h->stream);
+        }
+        CK(h, launch_nodes(node_args(h, 1), h->stream));
+        if (h->timing && e1) cudaEventRecord(e1, h->stream);
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LB_OK;
+}
+
+int lb_sync(lb_handle* h)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    Ctl c;
+    CK(h, cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.err_nonfinite || c.err_body) {
+        int z[3] = {0, 0, 0};
+        CK(h, cudaMemcpy(&h->ctl->err_nonfinite, z, sizeof(int) * 3, cudaMemcpyHostToDevice));
+        if (c.err_nonfinite) return fail(h, LB_ENONFINITE, "non-finite readout or node force");
+        return fail(h, LB_EBODY, "a ring left its work box or moved >= 1 cell in a step");
+    }
+    if (c.t != h->t) return fail(h, LB_ECUDA, "device step counter %lld != host %lld", c.t, h->t);
+    return LB_OK;
+}
+
+int64_t lb_time(const lb_handle* h) { return h ? h->t : -1; }
+
+int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst_is_device)
+{
+    if (!h || !dst) return fail(h, LB_EINVAL, "null argument");
+    const size_t N = (size_t)h->plane;
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (field == LB_FIELD_NODES) {
+        if (bytes != sizeof(double) * 2 * (size_t)h->n_total) return fail(h, LB_EINVAL, "bytes mismatch");
+        if (h->n_total) CK(h, cudaMemcpyAsync(dst, h->X, bytes, kind, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return LB_OK;
+    }
+    if (bytes != sizeof(float) * N) return fail(h, LB_EINVAL, "bytes mismatch");
+    const float* srcp = nullptr;
+    if (field >= LB_FIELD_DRHO && field <= LB_FIELD_UY) {
+        if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
+        FusedArgs fa = fused_args(h);
+        CK(h, launch_fused(fa, MODE_MOMENTS, h->stream, nullptr));
+        srcp = h->moments + (size_t)(field - LB_FIELD_DRHO) * N;
+    } else if (field >= LB_FIELD_SXX && field <= LB_FIELD_PY) {
+        srcp = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
+    } else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) {
+        srcp = h->state[h->cur] + (size_t)(field - LB_FIELD_POP0) * N;
+    } else {
+        return fail(h, LB_EINVAL, "unknown field %d", field);
+    }
+    CK(h, cudaMemcpyAsync(dst, srcp, bytes, kind, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, int32_t src_is_device)
+{
+    if (!h || !src) return fail(h, LB_EINVAL, "null argument");
+    const size_t N = (size_t)h->plane;
+    if (bytes != sizeof(float) * N) return fail(h, LB_EINVAL, "bytes mismatch");
+    size_t plane;
+    if (field >= LB_FIELD_SXX && field <= LB_FIELD_PY) plane = PL_SXX + field - LB_FIELD_SXX;
+    else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) plane = field - LB_FIELD_POP0;
+    else return fail(h, LB_EINVAL, "field %d is not writable", field);
+    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(h, cudaMemcpyAsync(h->state[h->cur] + plane * N, src, bytes, kind, h->stream));
+    if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int32_t lb_series_row_len(const lb_handle* h) { return h ? h->row_len : 0; }
+
+static int series_rows(const lb_handle* h)
+{
+    const long long every = h->p.readout_every;
+    const long long recorded = (h->t + every - 1) / every;   // t' in [0, t) with t' % every == 0
+    return (int)std::min<long long>(recorded, h->series_cap);
+}
+
+int lb_series(lb_handle* h, double* dst, int32_t max_rows, int32_t* rows_written)
+{
+    if (!h || !dst || max_rows < 0) return fail(h, LB_EINVAL, "bad argument");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const long long every = h->p.readout_every;
+    const long long recorded = (h->t + every - 1) / every;
+    const int rows = std::min(series_rows(h), max_rows);
+    std::vector<double> all((size_t)h->series_cap * h->row_len);
+    CK(h, cudaMemcpy(all.data(), h->series, sizeof(double) * all.size(), cudaMemcpyDeviceToHost));
+    const long long first = recorded - series_rows(h);      // oldest sample index kept
+    for (int r = 0; r < rows; ++r) {
+        const long long k = first + r;
+        memcpy(dst + (size_t)r * h->row_len, all.data() + (size_t)(k % h->series_cap) * h->row_len,
+               sizeof(double) * h->row_len);
+    }
+    if (rows_written) *rows_written = rows;
+    return LB_OK;
+}
+
+int lb_restoring_force(lb_handle* h, int32_t ring, double* dst, int32_t max_k, int32_t* k_written)
+{
+    if (!h || !dst || ring < 0 || ring >= h->n_rings) return fail(h, LB_EINVAL, "bad argument");
+    std::vector<double> rows((size_t)std::max(series_rows(h), 1) * h->row_len);
+    int n = 0;
+    int rc = lb_series(h, rows.data(), series_rows(h), &n);
+    if (rc) return rc;
+    const int k = std::min(n, max_k);
+    for (int i = 0; i < k; ++i) {
+        dst[2 * i] = rows[(size_t)i * h->row_len + 6 + 4 * ring];
+        dst[2 * i + 1] = rows[(size_t)i * h->row_len + 7 + 4 * ring];
+    }
+    if (k_written) *k_written = k;
+    return LB_OK;
+}
+
+int lb_timing(lb_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->timing = enable != 0;
+    h->ev_fused_used = h->ev_nodes_used = 0;
+    return LB_OK;
+}
+
+int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, double* node_ms,
+                   int64_t* node_launches)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    CK(h, cudaStreamSynchronize(h->stream));
+    double tf = 0.0, tn = 0.0;
+    for (size_t i = 0; i + 1 < h->ev_fused_used; i += 2) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev_fused[i], h->ev_fused[i + 1]));
+        tf += ms;
+    }
+    for (size_t i = 0; i + 1 < h->ev_nodes_used; i += 2) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev_nodes[i], h->ev_nodes[i + 1]));
+        tn += ms;
+    }
+    if (fused_ms) *fused_ms = tf;
+    if (fused_launches) *fused_launches = (int64_t)(h->ev_fused_used / 2);
+    if (node_ms) *node_ms = tn;
+    if (node_launches) *node_launches = (int64_t)(h->ev_nodes_used / 2);
+    return LB_OK;
+}
+
+int32_t lb_launches_per_step(const lb_handle* h) { return h ? 2 : 0; }
+
+double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * sizeof(float) : 0.0; }
+
+const char* lb_last_error(const lb_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+void lb_destroy(lb_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    free_rings(h);
+    dfree(h->state[0]);
+    dfree(h->state[1]);
+    dfree(h->lut);
+    dfree(h->ctl);
+    dfree(h->partials);
+    dfree(h->series);
+    dfree(h->moments);
+    for (auto e : h->ev_fused) cudaEventDestroy(e);
+    for (auto e : h->ev_nodes) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // extern "C"

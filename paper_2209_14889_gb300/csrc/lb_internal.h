@@ -1,0 +1,102 @@
+// lb_internal.h -- device-side data layout and kernel launchers shared by the CUDA sources of
+// the solver (not part of the public C ABI; see include/lb.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vlb {
+
+// Plane order of the stored state: 9 shifted populations d_n = h_n - w_n rho0, then
+// sigma^p (xx, yy, xy), then P (x, y).  Each plane is nx*ny FP32, x fastest.
+enum { PL_POP = 0, PL_SXX = 9, PL_SYY = 10, PL_SXY = 11, PL_PX = 12, PL_PY = 13, N_PLANES = 14 };
+
+// C~(P) table: a2(q) = r2/q and a4(q) = r4/q^2 with q = |P|^2, r_n = I_n(k)/I_0(k), k = k(|P|)
+// (Eq. Pk), sampled at LUT_N + 1 uniform points of q in [0, q_cap], q_cap = P_cap^2;
+// interpolated by 4-point Lagrange polynomials.  Beyond q_cap: a2 = a2(q_cap) q_cap/q,
+// a4 = a4(q_cap) (q_cap/q)^2 (k is fixed at the cap, theta_P still follows P).
+constexpr int LUT_N = 256;
+
+// Per-ring device record.
+struct RingDev {
+    int n_nodes, node_off;        // nodes [node_off, node_off + n_nodes)
+    double k_spring, eps_angle, l_eq, pull_x, pull_y;   // pull per node = pull / n_nodes
+    int box_x0, box_y0, box_w, box_h;  // work box of the current step (wrapped origin)
+    int cap_w, cap_h;             // capacity of the box buffers
+    long long box_off;            // offset (floats) of this ring's boxes in the box buffers
+};
+
+// Physical constants of the lattice kernel, FP32.
+struct Phys {
+    float omega;        // 1 / tau
+    float guo;          // 1 - 1/(2 tau)
+    float rho0;
+    float alpha, beta, xi, Gamma, kappa, Dp, inv_eta;
+    float kS8;          // (3K1111 + 2K1122 + 4K1212 + 3K2222) / 8
+    float kC12;         // (K1111 + 6K1122 - 4K1212 + K2222) / 8
+    float kC33;         // (K1111 - 2K1122 + 4K1212 + K2222) / 4
+    float dK;           // K1111 - K2222
+    float kX;           // K1111 - 2K1122 - 4K1212 + K2222
+    float q_cap;
+    float lut_scale;    // LUT_N / q_cap
+    int ericksen;
+};
+
+// Control block on the device.
+struct Ctl {
+    long long t;                 // step counter
+    unsigned int ticket;         // CTA arrival counter of the node kernel
+    int err_nonfinite;
+    int err_body;
+    int err_cfl;
+};
+
+struct FusedArgs {
+    const float* src;            // state at t (N_PLANES planes)
+    float* dst;                  // state at t + 1
+    long long plane;             // nx * ny
+    int nx, ny;
+    Phys ph;
+    const float2* lut;           // LUT_N + 1 entries (a2, a4)
+    int n_rings;
+    const RingDev* rings;
+    const int2* node_cell;       // grid view of the nodes: cell, fraction, force (FP32)
+    const float2* node_frac;
+    const float2* node_force;
+    float* ubox;                 // u(t) on each ring's box (written)
+    float* fpbox;                // f^p(t) on each ring's box (written on readout steps)
+    double* partials;            // per-CTA readout sums (5 per CTA)
+    const Ctl* ctl;
+    int every;                   // readout period
+    float* moments_out;          // MOMENTS mode: drho, ux, uy planes
+};
+
+struct NodeArgs {
+    int n_rings;
+    RingDev* rings;
+    double2* X;                  // FP64 master node positions, wrapped into [0, n)
+    int2* node_cell;
+    float2* node_frac;
+    float2* node_force;
+    const float* ubox;
+    const float* fpbox;
+    const double* partials;
+    int n_partials;
+    double* series;              // [cap][row_len]
+    int series_cap, row_len;
+    Ctl* ctl;
+    int every;
+    int nx, ny;
+    int advance;                 // 0: forces + box only (initial configuration)
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas);
+cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s);
+int fused_ctas(int nx, int ny);
+
+enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
+
+// Host-side table builder (FP64): fills lut[2*(LUT_N+1)] with (a2, a4) pairs.
+void build_lut(double P_cap, float* lut);
+
+}  // namespace vlb

@@ -1,0 +1,241 @@
+"""Python binding of the C ABI in include/lb.h (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of libvlb.so; this module only converts
+arguments, allocates readout tensors with torch and passes torch's current CUDA stream.  There
+is no CPU fallback: importing the binding fails if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EUNSTABLE, LB_EBODY, LB_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+LB_FP32 = 0
+FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
+LB_FIELD_POP0 = 8
+LB_FIELD_NODES = 17
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("K1111", ctypes.c_double), ("K1122", ctypes.c_double),
+                ("K2222", ctypes.c_double), ("K1212", ctypes.c_double),
+                ("eta_p", ctypes.c_double), ("lambda_steps", ctypes.c_double),
+                ("Dp", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("xi", ctypes.c_double),
+                ("Gamma", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("P_cap", ctypes.c_double), ("director_angle", ctypes.c_double),
+                ("ericksen", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32)]
+
+
+class lb_ring(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("k_spring", ctypes.c_double), ("eps_angle", ctypes.c_double),
+                ("l_eq", ctypes.c_double), ("pull_force", ctypes.c_double),
+                ("pull_angle", ctypes.c_double)]
+
+
+_lib = None
+_H = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libvlb.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libvlb.so not built: run __graft_entry__.build() (needs nvcc)")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, sz, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, \
+            ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "lb_create": (ctypes.c_int, [ctypes.POINTER(lb_params), vp, ctypes.POINTER(_H)]),
+            "lb_init_fields": (ctypes.c_int, [_H, vp]),
+            "lb_set_body": (ctypes.c_int, [_H, i32, ctypes.POINTER(lb_ring), vp]),
+            "lb_step": (ctypes.c_int, [_H, i64]),
+            "lb_sync": (ctypes.c_int, [_H]),
+            "lb_time": (i64, [_H]),
+            "lb_readout": (ctypes.c_int, [_H, i32, vp, sz, i32]),
+            "lb_write_field": (ctypes.c_int, [_H, i32, vp, sz, i32]),
+            "lb_series": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
+            "lb_series_row_len": (i32, [_H]),
+            "lb_restoring_force": (ctypes.c_int, [_H, i32, vp, i32, ctypes.POINTER(i32)]),
+            "lb_timing": (ctypes.c_int, [_H, i32]),
+            "lb_kernel_time": (ctypes.c_int, [_H, dp, ctypes.POINTER(i64), dp,
+                                              ctypes.POINTER(i64)]),
+            "lb_launches_per_step": (i32, [_H]),
+            "lb_bytes_per_cell": (ctypes.c_double, [_H]),
+            "lb_last_error": (ctypes.c_char_p, [_H]),
+            "lb_destroy": (None, [_H]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(h, rc):
+    if rc != LB_OK:
+        raise LBError(rc, lib().lb_last_error(h).decode())
+
+
+def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4096) -> lb_params:
+    K = w["K"]
+    return lb_params(nx=w["nx"], ny=w["ny"], tau=w["tau"], rho0=w["rho0"], K1111=K[0],
+                     K1122=K[1], K2222=K[2], K1212=K[3], eta_p=w.get("eta_p", 0.0) or 0.0,
+                     lambda_steps=w.get("lambda_steps", 0.0), Dp=w["Dp"], alpha=w["alpha"],
+                     beta=w["beta"], xi=w["xi"], Gamma=w["Gamma"], kappa=w["kappa"],
+                     P_cap=w.get("P_cap", 0.99), director_angle=w["director_angle"],
+                     ericksen=w.get("ericksen", 1), precision=precision,
+                     readout_every=w.get("every", 10), max_samples=max_samples)
+
+
+class Solver:
+    """One lattice with its rings, driven through the C ABI."""
+
+    def __init__(self, params: lb_params, stream=None):
+        import torch
+        self._torch = torch
+        L = lib()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.params = params
+        self.h = _H()
+        rc = L.lb_create(ctypes.byref(params), ctypes.c_void_p(stream.cuda_stream),
+                         ctypes.byref(self.h))
+        if rc != LB_OK:
+            raise LBError(rc, L.lb_last_error(None).decode())
+        self.nx, self.ny = params.nx, params.ny
+        self.n_rings = 0
+        self.n_total = 0
+
+    @staticmethod
+    def from_workload(w: dict, **kw) -> "Solver":
+        s = Solver(params_from_workload(w, **kw))
+        s.init_fields(w.get("noise"))
+        if w["rings"]:
+            s.set_body(w["rings"])
+        return s
+
+    def close(self):
+        if self.h:
+            lib().lb_destroy(self.h)
+            self.h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, noise=None):
+        if noise is not None:
+            noise = np.ascontiguousarray(noise, dtype=np.float64)
+            assert noise.shape == (2, self.ny, self.nx)
+        _check(self.h, lib().lb_init_fields(self.h, None if noise is None else noise.ctypes.data))
+
+    def set_body(self, rings):
+        arr = (lb_ring * max(1, len(rings)))()
+        xy = []
+        for i, r in enumerate(rings):
+            arr[i] = lb_ring(n_nodes=len(r["X"]), pad_=0, k_spring=r["k_spring"],
+                             eps_angle=r["eps_angle"], l_eq=r["l_eq"],
+                             pull_force=r["pull_force"], pull_angle=r["pull_angle"])
+            xy.append(np.asarray(r["X"], dtype=np.float64))
+        X = np.ascontiguousarray(np.concatenate(xy) if xy else np.zeros((0, 2)))
+        _check(self.h, lib().lb_set_body(self.h, len(rings), arr, X.ctypes.data if X.size else None))
+        self.n_rings = len(rings)
+        self.n_total = X.shape[0]
+
+    def step(self, n: int = 1):
+        _check(self.h, lib().lb_step(self.h, int(n)))
+
+    def sync(self):
+        _check(self.h, lib().lb_sync(self.h))
+
+    @property
+    def t(self) -> int:
+        return lib().lb_time(self.h)
+
+    def readout(self, name: str, device: bool = True):
+        """A field of the current state: torch FP32 [ny, nx] on the GPU (device=True) or numpy."""
+        torch = self._torch
+        fid = FIELDS[name] if name in FIELDS else LB_FIELD_POP0 + int(name[3:])
+        if device:
+            out = torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
+            _check(self.h, lib().lb_readout(self.h, fid, ctypes.c_void_p(out.data_ptr()),
+                                            out.numel() * 4, 1))
+            return out
+        out = np.empty((self.ny, self.nx), dtype=np.float32)
+        _check(self.h, lib().lb_readout(self.h, fid, out.ctypes.data, out.nbytes, 0))
+        return out
+
+    def fields(self) -> dict:
+        return {k: self.readout(k, device=False).astype(np.float64) for k in FIELDS}
+
+    def nodes(self) -> np.ndarray:
+        out = np.empty((self.n_total, 2), dtype=np.float64)
+        _check(self.h, lib().lb_readout(self.h, LB_FIELD_NODES, out.ctypes.data if out.size else
+                                        ctypes.c_void_p(1), out.nbytes, 0))
+        return out
+
+    def write_field(self, name: str, data):
+        fid = FIELDS[name] if name in FIELDS else LB_FIELD_POP0 + int(name[3:])
+        torch = self._torch
+        if isinstance(data, torch.Tensor):
+            assert data.dtype == torch.float32 and data.is_contiguous()
+            _check(self.h, lib().lb_write_field(self.h, fid, ctypes.c_void_p(data.data_ptr()),
+                                                data.numel() * 4, 1 if data.is_cuda else 0))
+        else:
+            a = np.ascontiguousarray(data, dtype=np.float32)
+            _check(self.h, lib().lb_write_field(self.h, fid, a.ctypes.data, a.nbytes, 0))
+
+    def series(self) -> np.ndarray:
+        L = lib()
+        rl = L.lb_series_row_len(self.h)
+        cap = self.params.max_samples
+        buf = np.zeros((cap, rl))
+        n = ctypes.c_int32(0)
+        _check(self.h, L.lb_series(self.h, buf.ctypes.data, cap, ctypes.byref(n)))
+        return buf[:n.value].copy()
+
+    def timing(self, enable: bool):
+        _check(self.h, lib().lb_timing(self.h, 1 if enable else 0))
+
+    def kernel_time(self):
+        f, n = ctypes.c_double(), ctypes.c_int64()
+        g, m = ctypes.c_double(), ctypes.c_int64()
+        _check(self.h, lib().lb_kernel_time(self.h, ctypes.byref(f), ctypes.byref(n),
+                                            ctypes.byref(g), ctypes.byref(m)))
+        return {"fused_ms": f.value, "fused_launches": n.value, "node_ms": g.value,
+                "node_launches": m.value}
+
+    @property
+    def bytes_per_cell(self) -> float:
+        return lib().lb_bytes_per_cell(self.h)
+
+    @property
+    def launches_per_step(self) -> int:
+        return lib().lb_launches_per_step(self.h)

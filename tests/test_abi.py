@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol include/lb.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libvlb():
+    from paper_2209_14889_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(libvlb):
+    names = declared("lb.h")
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(libvlb, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    from paper_2209_14889_gb300 import lb
+    L = lb.lib()
+    for n in declared("lb.h"):
+        assert hasattr(L, n)
+
+
+def test_struct_layout_matches_header():
+    # lb_params: 2 int32, 16 doubles, 4 int32 ; lb_ring: 2 int32 + 5 doubles
+    from paper_2209_14889_gb300 import lb
+    assert ctypes.sizeof(lb.lb_params) == 8 + 16 * 8 + 16
+    assert ctypes.sizeof(lb.lb_ring) == 8 + 5 * 8
+
+
+def test_create_without_gpu_fails_cleanly():
+    # No compute call is made: with no device, lb_create must return an error code, not crash.
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2209_14889_gb300 import lb
+    L = lb.lib()
+    p = lb.lb_params(nx=16, ny=16, tau=0.8, rho0=1.0, K1111=2e-3, K1122=1e-3, K2222=1e-3,
+                     K1212=1e-3, eta_p=0.1, lambda_steps=0.0, Dp=0.05, alpha=-0.9, beta=1.0,
+                     xi=1.1, Gamma=1.0, kappa=1e-3, P_cap=0.99, director_angle=0.0, ericksen=1,
+                     precision=0, readout_every=10, max_samples=16)
+    h = ctypes.c_void_p()
+    rc = L.lb_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc in (lb.LB_ECUDA, lb.LB_ENOMEM)
+    assert not h.value
+
+
+def test_parameter_validation_without_gpu():
+    from paper_2209_14889_gb300 import lb
+    L = lb.lib()
+    base = dict(nx=16, ny=16, tau=0.8, rho0=1.0, K1111=2e-3, K1122=1e-3, K2222=1e-3,
+                K1212=1e-3, eta_p=0.1, lambda_steps=0.0, Dp=0.05, alpha=-0.9, beta=1.0, xi=1.1,
+                Gamma=1.0, kappa=1e-3, P_cap=0.99, director_angle=0.0, ericksen=1, precision=0,
+                readout_every=10, max_samples=16)
+    for bad, code in [(dict(nx=4), lb.LB_EINVAL), (dict(tau=0.5), lb.LB_EINVAL),
+                      (dict(Dp=0.3), lb.LB_EUNSTABLE), (dict(alpha=-1.5), lb.LB_EUNSTABLE),
+                      (dict(precision=7), lb.LB_EINVAL), (dict(eta_p=0.0), lb.LB_EINVAL)]:
+        kw = dict(base)
+        kw.update(bad)
+        h = ctypes.c_void_p()
+        rc = L.lb_create(ctypes.byref(lb.lb_params(**kw)), None, ctypes.byref(h))
+        assert rc == code, (bad, rc)
+        assert L.lb_last_error(None)

@@ -1,0 +1,180 @@
+"""GPU (CUDA, FP32) vs FP64 oracle parity of the fused IB-LB step, through the C ABI.
+
+Tolerances (the target of the fused FP32 step): relative L2 <= 1e-5 on every field
+(rho - rho0, u, sigma^p, P) and <= 1e-4 on the restoring-force series after 2000 steps of the
+64^2 workload; the same bounds on shorter runs, ragged and tiny lattices and the degenerate
+cases.  Node positions are compared through their minimum-image difference.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2209_14889_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+FREST_TOL = 1e-4
+_cache = {}
+
+
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_14889_gb300 import lb
+    return lb
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def run_both(w, steps, key=None):
+    lb = _gpu()
+    if key is not None and key in _cache:
+        ref = _cache[key]
+    else:
+        sim = O.Sim.from_workload(w)
+        sim.step(steps, every=w.get("every", 10))
+        ref = dict(fields=sim.fields(), series=np.array(sim.series), X=sim.X.copy())
+        if key is not None:
+            _cache[key] = ref
+    s = lb.Solver.from_workload(w)
+    s.step(steps)
+    s.sync()
+    got = dict(fields=s.fields(), series=s.series(), X=s.nodes())
+    s.close()
+    return got, ref
+
+
+def check_fields(got, ref, tol=FIELD_TOL):
+    errs = {k: rel_l2(got["fields"][k], ref["fields"][k]) for k in ref["fields"]}
+    bad = {k: e for k, e in errs.items() if not e <= tol}
+    assert not bad, "field errors above %g: %s (all: %s)" % (tol, bad, errs)
+    return errs
+
+
+def check_nodes(got, ref, w, tol=1e-5):
+    if not ref["X"].size:
+        return
+    d = got["X"] - ref["X"]
+    d[:, 0] -= w["nx"] * np.round(d[:, 0] / w["nx"])
+    d[:, 1] -= w["ny"] * np.round(d[:, 1] / w["ny"])
+    assert np.abs(d).max() < tol, np.abs(d).max()
+
+
+def check_series(got, ref, n_rings, tol=FREST_TOL):
+    gs, rs = got["series"], ref["series"]
+    assert gs.shape == rs.shape, (gs.shape, rs.shape)
+    assert np.array_equal(gs[:, 0], rs[:, 0])
+    for r in range(n_rings):
+        fr_g = gs[:, 6 + 4 * r: 8 + 4 * r]
+        fr_r = rs[:, 6 + 4 * r: 8 + 4 * r]
+        if np.linalg.norm(fr_r) > 0:
+            assert rel_l2(fr_g, fr_r) <= tol, rel_l2(fr_g, fr_r)
+    # total force and momentum
+    assert np.abs(gs[:, 4:6] - rs[:, 4:6]).max() <= 1e-6 * max(1e-3, np.abs(rs[:, 4:6]).max())
+
+
+def test_cfg1_one_step():
+    w = W.cfg1()
+    got, ref = run_both(w, 1)
+    errs = check_fields(got, ref, tol=1e-6)
+    check_nodes(got, ref, w, tol=1e-9)
+    print(errs)
+
+
+def test_cfg1_50_steps():
+    w = W.cfg1()
+    got, ref = run_both(w, 50)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+def test_cfg1_full_2000_steps():
+    """The 64^2 workload for its full 2000 steps, restoring force every 10 steps."""
+    w = W.cfg1()
+    got, ref = run_both(w, 2000, key="cfg1_2000")
+    errs = check_fields(got, ref)
+    check_series(got, ref, 1)
+    check_nodes(got, ref, w, tol=1e-4)
+    assert got["series"].shape[0] == 200
+    print(errs)
+
+
+def test_ragged_lattice_ring_across_seam():
+    # 50 x 37: ragged tail of tiles in x and y; the ring straddles the periodic corner
+    w = W.small(50, 37, n_nodes=40, radius=6.0, centre=(2.3, 35.6), steps=120)
+    got, ref = run_both(w, 120)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+def test_small_lattice_wraps_inside_tile():
+    # 40 x 24: the staged halo regions wrap onto themselves
+    w = W.small(40, 24, n_nodes=16, radius=3.5, steps=80)
+    got, ref = run_both(w, 80)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+def test_no_ring_isotropic_degenerate():
+    # no body, alpha = 0 (P_eq = 0: P is noise around zero, k -> 0), no Ericksen force, no
+    # stress diffusion, kappa = 0
+    w = W.make(48, 40, rings=[], seed=5, alpha=0.0, ericksen=0, Dp=0.0, kappa=0.0, steps=60)
+    got, ref = run_both(w, 60)
+    check_fields(got, ref)
+    assert got["series"].shape == ref["series"].shape
+
+
+def test_P_beyond_cap_and_zero():
+    # noise of amplitude 0.2 around P_eq = 0.949 drives |P| above the 0.99 cap in places
+    w = W.small(64, 48, n_nodes=24, radius=5.0, noise_amp=0.2, steps=40)
+    got, ref = run_both(w, 40)
+    check_fields(got, ref)
+
+
+def test_invariants_on_gpu():
+    lb = _gpu()
+    w = W.small(64, 64, steps=0)
+    s = lb.Solver.from_workload(w)
+    s.step(101)
+    s.sync()
+    ser = s.series()
+    s.close()
+    N = 64 * 64
+    assert np.abs(ser[:, 1]).max() < 1e-3 * 1e-7 * N * 10         # mass: FP32 rounding only
+    pull = 1e-3 * np.array([math.cos(0.3), math.sin(0.3)])
+    assert np.abs(ser[:, 4:6] - pull).max() < 2e-6 * 1e-3 * N ** 0.5
+    dm = np.diff(ser[:, 2:4], axis=0) / 10.0
+    assert np.abs(dm - pull).max() < 1e-3 * 1e-3
+
+
+def test_bitwise_deterministic():
+    lb = _gpu()
+    w = W.small(64, 48, steps=0)
+    out = []
+    for _ in range(2):
+        s = lb.Solver.from_workload(w)
+        s.step(30)
+        s.sync()
+        out.append((s.readout("sxy", device=False), s.readout("ux", device=False), s.series(),
+                    s.nodes()))
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_cfg2_full_size_few_steps():
+    """The 1024^2 workload (ring of 256 nodes, pull at 30 degrees) for 3 steps, every field."""
+    w = W.cfg2()
+    got, ref = run_both(w, 3)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
