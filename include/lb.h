@@ -100,8 +100,8 @@ int lb_init_fields(lb_handle* h, const double* noise);
 /*
  * Immersed rings (App. A).  xy: host FP64 positions [n_total][2], ring after ring, in lattice
  * coordinates (cell (i, j) sits at (i, j)); copied.  Replaces any previous rings and computes
- * the forces of the initial configuration.  Each ring must fit in a box of
- * min(nx, ny) - 8 cells.
+ * the forces of the initial configuration.  Each ring, widened by 8 cells, must span at most
+ * half the lattice in x and in y (else LB_EINVAL).
  */
 int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const double* xy);
 

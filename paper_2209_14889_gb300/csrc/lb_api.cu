@@ -153,6 +153,19 @@ NodeArgs node_args(lb_handle* h, int advance)
     return a;
 }
 
+// dst = src + c (the stored polarisation is dP = P - P_ref)
+__global__ void k_shift(float* dst, const float* src, float c, long long n)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] + c;
+}
+
+cudaError_t shift(float* dst, const float* src, float c, long long n, cudaStream_t s)
+{
+    k_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, src, c, n);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -198,6 +211,13 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     ph.kappa = (float)p.kappa;
     ph.Dp = (float)p.Dp;
     ph.inv_eta = (float)(1.0 / eta);
+    {
+        const double Peq = (p.alpha < 0.0 && p.beta > 0.0) ? std::sqrt(-p.alpha / p.beta) : 0.0;
+        ph.prx = (float)(Peq * std::cos(p.director_angle));
+        ph.pry = (float)(Peq * std::sin(p.director_angle));
+        const double rx = ph.prx, ry = ph.pry;
+        ph.A0 = (float)(p.alpha + p.beta * (rx * rx + ry * ry));
+    }
     ph.kS8 = (float)S8;
     ph.kC12 = (float)((p.K1111 + 6 * p.K1122 - 4 * p.K1212 + p.K2222) / 8.0);
     ph.kC33 = (float)((p.K1111 - 2 * p.K1122 + 4 * p.K1212 + p.K2222) / 4.0);
@@ -250,10 +270,12 @@ int lb_init_fields(lb_handle* h, const double* noise)
     float* S = h->state[h->cur];
     // populations at rest (shifted form: zero) and sigma = 0
     CK(h, cudaMemsetAsync(S, 0, sizeof(float) * (PL_PY + 1) * N, h->stream));
+    // stored: dP = P - P_ref with P = P_eq (cos theta_d, sin theta_d) + noise (FP64 here)
     const double Peq = (p.alpha < 0.0 && p.beta > 0.0) ? std::sqrt(-p.alpha / p.beta) : 0.0;
     for (int c = 0; c < 2; ++c) {
         const double base = Peq * (c == 0 ? std::cos(p.director_angle) : std::sin(p.director_angle));
-        for (size_t i = 0; i < N; ++i) buf[i] = (float)(base + (noise ? noise[c * N + i] : 0.0));
+        const double ref = c == 0 ? h->ph.prx : h->ph.pry;
+        for (size_t i = 0; i < N; ++i) buf[i] = (float)((base - ref) + (noise ? noise[c * N + i] : 0.0));
         CK(h, cudaMemcpyAsync(S + (PL_PX + c) * N, buf.data(), sizeof(float) * N, cudaMemcpyHostToDevice,
                               h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -295,9 +317,11 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
             X.push_back(make_double2(xw, yw));
         }
         // box capacity: the initial extent + supports + a margin for motion and deformation
+        // positions relative to node 0 are taken as minimum images: the ring (with the
+        // supports of its nodes) must span less than half the lattice
         const int lim = std::min(nx, ny) - 8;
         int cw = (int)std::ceil(mxx - mnx) + 8, chh = (int)std::ceil(mxy - mny) + 8;
-        if (cw > lim || chh > lim) return fail(h, LB_EINVAL, "ring %d does not fit the lattice", r);
+        if (2 * cw > nx || 2 * chh > ny) return fail(h, LB_EINVAL, "ring %d does not fit the lattice", r);
         cw = std::min(cw + 2 * std::max(16, cw / 2), lim);
         chh = std::min(chh + 2 * std::max(16, chh / 2), lim);
         RingDev& d = rd[r];
@@ -407,7 +431,12 @@ int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst
         FusedArgs fa = fused_args(h);
         CK(h, launch_fused(fa, MODE_MOMENTS, h->stream, nullptr));
         srcp = h->moments + (size_t)(field - LB_FIELD_DRHO) * N;
-    } else if (field >= LB_FIELD_SXX && field <= LB_FIELD_PY) {
+    } else if (field == LB_FIELD_PX || field == LB_FIELD_PY) {
+        if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
+        const float* st = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
+        CK(h, shift(h->moments, st, field == LB_FIELD_PX ? h->ph.prx : h->ph.pry, (long long)N, h->stream));
+        srcp = h->moments;
+    } else if (field >= LB_FIELD_SXX && field <= LB_FIELD_SXY) {
         srcp = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
     } else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) {
         srcp = h->state[h->cur] + (size_t)(field - LB_FIELD_POP0) * N;
@@ -429,7 +458,10 @@ int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, i
     else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) plane = field - LB_FIELD_POP0;
     else return fail(h, LB_EINVAL, "field %d is not writable", field);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(h, cudaMemcpyAsync(h->state[h->cur] + plane * N, src, bytes, kind, h->stream));
+    float* dstp = h->state[h->cur] + plane * N;
+    CK(h, cudaMemcpyAsync(dstp, src, bytes, kind, h->stream));
+    if (plane == PL_PX || plane == PL_PY)
+        CK(h, shift(dstp, dstp, plane == PL_PX ? -h->ph.prx : -h->ph.pry, (long long)N, h->stream));
     if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }

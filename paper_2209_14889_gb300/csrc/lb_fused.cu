@@ -111,16 +111,26 @@ __device__ __forceinline__ St st_at(const float* base, int W, int lx, int ly)
     return St{p[0], p[1], p[-1], p[W], p[-W]};
 }
 
+// Molecular field h = (alpha + beta |P|^2) P - kappa lap P (Eq. Ffunctional) from the stencil
+// of dP = P - P_ref: alpha + beta |P|^2 = A0 + beta (2 P_ref.dP + |dP|^2) has no cancellation.
+__device__ __forceinline__ void molecular(const Phys& ph, const St& dx, const St& dy, float& hx,
+                                          float& hy)
+{
+    const float A = ph.A0 + ph.beta * (2.f * (ph.prx * dx.c + ph.pry * dy.c) + (dx.c * dx.c + dy.c * dy.c));
+    hx = A * (ph.prx + dx.c) - ph.kappa * (dx.e + dx.w + dx.n + dx.s - 4.f * dx.c);
+    hy = A * (ph.pry + dy.c) - ph.kappa * (dy.e + dy.w + dy.n + dy.s - 4.f * dy.c);
+}
+
 // Right-hand sides of Eq. StiffCons (with the Jaumann derivative) and Eq. BE at one cell, for
-// the frozen u, Psi = (pxx, pyy, pxy), omega = Omega_xy; s = sigma (xx, yy, xy), p = P (x, y).
+// the frozen u, Psi = (pxx, pyy, pxy), omega = Omega_xy; s = sigma (xx, yy, xy), p = dP (x, y).
 __device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, float ux, float uy,
                                          float pxx, float pyy, float pxy, float om,
                                          const St& s0, const St& s1, const St& s2,
                                          const St& p0, const St& p1, float hx, float hy,
                                          float* r)
 {
-    // stiffness C~(P) (App. B) from the table of a2, a4 and polynomials in P
-    const float Px = p0.c, Py = p1.c;
+    // stiffness C~(P) (App. B) from the table of a2, a4 and polynomials in P = P_ref + dP
+    const float Px = ph.prx + p0.c, Py = ph.pry + p1.c;
     const float q = Px * Px + Py * Py;
     float a2, a4;
     lut_eval(lut, ph, q, a2, a4);
@@ -234,23 +244,23 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     // ---- B: molecular field and Ericksen stress on the halo-3 region ------------------------
     for (int i = tid; i < R3; i += NT) {
         const int ly = i / R3W, lx = i - ly * R3W;
-        const St px = st_at(sP, R4W, lx + 1, ly + 1);
+        const St px = st_at(sP, R4W, lx + 1, ly + 1);         // dP stencils
         const St py = st_at(sP + R4, R4W, lx + 1, ly + 1);
-        const float A = ph.alpha + ph.beta * (px.c * px.c + py.c * py.c);
-        const float hx = A * px.c - ph.kappa * (px.e + px.w + px.n + px.s - 4.f * px.c);
-        const float hy = A * py.c - ph.kappa * (py.e + py.w + py.n + py.s - 4.f * py.c);
+        float hx, hy;
+        molecular(ph, px, py, hx, hy);
         sH[i] = hx;
         sH[R3 + i] = hy;
         if (ph.ericksen) {
+            const float Px = ph.prx + px.c, Py = ph.pry + py.c;
             const float gxPx = 0.5f * (px.e - px.w), gyPx = 0.5f * (px.n - px.s);
             const float gxPy = 0.5f * (py.e - py.w), gyPy = 0.5f * (py.n - py.s);
-            const float anti = px.c * hy - hx * py.c;
-            const float sym = px.c * hy + hx * py.c;
+            const float anti = Px * hy - hx * Py;
+            const float sym = Px * hy + hx * Py;
             const float cross = ph.kappa * (gxPx * gyPx + gxPy * gyPy);
-            sE[i] = ph.xi * px.c * hx - ph.kappa * (gxPx * gxPx + gxPy * gxPy);          // xx
+            sE[i] = ph.xi * Px * hx - ph.kappa * (gxPx * gxPx + gxPy * gxPy);            // xx
             sE[R3 + i] = -0.5f * anti + 0.5f * ph.xi * sym - cross;                       // xy
             sE[2 * R3 + i] = 0.5f * anti + 0.5f * ph.xi * sym - cross;                    // yx
-            sE[3 * R3 + i] = ph.xi * py.c * hy - ph.kappa * (gyPx * gyPx + gyPy * gyPy);  // yy
+            sE[3 * R3 + i] = ph.xi * Py * hy - ph.kappa * (gyPx * gyPx + gyPy * gyPy);    // yy
         }
     }
 
@@ -271,10 +281,13 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
                 const int2 c = a.node_cell[R.node_off + k];
                 fr = a.node_frac[R.node_off + k];
                 f = a.node_force[R.node_off + k];
-                cxr = mimg(c.x - (x0 - 2), nx);
-                cyr = mimg(c.y - (y0 - 2), ny);
-                // support cells c-1 .. c+2 meet the region [0, R2W) x [0, R2H)?
-                keep = small || (cxr >= -2 && cxr <= R2W && cyr >= -2 && cyr <= R2H);
+                // the image of the node nearest the region: support cells c-1 .. c+2 meet
+                // [0, R2W) iff the offset lies in [-2, R2W]
+                cxr = wrapn(c.x - (x0 - 2), nx);
+                cyr = wrapn(c.y - (y0 - 2), ny);
+                if (cxr > R2W) cxr -= nx;
+                if (cyr > R2H) cyr -= ny;
+                keep = small || (cxr >= -2 && cyr >= -2);
             }
             // order-preserving compaction of the kept nodes
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -415,31 +428,46 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         const float drho = sM[j2], ux = sM[R2 + j2], uy = sM[2 * R2 + j2];
         const float Fx = sM[3 * R2 + j2], Fy = sM[4 * R2 + j2];
 
-        // collision: d*_n = (1 - omega) d_n + omega d^eq_n + guo * S_n, pushed to x + c_n
+        // collision: d*_n = d_n + omega (d^eq_n - d_n) + guo * S_n, pushed to x + c_n.
+        // The change D_n = d*_n - d_n of one cell carries no mass and the momentum F in exact
+        // arithmetic; in FP32 the rounding of u (coherent over a uniform flow) would leak
+        // momentum into every cell alike, so the FP32 changes are corrected to exactly
+        // sum D_n = 0 and sum c_n D_n = F (pair and rest-population corrections).
         {
             const float rho = ph.rho0 + drho;
             const float uu = 1.5f * (ux * ux + uy * uy);
             const float uF = ux * Fx + uy * Fy;
-            double jxs = 0.0, jys = 0.0;
-            float dsum = 0.f;
+            float dn[9], D[9];
 #pragma unroll
             for (int n = 0; n < 9; ++n) {
-                const float dn = __ldg(src + n * NP + g);
-                const int cx = c_cx[n], cy = c_cy[n];
-                const float cu = (float)cx * ux + (float)cy * uy;
-                const float cF = (float)cx * Fx + (float)cy * Fy;
+                dn[n] = __ldg(src + n * NP + g);
+                const float cu = (float)c_cx[n] * ux + (float)c_cy[n] * uy;
+                const float cF = (float)c_cx[n] * Fx + (float)c_cy[n] * Fy;
                 const float deq = w9[n] * (drho + rho * (3.f * cu + 4.5f * cu * cu - uu));
                 const float S = w9[n] * (3.f * (cF - uF) + 9.f * cu * cF);
-                const float out = dn + ph.omega * (deq - dn) + ph.guo * S;
-                const long long gd = (long long)sYi[ly + 4 + cy] * nx + sXi[lx + 4 + cx];
-                dst[n * NP + gd] = out;
-                if (readout) {
-                    dsum += dn;
-                    jxs += (double)((float)cx * dn);
-                    jys += (double)((float)cy * dn);
-                }
+                D[n] = ph.omega * (deq - dn[n]) + ph.guo * S;
+            }
+            const float ex = ((D[1] - D[3]) + (D[5] - D[6]) + (D[8] - D[7])) - Fx;
+            const float ey = ((D[2] - D[4]) + (D[5] - D[8]) + (D[6] - D[7])) - Fy;
+            D[1] -= 0.5f * ex;
+            D[3] += 0.5f * ex;
+            D[2] -= 0.5f * ey;
+            D[4] += 0.5f * ey;
+            D[0] -= ((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8])) + D[0];
+#pragma unroll
+            for (int n = 0; n < 9; ++n) {
+                const long long gd = (long long)sYi[ly + 4 + c_cy[n]] * nx + sXi[lx + 4 + c_cx[n]];
+                dst[n * NP + gd] = dn[n] + D[n];
             }
             if (readout) {
+                float dsum = 0.f;
+                double jxs = 0.0, jys = 0.0;
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    dsum += dn[n];
+                    jxs += (double)((float)c_cx[n] * dn[n]);
+                    jys += (double)((float)c_cy[n] * dn[n]);
+                }
                 acc[0] += (double)dsum;
                 acc[1] += jxs;
                 acc[2] += jys;
@@ -457,9 +485,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
             const St s2 = st_at(sY + 2 * R1, R1W, lx + 1, ly + 1);
             const St p0 = st_at(sY + 3 * R1, R1W, lx + 1, ly + 1);
             const St p1 = st_at(sY + 4 * R1, R1W, lx + 1, ly + 1);
-            const float A = ph.alpha + ph.beta * (p0.c * p0.c + p1.c * p1.c);
-            const float hx = A * p0.c - ph.kappa * (p0.e + p0.w + p0.n + p0.s - 4.f * p0.c);
-            const float hy = A * p1.c - ph.kappa * (p1.e + p1.w + p1.n + p1.s - 4.f * p1.c);
+            float hx, hy;
+            molecular(ph, p0, p1, hx, hy);
             float r[5];
             rhs_cell(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
             const int j3 = (ly + 3) * R3W + lx + 3;

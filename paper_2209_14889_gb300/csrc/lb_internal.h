@@ -7,7 +7,10 @@
 namespace vlb {
 
 // Plane order of the stored state: 9 shifted populations d_n = h_n - w_n rho0, then
-// sigma^p (xx, yy, xy), then P (x, y).  Each plane is nx*ny FP32, x fastest.
+// sigma^p (xx, yy, xy), then the shifted polarisation dP = P - P_ref (x, y), where P_ref is the
+// uniform initial director field P_eq (cos theta_d, sin theta_d) rounded to FP32.  Each plane is
+// nx*ny FP32, x fastest.  Storing deviations keeps FP32 resolution where the physics needs it:
+// the molecular field depends on alpha + beta |P|^2, which nearly cancels at |P| ~ P_eq.
 enum { PL_POP = 0, PL_SXX = 9, PL_SYY = 10, PL_SXY = 11, PL_PX = 12, PL_PY = 13, N_PLANES = 14 };
 
 // C~(P) table: a2(q) = r2/q and a4(q) = r4/q^2 with q = |P|^2, r_n = I_n(k)/I_0(k), k = k(|P|)
@@ -31,6 +34,8 @@ struct Phys {
     float guo;          // 1 - 1/(2 tau)
     float rho0;
     float alpha, beta, xi, Gamma, kappa, Dp, inv_eta;
+    float prx, pry;     // P_ref (FP32)
+    float A0;           // alpha + beta |P_ref|^2, formed in FP64 from the FP32 P_ref
     float kS8;          // (3K1111 + 2K1122 + 4K1212 + 3K2222) / 8
     float kC12;         // (K1111 + 6K1122 - 4K1212 + K2222) / 8
     float kC33;         // (K1111 - 2K1122 + 4K1212 + K2222) / 4
