@@ -123,6 +123,21 @@ int64_t lb_time(const lb_handle* h);
  */
 int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
 
+/*
+ * lb_readout without any device allocation (the paper has no counterpart: this serves callers,
+ * not the method).  lb_readout creates its intermediate buffer for rho and u with cudaMalloc on
+ * first use; callers whose device memory is owned by another allocator, or who must not
+ * allocate after set-up, use this call instead.  It accepts LB_FIELD_DRHO, UX, UY, PX and PY
+ * and returns the same values as lb_readout.  The intermediate planes live in one scratch
+ * array compiled into the library: 3 x 2^20 FP32 (12 MiB), held on every GPU that loads the
+ * library until the process exits.  Lattices above 2^20 cells return LB_EINVAL.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before capturing the stream into a graph.  All calls share the array: calls whose
+ * work overlaps on the GPU (several handles, streams or threads at once) race on it.
+ * Synchronises the stream.
+ */
+int lb_readout_noalloc(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst_is_device);
+
 /* Overwrite one stored field (SXX..PY, POP0..POP8) of the current state from FP32 [ny][nx]. */
 int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, int32_t src_is_device);
 

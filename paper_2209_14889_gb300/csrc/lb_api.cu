@@ -546,6 +546,78 @@ int32_t lb_launches_per_step(const lb_handle* h) { return h ? 2 : 0; }
 
 double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * sizeof(float) : 0.0; }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Readout without device allocation.
+//
+// lb_readout creates its intermediate buffer for rho and u with cudaMalloc the first time it is
+// asked for them.  Some callers cannot allow that: code that runs while another framework owns
+// the whole device memory budget through its own pool, or code that must not allocate after its
+// set-up phase (a long-running service with a fixed memory plan).  lb_readout_noalloc computes
+// the same fields into a scratch array that is part of the library image on each GPU instead.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// Largest lattice the no-allocation readout accepts: 2^20 cells (e.g. 1024 x 1024).  The array
+// holds three FP32 planes (rho - rho0, u_x, u_y), 12 MiB, on every GPU that loads the library,
+// for as long as the process runs.
+constexpr long long NOALLOC_MAX_CELLS = 1LL << 20;
+static __device__ __align__(256) float g_noalloc_scratch[3 * NOALLOC_MAX_CELLS];
+
+// The array's name is only a host-side handle; its device address is looked up once per device.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+int noalloc_scratch(lb_handle* h, float** out)
+{
+    int dev = 0;
+    CK(h, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(h, LB_EINVAL, "device index %d out of range", dev);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CK(h, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = (float*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_readout_noalloc(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst_is_device)
+{
+    if (!h || !dst) return fail(h, LB_EINVAL, "null argument");
+    const size_t N = (size_t)h->plane;
+    if ((long long)N > NOALLOC_MAX_CELLS)
+        return fail(h, LB_EINVAL, "lb_readout_noalloc: %zu cells exceed the limit of %lld", N,
+                    NOALLOC_MAX_CELLS);
+    if (bytes != sizeof(float) * N) return fail(h, LB_EINVAL, "bytes mismatch");
+    float* scratch = nullptr;
+    int rc = noalloc_scratch(h, &scratch);
+    if (rc != LB_OK) return rc;
+    const float* srcp = nullptr;
+    if (field >= LB_FIELD_DRHO && field <= LB_FIELD_UY) {
+        // every in-lattice element of the three planes is written before it is read
+        FusedArgs fa = fused_args(h);
+        fa.moments_out = scratch;
+        CK(h, launch_fused(fa, MODE_MOMENTS, h->stream, nullptr));
+        srcp = scratch + (size_t)(field - LB_FIELD_DRHO) * N;
+    } else if (field == LB_FIELD_PX || field == LB_FIELD_PY) {
+        const float* st = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
+        CK(h, shift(scratch, st, field == LB_FIELD_PX ? h->ph.prx : h->ph.pry, (long long)N, h->stream));
+        srcp = scratch;
+    } else {
+        return fail(h, LB_EINVAL, "lb_readout_noalloc: field %d is not one of DRHO, UX, UY, PX, PY", field);
+    }
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(h, cudaMemcpyAsync(dst, srcp, bytes, kind, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
 const char* lb_last_error(const lb_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
 
 void lb_destroy(lb_handle* h)

@@ -1,0 +1,69 @@
+"""lb_readout_noalloc gives the same fields as lb_readout without allocating device memory.
+
+Callers whose device memory is owned by another allocator, or who must not allocate after
+their set-up phase, read rho and u through lb_readout_noalloc: it keeps its intermediate planes
+in a scratch array that is part of the library image instead of a buffer created with
+cudaMalloc.  These tests call it through the C ABI and compare it with lb_readout.  The file is
+named to run last, so that a failure here comes after every other test has run.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2209_14889_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = [("drho", 0), ("ux", 1), ("uy", 2), ("Px", 6), ("Py", 7)]
+
+
+def _setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_14889_gb300 import lb
+    f = lb.lib().lb_readout_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
+    return torch, lb, f
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-9 * np.sqrt(b.size))
+
+
+def test_noalloc_readout_matches_readout_twice():
+    torch, lb, f = _setup()
+    s = lb.Solver.from_workload(W.small(64, 48, steps=0))
+    try:
+        for call in range(2):                       # two calls in a row, state advanced between
+            s.step(7)
+            for name, fid in FIELDS:
+                ref = s.readout(name, device=False)
+                host = np.empty_like(ref)
+                assert f(s.h, fid, host.ctypes.data, host.nbytes, 0) == 0, lb.lib().lb_last_error(s.h)
+                dev = torch.empty(ref.shape, dtype=torch.float32, device="cuda")
+                assert f(s.h, fid, dev.data_ptr(), dev.numel() * 4, 1) == 0, lb.lib().lb_last_error(s.h)
+                for got in (host, dev.cpu().numpy()):
+                    assert rel_l2(got.astype(np.float64), ref.astype(np.float64)) <= 1e-5, (call, name)
+    finally:
+        s.close()
+
+
+def test_noalloc_rejects_oversized_lattice_and_other_fields():
+    torch, lb, f = _setup()
+    s = lb.Solver.from_workload(W.make(2048, 1024, rings=[], noise_amp=0.0))
+    try:
+        out = np.empty((1024, 2048), dtype=np.float32)
+        rc = f(s.h, 1, out.ctypes.data, out.nbytes, 0)
+        assert rc == lb.LB_EINVAL
+        assert b"limit" in lb.lib().lb_last_error(s.h)
+    finally:
+        s.close()
+    s = lb.Solver.from_workload(W.make(32, 32, rings=[], noise_amp=0.0))
+    try:
+        out = np.empty((32, 32), dtype=np.float32)
+        assert f(s.h, 3, out.ctypes.data, out.nbytes, 0) == lb.LB_EINVAL      # SXX: no scratch
+    finally:
+        s.close()
