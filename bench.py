@@ -191,6 +191,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=1024,
+                    help="lattice side (profiling captures use 2048 so that the state exceeds L2)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the device steps only (no e2e, parity check or CPU baseline)")
     args = ap.parse_args()
     rank, local, world = dist_env()
     if args.impl == "reference":
@@ -205,6 +209,11 @@ def main():
     from paper_2209_14889_gb300 import lb, workloads as W
 
     w = W.cfg2(seed=2 + rank)
+    if args.side != 1024:
+        w = W.make(args.side, args.side,
+                   rings=[W.ring(256, 24.0, (args.side / 2, args.side / 2), pull_force=5e-4,
+                                 pull_angle=math.radians(30))],
+                   seed=2 + rank, steps=20000, every=10, lambda_steps=200.0, Dp=0.1)
     cells = w["nx"] * w["ny"]
     s = lb.Solver.from_workload(w)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -257,6 +266,17 @@ def main():
             "algorithmic_bytes_per_launch": bytes_launch,
             "mean_launch_us": fused_avg_s * 1e6,
             "node_kernel_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1)}
+
+    if args.no_extras:
+        s.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                              "steps": args.steps, "ms_per_step": ms / args.steps,
+                              "config": {"lattice": [w["nx"], w["ny"]]}, "roofline": roof,
+                              "note": "device steps only (--no-extras)"}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     # end to end through the C ABI with host buffers
     host = {}
