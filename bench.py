@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=1024,
                     help="lattice side (profiling captures use 2048 so that the state exceeds L2)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "sweep"],
+                    help="lattice kernel (auto: the sweep when eligible)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the device steps only (no e2e, parity check or CPU baseline)")
     args = ap.parse_args()
@@ -216,6 +218,8 @@ def main():
                    seed=2 + rank, steps=20000, every=10, lambda_steps=200.0, Dp=0.1)
     cells = w["nx"] * w["ny"]
     s = lb.Solver.from_workload(w)
+    s.set_kernel({"auto": lb.LB_KERNEL_AUTO, "tile": lb.LB_KERNEL_TILE,
+                  "sweep": lb.LB_KERNEL_SWEEP}[args.kernel])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 

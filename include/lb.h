@@ -39,6 +39,7 @@ extern "C" {
 #define LB_EUNSTABLE (-5)   /* parameters outside the explicit stability bounds          */
 #define LB_EBODY (-6)       /* a ring left its work box or moved >= 1 cell in one step   */
 #define LB_ESTATE (-7)      /* call out of order (e.g. lb_step before lb_init_fields)    */
+#define LB_ETIMEOUT (-8)    /* a bounded wait inside a kernel gave up (results invalid)  */
 
 /* Storage precision of the lattice state. */
 #define LB_FP32 0
@@ -165,11 +166,31 @@ int lb_timing(lb_handle* h, int32_t enable);
 int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, double* node_ms,
                    int64_t* node_launches);
 
+/*
+ * Lattice kernel used by lb_step.  Both compute the same step with the same per-cell
+ * arithmetic.  LB_KERNEL_TILE: 32 x 16 tiles with their halo recomputed (any lattice).
+ * LB_KERNEL_SWEEP: column strips swept row by row, rows streamed by asynchronous bulk copies
+ * (needs nx % 4 == 0, nx >= 256, ny >= 16, else LB_EINVAL).  LB_KERNEL_AUTO (default): the
+ * kernel measured fastest on GB300, currently the tile kernel.
+ */
+#define LB_KERNEL_AUTO 0
+#define LB_KERNEL_TILE 1
+#define LB_KERNEL_SWEEP 2
+int lb_set_kernel(lb_handle* h, int32_t kernel);
+
 /* Number of kernels launched per lb_step(1) call (2: fused lattice + node kernel). */
 int32_t lb_launches_per_step(const lb_handle* h);
 
 /* Bytes of lattice state per cell moved by one step (read + write, the algorithmic minimum). */
 double lb_bytes_per_cell(const lb_handle* h);
+
+/*
+ * The host-built table behind C~(P) (App. B), for inspection: entry i (i = 0 .. n-1) holds
+ * (a2, a4) = (r2 / q, r4 / q^2) at q = |P|^2 = P_cap^2 i / (n - 1), with r_n = I_n(k) / I_0(k) and
+ * k solving I1(k) / I0(k) = |P| (Eq. Pk); a2(0) = 1/2, a4(0) = 1/24.  dst: host FP32 [n][2], or
+ * NULL to query n.  Returns n, or a negative LB_E* code.  Needs no GPU.
+ */
+int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries);
 
 const char* lb_last_error(const lb_handle* h);
 void lb_destroy(lb_handle* h);

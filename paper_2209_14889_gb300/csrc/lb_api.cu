@@ -1,6 +1,9 @@
 // lb_api.cu -- the C ABI declared in include/lb.h: handle, validation, device buffers, launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,7 +27,9 @@ struct lb_handle {
     float2* lut = nullptr;
     Ctl* ctl = nullptr;
     double* partials = nullptr;
-    int n_partials = 0;
+    int n_partials = 0;                     // partial sums written by the last lattice launch
+    int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP
+    int sweep_chunk = 0;
     double* series = nullptr;
     int series_cap = 0;
     int row_len = 6;
@@ -153,6 +158,21 @@ NodeArgs node_args(lb_handle* h, int advance)
     return a;
 }
 
+// The C~ table depends only on P_cap; it is built once per value in the process.
+void cached_lut(double P_cap, std::vector<float>& out)
+{
+    static std::mutex mu;
+    static std::map<double, std::vector<float>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(P_cap);
+    if (it == cache.end()) {
+        std::vector<float> t(2 * (LUT_N + 1));
+        build_lut(P_cap, t.data());
+        it = cache.emplace(P_cap, std::move(t)).first;
+    }
+    out = it->second;
+}
+
 // dst = src + c (the stored polarisation is dP = P - P_ref)
 __global__ void k_shift(float* dst, const float* src, float c, long long n)
 {
@@ -237,14 +257,18 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
         cudaError_t e = cudaMalloc(&h->state[b], state_bytes);
         if (e != cudaSuccess) { rc = cuda_fail(nullptr, e, "cudaMalloc(state)"); return bail(rc); }
     }
-    std::vector<float> lut(2 * (LUT_N + 1));
-    build_lut(p.P_cap, lut.data());
+    std::vector<float> lut;
+    cached_lut(p.P_cap, lut);
+    int dev = 0, n_sm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    h->sweep_chunk = sweep_chunk(p.nx, p.ny, n_sm);
     h->n_partials = fused_ctas(p.nx, p.ny);
+    const int partial_cap = std::max(h->n_partials, sweep_ctas(p.nx, p.ny, h->sweep_chunk));
     h->series_cap = p.max_samples;
     cudaError_t e;
     if ((e = cudaMalloc(&h->lut, sizeof(float) * lut.size())) != cudaSuccess ||
         (e = cudaMalloc(&h->ctl, sizeof(Ctl))) != cudaSuccess ||
-        (e = cudaMalloc(&h->partials, sizeof(double) * 5 * (size_t)h->n_partials)) != cudaSuccess) {
+        (e = cudaMalloc(&h->partials, sizeof(double) * 5 * (size_t)partial_cap)) != cudaSuccess) {
         rc = cuda_fail(nullptr, e, "cudaMalloc");
         return bail(rc);
     }
@@ -380,7 +404,15 @@ int lb_step(lb_handle* h, int64_t n)
             e1 = ev_get(h->ev_fused, h->ev_fused_used);
             if (e0) cudaEventRecord(e0, h->stream);
         }
-        CK(h, launch_fused(fa, MODE_STEP, h->stream, nullptr));
+        // LB_KERNEL_AUTO takes the tile kernel: measured faster than the sweep on GB300 so far
+        // (1024^2: 84 vs 121 us per launch; the sweep stalls on its per-row barriers)
+        const bool sweep = h->kernel == LB_KERNEL_SWEEP;
+        if (sweep) {
+            CK(h, launch_sweep(fa, h->sweep_chunk, h->stream));
+            h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
+        } else {
+            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials));
+        }
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
         if (h->timing) {
             e0 = ev_get(h->ev_nodes, h->ev_nodes_used);
@@ -401,9 +433,10 @@ int lb_sync(lb_handle* h)
     CK(h, cudaStreamSynchronize(h->stream));
     Ctl c;
     CK(h, cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    if (c.err_nonfinite || c.err_body) {
-        int z[3] = {0, 0, 0};
-        CK(h, cudaMemcpy(&h->ctl->err_nonfinite, z, sizeof(int) * 3, cudaMemcpyHostToDevice));
+    if (c.err_nonfinite || c.err_body || c.err_timeout) {
+        int z[4] = {0, 0, 0, 0};
+        CK(h, cudaMemcpy(&h->ctl->err_nonfinite, z, sizeof(int) * 4, cudaMemcpyHostToDevice));
+        if (c.err_timeout) return fail(h, LB_ETIMEOUT, "a bounded wait in the lattice kernel timed out");
         if (c.err_nonfinite) return fail(h, LB_ENONFINITE, "non-finite readout or node force");
         return fail(h, LB_EBODY, "a ring left its work box or moved >= 1 cell in a step");
     }
@@ -543,6 +576,27 @@ int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, doub
 }
 
 int32_t lb_launches_per_step(const lb_handle* h) { return h ? 2 : 0; }
+
+int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries)
+{
+    if (!(P_cap > 0.0 && P_cap < 1.0)) return fail(nullptr, LB_EINVAL, "need 0 < P_cap < 1");
+    if (!dst) return LUT_N + 1;
+    if (max_entries < LUT_N + 1) return fail(nullptr, LB_EINVAL, "need %d entries", LUT_N + 1);
+    std::vector<float> t;
+    cached_lut(P_cap, t);
+    memcpy(dst, t.data(), sizeof(float) * t.size());
+    return LUT_N + 1;
+}
+
+int lb_set_kernel(lb_handle* h, int32_t kernel)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_SWEEP) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))
+        return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");
+    h->kernel = kernel;
+    return LB_OK;
+}
 
 double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * sizeof(float) : 0.0; }
 

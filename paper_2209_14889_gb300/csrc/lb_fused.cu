@@ -18,11 +18,14 @@
 // so that FP32 keeps the small deviations that carry the flow.
 #include <cuda_runtime.h>
 
+#include "lb_cell.cuh"
 #include "lb_internal.h"
 
 namespace vlb {
 
 namespace {
+
+using namespace cell;
 
 constexpr int TX = 32;
 constexpr int TY = 16;
@@ -46,8 +49,8 @@ constexpr int OFF_H = OFF_E + SZ_E;                       // h        [2][R3]
 constexpr int OFF_M = OFF_H + 2 * R3;                     // drho,ux,uy,Fx,Fy [5][R2]
 constexpr int OFF_R = OFF_M + 5 * R2;                     // RHS(y)   [5][R0] | f_IB [2][R2]
 constexpr int SZ_R = cmax(5 * R0, 2 * R2);
-constexpr int OFF_L = OFF_R + SZ_R;                       // LUT      [2][LUT_N+1]
-constexpr int OFF_N = al4(OFF_L + 2 * (LUT_N + 1));       // nodes    [NT] float4 (cell, frac)
+constexpr int OFF_L = OFF_R + SZ_R;                       // (the C~ table is read through L1)
+constexpr int OFF_N = al4(OFF_L);                         // nodes    [NT] float4 (cell, frac)
 constexpr int OFF_NF = OFF_N + 4 * NT;                    // node forces [NT] float2
 constexpr int OFF_XI = OFF_NF + 2 * NT;                   // wrapped x index [R4W] (int)
 constexpr int OFF_YI = OFF_XI + R4W;                      // wrapped y index [R4H] (int)
@@ -57,140 +60,6 @@ constexpr int SMEM_FLOATS = OFF_RED + 2 * 5 * (NT / 32);
 constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 static_assert(OFF_N % 4 == 0 && OFF_NF % 2 == 0 && OFF_RED % 2 == 0, "shared-memory alignment");
 static_assert(SMEM_BYTES <= 75 * 1024, "three CTAs per SM");
-
-__device__ __forceinline__ int wrapn(int i, int n)
-{
-    i %= n;
-    return i < 0 ? i + n : i;
-}
-
-// minimum image of an integer offset on a periodic axis of length n, in [-n/2, n/2)
-__device__ __forceinline__ int mimg(int d, int n)
-{
-    d %= n;
-    if (d < -(n / 2)) d += n;
-    else if (d >= n - n / 2) d -= n;
-    return d;
-}
-
-// cosine IB kernel phi(r) = (1 + cos(pi r / 2)) / 4 for |r| < 2 (App. A)
-__device__ __forceinline__ float phi(float r)
-{
-    return fabsf(r) < 2.f ? 0.25f * (1.f + cospif(0.5f * r)) : 0.f;
-}
-
-__device__ __forceinline__ void lut_eval(const float* L, const Phys& ph, float q, float& a2, float& a4)
-{
-    float qq = fminf(q, ph.q_cap);
-    float t = qq * ph.lut_scale;
-    int i = min(max((int)t, 1), LUT_N - 2);
-    float f = t - (float)i;
-    float fm1 = f - 1.f, fm2 = f - 2.f, fp1 = f + 1.f;
-    float w0 = -f * fm1 * fm2 * (1.f / 6.f);
-    float w1 = fp1 * fm1 * fm2 * 0.5f;
-    float w2 = -fp1 * f * fm2 * 0.5f;
-    float w3 = fp1 * f * fm1 * (1.f / 6.f);
-    const float* v = L + 2 * (i - 1);
-    a2 = w0 * v[0] + w1 * v[2] + w2 * v[4] + w3 * v[6];
-    a4 = w0 * v[1] + w1 * v[3] + w2 * v[5] + w3 * v[7];
-    if (q > ph.q_cap) {
-        float s = ph.q_cap / q;
-        a2 *= s;
-        a4 *= s * s;
-    }
-}
-
-// Stencil values of one component: centre, east (+x), west, north (+y), south.
-struct St {
-    float c, e, w, n, s;
-};
-
-__device__ __forceinline__ St st_at(const float* base, int W, int lx, int ly)
-{
-    const float* p = base + ly * W + lx;
-    return St{p[0], p[1], p[-1], p[W], p[-W]};
-}
-
-// Molecular field h = (alpha + beta |P|^2) P - kappa lap P (Eq. Ffunctional) from the stencil
-// of dP = P - P_ref: alpha + beta |P|^2 = A0 + beta (2 P_ref.dP + |dP|^2) has no cancellation.
-__device__ __forceinline__ void molecular(const Phys& ph, const St& dx, const St& dy, float& hx,
-                                          float& hy)
-{
-    const float A = ph.A0 + ph.beta * (2.f * (ph.prx * dx.c + ph.pry * dy.c) + (dx.c * dx.c + dy.c * dy.c));
-    hx = A * (ph.prx + dx.c) - ph.kappa * (dx.e + dx.w + dx.n + dx.s - 4.f * dx.c);
-    hy = A * (ph.pry + dy.c) - ph.kappa * (dy.e + dy.w + dy.n + dy.s - 4.f * dy.c);
-}
-
-// Right-hand sides of Eq. StiffCons (with the Jaumann derivative) and Eq. BE at one cell, for
-// the frozen u, Psi = (pxx, pyy, pxy), omega = Omega_xy; s = sigma (xx, yy, xy), p = dP (x, y).
-__device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, float ux, float uy,
-                                         float pxx, float pyy, float pxy, float om,
-                                         const St& s0, const St& s1, const St& s2,
-                                         const St& p0, const St& p1, float hx, float hy,
-                                         float* r)
-{
-    // stiffness C~(P) (App. B) from the table of a2, a4 and polynomials in P = P_ref + dP
-    const float Px = ph.prx + p0.c, Py = ph.pry + p1.c;
-    const float q = Px * Px + Py * Py;
-    float a2, a4;
-    lut_eval(lut, ph, q, a2, a4);
-    const float c2q = Px * Px - Py * Py, s2q = 2.f * Px * Py;
-    const float r2c2 = a2 * c2q, r2s2 = a2 * s2q;
-    const float r4c4 = a4 * (c2q * c2q - s2q * s2q), r4s4 = a4 * (2.f * c2q * s2q);
-    const float C11 = ph.kS8 + 0.5f * ph.dK * r2c2 + 0.125f * ph.kX * r4c4;
-    const float C12 = ph.kC12 - 0.125f * ph.kX * r4c4;
-    const float C13 = 0.25f * ph.kX * r4s4 + 0.5f * ph.dK * r2s2;
-    const float C22 = C11 - ph.dK * r2c2;
-    const float C23 = 0.5f * ph.dK * r2s2 - 0.25f * ph.kX * r4s4;
-    const float C33 = ph.kC33 - 0.25f * ph.kX * r4c4;
-
-    // C psi - C s / eta_p = C (psi - s / eta_p)
-    const float v0 = pxx - ph.inv_eta * s0.c;
-    const float v1 = pyy - ph.inv_eta * s1.c;
-    const float v2 = pxy - ph.inv_eta * s2.c;
-    const float Cv0 = C11 * v0 + C12 * v1 + C13 * v2;
-    const float Cv1 = C12 * v0 + C22 * v1 + C23 * v2;
-    const float Cv2 = 0.5f * C13 * v0 + 0.5f * C23 * v1 + C33 * v2;
-
-    // Jaumann rotation (Omega s - s Omega) = (2 w sxy, -2 w sxy, w (syy - sxx))
-    const float J0 = 2.f * om * s2.c;
-    const float J2 = om * (s1.c - s0.c);
-
-    const float D = ph.Dp;
-    r[0] = -(ux * 0.5f * (s0.e - s0.w) + uy * 0.5f * (s0.n - s0.s)) - J0 + Cv0 +
-           D * (s0.e + s0.w + s0.n + s0.s - 4.f * s0.c);
-    r[1] = -(ux * 0.5f * (s1.e - s1.w) + uy * 0.5f * (s1.n - s1.s)) + J0 + Cv1 +
-           D * (s1.e + s1.w + s1.n + s1.s - 4.f * s1.c);
-    r[2] = -(ux * 0.5f * (s2.e - s2.w) + uy * 0.5f * (s2.n - s2.s)) - J2 + Cv2 +
-           D * (s2.e + s2.w + s2.n + s2.s - 4.f * s2.c);
-    // Eq. BE: -(u.grad)P - Omega P + xi Psi P - Gamma h
-    r[3] = -(ux * 0.5f * (p0.e - p0.w) + uy * 0.5f * (p0.n - p0.s)) - om * Py +
-           ph.xi * (pxx * Px + pxy * Py) - ph.Gamma * hx;
-    r[4] = -(ux * 0.5f * (p1.e - p1.w) + uy * 0.5f * (p1.n - p1.s)) + om * Px +
-           ph.xi * (pxy * Px + pyy * Py) - ph.Gamma * hy;
-}
-
-// Velocity gradient at the cell (lx, ly) of a region of width W (u planes at ux, uy).
-__device__ __forceinline__ void vgrad(const float* ux, const float* uy, int W, int i, float& pxx,
-                                      float& pyy, float& pxy, float& om)
-{
-    const float dxux = 0.5f * (ux[i + 1] - ux[i - 1]);
-    const float dyux = 0.5f * (ux[i + W] - ux[i - W]);
-    const float dxuy = 0.5f * (uy[i + 1] - uy[i - 1]);
-    const float dyuy = 0.5f * (uy[i + W] - uy[i - W]);
-    pxx = dxux;
-    pyy = dyuy;
-    pxy = 0.5f * (dxuy + dyux);
-    om = 0.5f * (dxuy - dyux);
-}
-
-// Does the periodic interval [b, b + bw) meet [a, a + aw) on an axis of length n?
-__device__ __forceinline__ bool meets(int a, int aw, int b, int bw, int n)
-{
-    if (aw >= n || bw >= n) return true;
-    int d1 = wrapn(a - b, n), d2 = wrapn(b - a, n);
-    return d1 < bw || d2 < aw;
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
@@ -204,7 +73,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     float* sM = sm + OFF_M;
     float* sR = sm + OFF_R;
     float* sFib = sm + OFF_R;    // f_IB before RHS(y) is written
-    float* sL = sm + OFF_L;
+    const float* sL = reinterpret_cast<const float*>(a.lut);   // C~ table (global, L1)
     float4* sNode = reinterpret_cast<float4*>(sm + OFF_N);
     float2* sNodeF = reinterpret_cast<float2*>(sm + OFF_NF);
     int* sXi = reinterpret_cast<int*>(sm + OFF_XI);
@@ -221,7 +90,6 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 
     for (int i = tid; i < R4W; i += NT) sXi[i] = wrapn(x0 - 4 + i, nx);
     for (int i = tid; i < R4H; i += NT) sYi[i] = wrapn(y0 - 4 + i, ny);
-    for (int i = tid; i < 2 * (LUT_N + 1); i += NT) sL[i] = reinterpret_cast<const float*>(a.lut)[i];
     for (int i = tid; i < 2 * R2; i += NT) sFib[i] = 0.f;
     __syncthreads();
 
@@ -246,21 +114,15 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         const int ly = i / R3W, lx = i - ly * R3W;
         const St px = st_at(sP, R4W, lx + 1, ly + 1);         // dP stencils
         const St py = st_at(sP + R4, R4W, lx + 1, ly + 1);
-        float hx, hy;
-        molecular(ph, px, py, hx, hy);
+        float hx, hy, E[4];
+        ericksen(ph, px, py, hx, hy, E);
         sH[i] = hx;
         sH[R3 + i] = hy;
         if (ph.ericksen) {
-            const float Px = ph.prx + px.c, Py = ph.pry + py.c;
-            const float gxPx = 0.5f * (px.e - px.w), gyPx = 0.5f * (px.n - px.s);
-            const float gxPy = 0.5f * (py.e - py.w), gyPy = 0.5f * (py.n - py.s);
-            const float anti = Px * hy - hx * Py;
-            const float sym = Px * hy + hx * Py;
-            const float cross = ph.kappa * (gxPx * gyPx + gxPy * gyPy);
-            sE[i] = ph.xi * Px * hx - ph.kappa * (gxPx * gxPx + gxPy * gxPy);            // xx
-            sE[R3 + i] = -0.5f * anti + 0.5f * ph.xi * sym - cross;                       // xy
-            sE[2 * R3 + i] = 0.5f * anti + 0.5f * ph.xi * sym - cross;                    // yx
-            sE[3 * R3 + i] = ph.xi * Py * hy - ph.kappa * (gyPx * gyPx + gyPy * gyPy);    // yy
+            sE[i] = E[0];
+            sE[R3 + i] = E[1];
+            sE[2 * R3 + i] = E[2];
+            sE[3 * R3 + i] = E[3];
         }
     }
 
@@ -341,26 +203,29 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     for (int i = tid; i < R2; i += NT) {
         const int ly = i / R2W, lx = i - ly * R2W;
         const int j3 = (ly + 1) * R3W + lx + 1;
-        float Fx = 0.5f * (sS[j3 + 1] - sS[j3 - 1]) + 0.5f * (sS[2 * R3 + j3 + R3W] - sS[2 * R3 + j3 - R3W]);
-        float Fy = 0.5f * (sS[2 * R3 + j3 + 1] - sS[2 * R3 + j3 - 1]) + 0.5f * (sS[R3 + j3 + R3W] - sS[R3 + j3 - R3W]);
+        float Fx, Fy;
+        div_sigma(st_at(sS, R3W, lx + 1, ly + 1), st_at(sS + R3, R3W, lx + 1, ly + 1),
+                  st_at(sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
         if (ph.ericksen) {
-            Fx += 0.5f * (sE[j3 + 1] - sE[j3 - 1]) + 0.5f * (sE[R3 + j3 + R3W] - sE[R3 + j3 - R3W]);
-            Fy += 0.5f * (sE[2 * R3 + j3 + 1] - sE[2 * R3 + j3 - 1]) +
-                  0.5f * (sE[3 * R3 + j3 + R3W] - sE[3 * R3 + j3 - R3W]);
+            float ex, ey;
+            div_ericksen(st_at(sE, R3W, lx + 1, ly + 1), st_at(sE + R3, R3W, lx + 1, ly + 1),
+                         st_at(sE + 2 * R3, R3W, lx + 1, ly + 1), st_at(sE + 3 * R3, R3W, lx + 1, ly + 1),
+                         ex, ey);
+            Fx += ex;
+            Fy += ey;
         }
+        (void)j3;
         Fx += sFib[i];
         Fy += sFib[R2 + i];
         const long long g = (long long)sYi[ly + 2] * nx + sXi[lx + 2];
         float d[9];
 #pragma unroll
         for (int n = 0; n < 9; ++n) d[n] = __ldg(src + n * NP + g);
-        const float drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-        const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-        const float jy = (d[2] - d[4]) + (d[5] - d[8]) + (d[6] - d[7]);
-        const float inv = 1.f / (ph.rho0 + drho);
+        float drho, ux, uy;
+        moments(ph, d, Fx, Fy, drho, ux, uy);
         sM[i] = drho;
-        sM[R2 + i] = (jx + 0.5f * Fx) * inv;
-        sM[2 * R2 + i] = (jy + 0.5f * Fy) * inv;
+        sM[R2 + i] = ux;
+        sM[2 * R2 + i] = uy;
         sM[3 * R2 + i] = Fx;
         sM[4 * R2 + i] = Fy;
     }
@@ -428,32 +293,13 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         const float drho = sM[j2], ux = sM[R2 + j2], uy = sM[2 * R2 + j2];
         const float Fx = sM[3 * R2 + j2], Fy = sM[4 * R2 + j2];
 
-        // collision: d*_n = d_n + omega (d^eq_n - d_n) + guo * S_n, pushed to x + c_n.
-        // The change D_n = d*_n - d_n of one cell carries no mass and the momentum F in exact
-        // arithmetic; in FP32 the rounding of u (coherent over a uniform flow) would leak
-        // momentum into every cell alike, so the FP32 changes are corrected to exactly
-        // sum D_n = 0 and sum c_n D_n = F (pair and rest-population corrections).
+        // collision (Eq. LB, Eq. BGK, Guo source; exactly conservative FP32 increments),
+        // pushed to x + c_n
         {
-            const float rho = ph.rho0 + drho;
-            const float uu = 1.5f * (ux * ux + uy * uy);
-            const float uF = ux * Fx + uy * Fy;
             float dn[9], D[9];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) {
-                dn[n] = __ldg(src + n * NP + g);
-                const float cu = (float)c_cx[n] * ux + (float)c_cy[n] * uy;
-                const float cF = (float)c_cx[n] * Fx + (float)c_cy[n] * Fy;
-                const float deq = w9[n] * (drho + rho * (3.f * cu + 4.5f * cu * cu - uu));
-                const float S = w9[n] * (3.f * (cF - uF) + 9.f * cu * cF);
-                D[n] = ph.omega * (deq - dn[n]) + ph.guo * S;
-            }
-            const float ex = ((D[1] - D[3]) + (D[5] - D[6]) + (D[8] - D[7])) - Fx;
-            const float ey = ((D[2] - D[4]) + (D[5] - D[8]) + (D[6] - D[7])) - Fy;
-            D[1] -= 0.5f * ex;
-            D[3] += 0.5f * ex;
-            D[2] -= 0.5f * ey;
-            D[4] += 0.5f * ey;
-            D[0] -= ((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8])) + D[0];
+            for (int n = 0; n < 9; ++n) dn[n] = __ldg(src + n * NP + g);
+            collide(ph, dn, drho, ux, uy, Fx, Fy, D);
 #pragma unroll
             for (int n = 0; n < 9; ++n) {
                 const long long gd = (long long)sYi[ly + 4 + c_cy[n]] * nx + sXi[lx + 4 + c_cx[n]];

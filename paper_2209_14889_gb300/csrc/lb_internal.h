@@ -15,9 +15,10 @@ enum { PL_POP = 0, PL_SXX = 9, PL_SYY = 10, PL_SXY = 11, PL_PX = 12, PL_PY = 13,
 
 // C~(P) table: a2(q) = r2/q and a4(q) = r4/q^2 with q = |P|^2, r_n = I_n(k)/I_0(k), k = k(|P|)
 // (Eq. Pk), sampled at LUT_N + 1 uniform points of q in [0, q_cap], q_cap = P_cap^2;
-// interpolated by 4-point Lagrange polynomials.  Beyond q_cap: a2 = a2(q_cap) q_cap/q,
-// a4 = a4(q_cap) (q_cap/q)^2 (k is fixed at the cap, theta_P still follows P).
-constexpr int LUT_N = 256;
+// interpolated linearly (relative error <= 3.2e-7 for a4, 2e-8 for a2; read through L1).
+// Beyond q_cap: a2 = a2(q_cap) q_cap/q, a4 = a4(q_cap) (q_cap/q)^2 (k is fixed at the cap,
+// theta_P still follows P).
+constexpr int LUT_N = 4096;
 
 // Per-ring device record.
 struct RingDev {
@@ -53,6 +54,7 @@ struct Ctl {
     int err_nonfinite;
     int err_body;
     int err_cfl;
+    int err_timeout;             // a bounded wait of a lattice kernel gave up
 };
 
 struct FusedArgs {
@@ -70,7 +72,7 @@ struct FusedArgs {
     float* ubox;                 // u(t) on each ring's box (written)
     float* fpbox;                // f^p(t) on each ring's box (written on readout steps)
     double* partials;            // per-CTA readout sums (5 per CTA)
-    const Ctl* ctl;
+    Ctl* ctl;
     int every;                   // readout period
     float* moments_out;          // MOMENTS mode: drho, ux, uy planes
 };
@@ -96,6 +98,11 @@ struct NodeArgs {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas);
+// column-strip sweep (lb_sweep.cu): eligibility, rows per CTA chunk, CTA count, launch
+bool sweep_eligible(int nx, int ny);
+int sweep_chunk(int nx, int ny, int n_sm);
+int sweep_ctas(int nx, int ny, int chunk);
+cudaError_t launch_sweep(const FusedArgs& a, int chunk, cudaStream_t s);
 cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s);
 int fused_ctas(int nx, int ny);
 

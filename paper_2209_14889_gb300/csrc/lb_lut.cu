@@ -18,7 +18,7 @@ namespace vlb {
 
 namespace {
 
-constexpr int M_TRAP = 1024;
+constexpr int M_TRAP = 256;   // spectrally accurate: the integrand is smooth and periodic
 
 // I_n(k) e^{-k} * pi (the common factor cancels in the ratios)
 double scaled_in(int n, double k)
@@ -35,13 +35,14 @@ double scaled_in(int n, double k)
 
 double ratio(int n, double k) { return scaled_in(n, k) / scaled_in(0, k); }
 
-// Invert P = I1(k)/I0(k) (monotone increasing, P'(k) = 1 - P/k - P^2).
-double invert_P(double P)
+// Invert P = I1(k)/I0(k) (monotone increasing, P'(k) = 1 - P/k - P^2) by safeguarded Newton,
+// starting from k0 (the previous table entry).
+double invert_P(double P, double k0)
 {
     if (P <= 0.0) return 0.0;
     double lo = 0.0, hi = 4.0;
     while (ratio(1, hi) < P) { lo = hi; hi *= 2.0; }
-    double k = 0.5 * (lo + hi);
+    double k = (k0 > lo && k0 < hi) ? k0 : 0.5 * (lo + hi);
     for (int it = 0; it < 100; ++it) {
         double r = ratio(1, k);
         if (r > P) hi = k; else lo = k;
@@ -59,6 +60,7 @@ double invert_P(double P)
 void build_lut(double P_cap, float* lut)
 {
     const double q_cap = P_cap * P_cap;
+    double k = 0.0;
     for (int i = 0; i <= LUT_N; ++i) {
         double a2, a4;
         if (i == 0) {
@@ -66,7 +68,7 @@ void build_lut(double P_cap, float* lut)
             a4 = 1.0 / 24.0;     // r4 ~ k^4/384, q^2 ~ k^4/16
         } else {
             double q = q_cap * i / LUT_N;
-            double k = invert_P(std::sqrt(q));
+            k = invert_P(std::sqrt(q), k);
             a2 = ratio(2, k) / q;
             a4 = ratio(4, k) / (q * q);
         }

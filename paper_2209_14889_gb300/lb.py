@@ -16,7 +16,9 @@ from . import _build
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EUNSTABLE, LB_EBODY, LB_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
+LB_ETIMEOUT = -8
 LB_FP32 = 0
+LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP = 0, 1, 2
 FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
 LB_FIELD_POP0 = 8
 LB_FIELD_NODES = 17
@@ -83,6 +85,8 @@ def lib():
             "lb_kernel_time": (ctypes.c_int, [_H, dp, ctypes.POINTER(i64), dp,
                                               ctypes.POINTER(i64)]),
             "lb_launches_per_step": (i32, [_H]),
+            "lb_set_kernel": (ctypes.c_int, [_H, i32]),
+            "lb_stiffness_table": (i32, [ctypes.c_double, vp, i32]),
             "lb_bytes_per_cell": (ctypes.c_double, [_H]),
             "lb_last_error": (ctypes.c_char_p, [_H]),
             "lb_destroy": (None, [_H]),
@@ -109,6 +113,17 @@ def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4
                      P_cap=w.get("P_cap", 0.99), director_angle=w["director_angle"],
                      ericksen=w.get("ericksen", 1), precision=precision,
                      readout_every=w.get("every", 10), max_samples=max_samples)
+
+
+def stiffness_table(P_cap: float = 0.99) -> np.ndarray:
+    """The host-built (a2, a4) table behind C~(P): FP32 [n, 2] (see lb_stiffness_table)."""
+    L = lib()
+    n = L.lb_stiffness_table(P_cap, None, 0)
+    if n < 0:
+        raise LBError(n, L.lb_last_error(None).decode())
+    out = np.zeros((n, 2), dtype=np.float32)
+    _check(None, 0 if L.lb_stiffness_table(P_cap, out.ctypes.data, n) == n else LB_EINVAL)
+    return out
 
 
 class Solver:
@@ -220,6 +235,10 @@ class Solver:
         n = ctypes.c_int32(0)
         _check(self.h, L.lb_series(self.h, buf.ctypes.data, cap, ctypes.byref(n)))
         return buf[:n.value].copy()
+
+    def set_kernel(self, kernel: int):
+        """LB_KERNEL_AUTO (sweep when eligible), LB_KERNEL_TILE or LB_KERNEL_SWEEP."""
+        _check(self.h, lib().lb_set_kernel(self.h, int(kernel)))
 
     def timing(self, enable: bool):
         _check(self.h, lib().lb_timing(self.h, 1 if enable else 0))

@@ -75,3 +75,23 @@ def test_parameter_validation_without_gpu():
         rc = L.lb_create(ctypes.byref(lb.lb_params(**kw)), None, ctypes.byref(h))
         assert rc == code, (bad, rc)
         assert L.lb_last_error(None)
+
+
+def test_library_stiffness_table_matches_oracle():
+    """The table the kernels interpolate (host code of the library, no GPU) against the oracle's
+    independent Bessel functions and k(P) inversion (Eq. Pk, App. B)."""
+    import numpy as np
+    import oracle as O
+    from paper_2209_14889_gb300 import lb
+    tab = lb.stiffness_table(0.99).astype(np.float64)
+    n = tab.shape[0] - 1
+    qcap = 0.99 ** 2
+    assert abs(tab[0, 0] - 0.5) < 1e-7 and abs(tab[0, 1] - 1.0 / 24) < 1e-8
+    for i in list(range(1, n + 1, 97)) + [n]:
+        q = qcap * i / n
+        k = O.k_of_P(np.sqrt(q))
+        I0 = O.bessel_i(0, k)
+        a2 = O.bessel_i(2, k) / I0 / q
+        a4 = O.bessel_i(4, k) / I0 / q ** 2
+        assert abs(tab[i, 0] - a2) < 2e-7 * a2, i
+        assert abs(tab[i, 1] - a4) < 2e-7 * a4, i

@@ -176,8 +176,52 @@ def test_bitwise_deterministic():
 
 
 def test_cfg2_full_size_few_steps():
-    """The 1024^2 workload (ring of 256 nodes, pull at 30 degrees) for 3 steps, every field."""
+    """The 1024^2 workload (ring of 256 nodes, pull at 30 degrees) for 3 steps, every field, with
+    both lattice kernels."""
+    lb = _gpu()
     w = W.cfg2()
-    got, ref = run_both(w, 3)
+    got, ref = run_both(w, 3, key="cfg2_3")
     check_fields(got, ref)
     check_nodes(got, ref, w)
+    sw = _run_gpu(w, 3, lb.LB_KERNEL_SWEEP)
+    check_fields(sw, ref)
+    check_nodes(sw, ref, w)
+
+
+def _run_gpu(w, steps, kernel):
+    lb = _gpu()
+    s = lb.Solver.from_workload(w)
+    s.set_kernel(kernel)
+    s.step(steps)
+    s.sync()
+    out = dict(fields=s.fields(), series=s.series(), X=s.nodes())
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,centre", [(256, 48, (3.0, 45.5)), (260, 36, (130.2, 17.7)),
+                                          (512, 64, (251.3, 33.0))])
+def test_sweep_kernel_matches_tile_kernel_and_oracle(nx, ny, centre):
+    """The column-strip sweep kernel against the tile kernel (same per-cell arithmetic) and the
+    oracle, on lattices whose ring crosses strip, chunk and periodic boundaries."""
+    lb = _gpu()
+    w = W.small(nx, ny, n_nodes=24, radius=4.0, centre=centre, steps=60)
+    sw = _run_gpu(w, 60, lb.LB_KERNEL_SWEEP)
+    ti = _run_gpu(w, 60, lb.LB_KERNEL_TILE)
+    for k in ti["fields"]:
+        assert rel_l2(sw["fields"][k], ti["fields"][k]) <= 1e-6, k
+    assert np.allclose(sw["series"], ti["series"], rtol=1e-6, atol=1e-9)
+    sim = O.Sim.from_workload(w)
+    sim.step(60, every=10)
+    ref = dict(fields=sim.fields(), series=np.array(sim.series), X=sim.X.copy())
+    check_fields(sw, ref)
+    check_nodes(sw, ref, w)
+    check_series(sw, ref, 1)
+
+
+def test_sweep_kernel_rejects_ineligible_lattice():
+    lb = _gpu()
+    s = lb.Solver.from_workload(W.make(64, 64, rings=[], noise_amp=0.0))
+    with pytest.raises(lb.LBError):
+        s.set_kernel(lb.LB_KERNEL_SWEEP)
+    s.close()
