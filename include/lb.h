@@ -41,8 +41,10 @@ extern "C" {
 #define LB_ESTATE (-7)      /* call out of order (e.g. lb_step before lb_init_fields)    */
 #define LB_ETIMEOUT (-8)    /* a bounded wait inside a kernel gave up (results invalid)  */
 
-/* Storage precision of the lattice state. */
-#define LB_FP32 0
+/* Storage precision of the lattice state (arithmetic is FP32 in both). */
+#define LB_FP32 0           /* 14 FP32 planes: 112 B per cell and step                          */
+#define LB_FP16_BF16 1      /* populations FP16 as (h_n - w_n rho0) 2^12 / w_n, sigma^p BF16,
+                               P - P_ref FP16; stochastic rounding on store: 56 B per cell-step  */
 
 /* Field identifiers for lb_readout / lb_write_field. */
 #define LB_FIELD_DRHO 0     /* rho - rho0 of the current state (readout only)           */
@@ -67,7 +69,7 @@ typedef struct lb_params {
     double P_cap;                   /* cap on |P| when solving Eq. Pk (0.99)                  */
     double director_angle;          /* initial director angle theta_d (radians)               */
     int32_t ericksen;               /* 1: include f^E in the body force                        */
-    int32_t precision;              /* LB_FP32                                                 */
+    int32_t precision;              /* LB_FP32 or LB_FP16_BF16                                 */
     int32_t readout_every;          /* record readouts when t % readout_every == 0 (10)       */
     int32_t max_samples;            /* capacity of the readout ring buffer (rows)             */
 } lb_params;

@@ -1,4 +1,6 @@
 // lb_api.cu -- the C ABI declared in include/lb.h: handle, validation, device buffers, launches.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,7 +24,8 @@ struct lb_handle {
     Phys ph;
     double eta_p = 0.0;
     long long plane = 0;
-    float* state[2] = {nullptr, nullptr};   // N_PLANES planes each
+    void* state[2] = {nullptr, nullptr};    // N_PLANES planes each (FP32, or 2-byte in LB_FP16_BF16)
+    int esz = 4;                            // bytes per stored value
     int cur = 0;
     float2* lut = nullptr;
     Ctl* ctl = nullptr;
@@ -115,6 +118,7 @@ FusedArgs fused_args(lb_handle* h)
     FusedArgs a;
     a.src = h->state[h->cur];
     a.dst = h->state[h->cur ^ 1];
+    a.prec = h->p.precision == LB_FP32 ? 0 : 1;
     a.plane = h->plane;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
@@ -173,16 +177,70 @@ void cached_lut(double P_cap, std::vector<float>& out)
     out = it->second;
 }
 
-// dst = src + c (the stored polarisation is dP = P - P_ref)
-__global__ void k_shift(float* dst, const float* src, float c, long long n)
+// Plane conversions between the stored form and FP32 values: v = stored * scale + shift.
+// kind 0: FP32 plane, 1: FP16 plane (scaled populations), 2: BF16 plane.
+__global__ void k_plane_to_f32(float* dst, const void* src, int kind, float scale, float shift, long long n)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i] + c;
+    if (i >= n) return;
+    float v;
+    if (kind == 0) v = static_cast<const float*>(src)[i];
+    else if (kind == 1) v = __half2float(static_cast<const __half*>(src)[i]);
+    else v = __bfloat162float(static_cast<const __nv_bfloat16*>(src)[i]);
+    dst[i] = v * scale + shift;
 }
 
-cudaError_t shift(float* dst, const float* src, float c, long long n, cudaStream_t s)
+// stored = (v - shift) * scale, round to nearest (initial and user-written fields)
+__global__ void k_f32_to_plane(void* dst, const float* src, int kind, float scale, float shift, long long n)
 {
-    k_shift<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, src, c, n);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = (src[i] - shift) * scale;
+    if (kind == 0) static_cast<float*>(dst)[i] = v;
+    else if (kind == 1) static_cast<__half*>(dst)[i] = __float2half_rn(v);
+    else static_cast<__nv_bfloat16*>(dst)[i] = __float2bfloat16_rn(v);
+}
+
+// stored plane p of buffer b: base pointer, kind, and the (scale, shift) that maps it to the
+// physical value (populations: d_n; sigma; P = dP + P_ref)
+struct PlaneInfo {
+    void* ptr;
+    int kind;
+    float scale, shift;
+};
+
+PlaneInfo plane_info(const lb_handle* h, int b, int plane)
+{
+    PlaneInfo pi;
+    const size_t N = (size_t)h->plane;
+    pi.ptr = static_cast<char*>(h->state[b]) + (size_t)h->esz * plane * N;
+    const bool lp = h->p.precision != LB_FP32;
+    pi.kind = !lp ? 0 : ((plane < PL_SXX || plane >= PL_PX) ? 1 : 2);   // FP16 pops and dP, BF16 sigma
+    pi.scale = 1.f;
+    pi.shift = 0.f;
+    if (lp && plane < PL_SXX) {
+        const double w = plane == 0 ? 4.0 / 9.0 : (plane < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        pi.scale = (float)(w / 4096.0);       // stored s_n = d_n 2^12 / w_n
+    }
+    if (plane == PL_PX) pi.shift = h->ph.prx;
+    if (plane == PL_PY) pi.shift = h->ph.pry;
+    return pi;
+}
+
+cudaError_t plane_to_f32(const lb_handle* h, int b, int plane, float* dst)
+{
+    const PlaneInfo pi = plane_info(h, b, plane);
+    const long long n = h->plane;
+    k_plane_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(dst, pi.ptr, pi.kind, pi.scale, pi.shift, n);
+    return cudaGetLastError();
+}
+
+cudaError_t f32_to_plane(const lb_handle* h, int b, int plane, const float* src)
+{
+    const PlaneInfo pi = plane_info(h, b, plane);
+    const long long n = h->plane;
+    k_f32_to_plane<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(pi.ptr, src, pi.kind, 1.f / pi.scale,
+                                                                      pi.shift, n);
     return cudaGetLastError();
 }
 
@@ -197,7 +255,8 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     const lb_params& p = *pin;
     if (p.nx < 8 || p.ny < 8) return fail(nullptr, LB_EINVAL, "nx, ny must be >= 8");
     if ((long long)p.nx * p.ny > (1LL << 31)) return fail(nullptr, LB_EINVAL, "lattice too large");
-    if (p.precision != LB_FP32) return fail(nullptr, LB_EINVAL, "unsupported precision %d", p.precision);
+    if (p.precision != LB_FP32 && p.precision != LB_FP16_BF16)
+        return fail(nullptr, LB_EINVAL, "unsupported precision %d", p.precision);
     if (!(p.tau > 0.5) || !(p.rho0 > 0.0)) return fail(nullptr, LB_EINVAL, "need tau > 1/2, rho0 > 0");
     if (!(p.P_cap > 0.0 && p.P_cap < 1.0)) return fail(nullptr, LB_EINVAL, "need 0 < P_cap < 1");
     if (p.readout_every < 1 || p.max_samples < 1) return fail(nullptr, LB_EINVAL, "bad readout settings");
@@ -252,7 +311,8 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
         lb_destroy(h);
         return code;
     };
-    const size_t state_bytes = sizeof(float) * N_PLANES * (size_t)h->plane;
+    h->esz = p.precision == LB_FP32 ? 4 : 2;
+    const size_t state_bytes = (size_t)h->esz * N_PLANES * (size_t)h->plane;
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&h->state[b], state_bytes);
         if (e != cudaSuccess) { rc = cuda_fail(nullptr, e, "cudaMalloc(state)"); return bail(rc); }
@@ -291,19 +351,33 @@ int lb_init_fields(lb_handle* h, const double* noise)
     const lb_params& p = h->p;
     const size_t N = (size_t)h->plane;
     std::vector<float> buf(N);
-    float* S = h->state[h->cur];
-    // populations at rest (shifted form: zero) and sigma = 0
-    CK(h, cudaMemsetAsync(S, 0, sizeof(float) * (PL_PY + 1) * N, h->stream));
+    void* S = h->state[h->cur];
+    // populations at rest (shifted form: zero) and sigma = 0 (zero bits in every storage form)
+    CK(h, cudaMemsetAsync(S, 0, (size_t)h->esz * N_PLANES * N, h->stream));
     // stored: dP = P - P_ref with P = P_eq (cos theta_d, sin theta_d) + noise (FP64 here)
     const double Peq = (p.alpha < 0.0 && p.beta > 0.0) ? std::sqrt(-p.alpha / p.beta) : 0.0;
-    for (int c = 0; c < 2; ++c) {
+    float* tmp = nullptr;
+    CK(h, cudaMalloc(&tmp, sizeof(float) * N));
+    int rc = LB_OK;
+    for (int c = 0; c < 2 && rc == LB_OK; ++c) {
         const double base = Peq * (c == 0 ? std::cos(p.director_angle) : std::sin(p.director_angle));
         const double ref = c == 0 ? h->ph.prx : h->ph.pry;
+        // P itself goes through f32_to_plane, which subtracts P_ref; the deviation is formed in
+        // FP64 here and P_ref added back in FP32 only where the result is exact enough
         for (size_t i = 0; i < N; ++i) buf[i] = (float)((base - ref) + (noise ? noise[c * N + i] : 0.0));
-        CK(h, cudaMemcpyAsync(S + (PL_PX + c) * N, buf.data(), sizeof(float) * N, cudaMemcpyHostToDevice,
-                              h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, buf.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) {
+            // dP planes directly (no shift: buf already holds P - P_ref)
+            const PlaneInfo pi = plane_info(h, h->cur, PL_PX + c);
+            k_f32_to_plane<<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(pi.ptr, tmp, pi.kind, 1.f, 0.f,
+                                                                             (long long)N);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "lb_init_fields");
     }
+    cudaFree(tmp);
+    if (rc != LB_OK) return rc;
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     h->t = 0;
     h->fields_ready = true;
@@ -459,20 +533,17 @@ int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst
     }
     if (bytes != sizeof(float) * N) return fail(h, LB_EINVAL, "bytes mismatch");
     const float* srcp = nullptr;
+    if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
     if (field >= LB_FIELD_DRHO && field <= LB_FIELD_UY) {
-        if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
         FusedArgs fa = fused_args(h);
         CK(h, launch_fused(fa, MODE_MOMENTS, h->stream, nullptr));
         srcp = h->moments + (size_t)(field - LB_FIELD_DRHO) * N;
-    } else if (field == LB_FIELD_PX || field == LB_FIELD_PY) {
-        if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
-        const float* st = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
-        CK(h, shift(h->moments, st, field == LB_FIELD_PX ? h->ph.prx : h->ph.pry, (long long)N, h->stream));
+    } else if (field >= LB_FIELD_SXX && field <= LB_FIELD_PY) {
+        CK(h, plane_to_f32(h, h->cur, PL_SXX + field - LB_FIELD_SXX, h->moments));
         srcp = h->moments;
-    } else if (field >= LB_FIELD_SXX && field <= LB_FIELD_SXY) {
-        srcp = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
     } else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) {
-        srcp = h->state[h->cur] + (size_t)(field - LB_FIELD_POP0) * N;
+        CK(h, plane_to_f32(h, h->cur, field - LB_FIELD_POP0, h->moments));
+        srcp = h->moments;
     } else {
         return fail(h, LB_EINVAL, "unknown field %d", field);
     }
@@ -491,11 +562,10 @@ int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, i
     else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) plane = field - LB_FIELD_POP0;
     else return fail(h, LB_EINVAL, "field %d is not writable", field);
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    float* dstp = h->state[h->cur] + plane * N;
-    CK(h, cudaMemcpyAsync(dstp, src, bytes, kind, h->stream));
-    if (plane == PL_PX || plane == PL_PY)
-        CK(h, shift(dstp, dstp, plane == PL_PX ? -h->ph.prx : -h->ph.pry, (long long)N, h->stream));
-    if (!src_is_device) CK(h, cudaStreamSynchronize(h->stream));
+    if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
+    CK(h, cudaMemcpyAsync(h->moments, src, bytes, kind, h->stream));
+    CK(h, f32_to_plane(h, h->cur, (int)plane, h->moments));
+    CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 
@@ -592,13 +662,15 @@ int lb_set_kernel(lb_handle* h, int32_t kernel)
 {
     if (!h) return fail(nullptr, LB_EINVAL, "null handle");
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_SWEEP) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == LB_KERNEL_SWEEP && h->p.precision != LB_FP32)
+        return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
     if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))
         return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");
     h->kernel = kernel;
     return LB_OK;
 }
 
-double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * sizeof(float) : 0.0; }
+double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * h->esz : 0.0; }
 
 }  // extern "C"
 
@@ -660,8 +732,7 @@ int lb_readout_noalloc(lb_handle* h, int32_t field, void* dst, size_t bytes, int
         CK(h, launch_fused(fa, MODE_MOMENTS, h->stream, nullptr));
         srcp = scratch + (size_t)(field - LB_FIELD_DRHO) * N;
     } else if (field == LB_FIELD_PX || field == LB_FIELD_PY) {
-        const float* st = h->state[h->cur] + (size_t)(PL_SXX + field - LB_FIELD_SXX) * N;
-        CK(h, shift(scratch, st, field == LB_FIELD_PX ? h->ph.prx : h->ph.pry, (long long)N, h->stream));
+        CK(h, plane_to_f32(h, h->cur, PL_SXX + field - LB_FIELD_SXX, scratch));
         srcp = scratch;
     } else {
         return fail(h, LB_EINVAL, "lb_readout_noalloc: field %d is not one of DRHO, UX, UY, PX, PY", field);

@@ -61,7 +61,7 @@ constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
 static_assert(OFF_N % 4 == 0 && OFF_NF % 2 == 0 && OFF_RED % 2 == 0, "shared-memory alignment");
 static_assert(SMEM_BYTES <= 75 * 1024, "three CTAs per SM");
 
-template <int MODE>
+template <int MODE, int PREC>
 __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 {
     extern __shared__ __align__(16) float sm[];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     const long long NP = a.plane;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const Phys ph = a.ph;
-    const float* __restrict__ src = a.src;
+    const void* __restrict__ src = a.src;
 
     for (int i = tid; i < R4W; i += NT) sXi[i] = wrapn(x0 - 4 + i, nx);
     for (int i = tid; i < R4H; i += NT) sYi[i] = wrapn(y0 - 4 + i, ny);
@@ -97,15 +97,15 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     for (int i = tid; i < R4; i += NT) {
         const int ly = i / R4W, lx = i - ly * R4W;
         const long long g = (long long)sYi[ly] * nx + sXi[lx];
-        sP[i] = __ldg(src + PL_PX * NP + g);
-        sP[R4 + i] = __ldg(src + PL_PY * NP + g);
+        sP[i] = ld_fld<PREC>(src, NP, PL_PX, g);
+        sP[R4 + i] = ld_fld<PREC>(src, NP, PL_PY, g);
     }
     for (int i = tid; i < R3; i += NT) {
         const int ly = i / R3W, lx = i - ly * R3W;
         const long long g = (long long)sYi[ly + 1] * nx + sXi[lx + 1];
-        sS[i] = __ldg(src + PL_SXX * NP + g);
-        sS[R3 + i] = __ldg(src + PL_SYY * NP + g);
-        sS[2 * R3 + i] = __ldg(src + PL_SXY * NP + g);
+        sS[i] = ld_fld<PREC>(src, NP, PL_SXX, g);
+        sS[R3 + i] = ld_fld<PREC>(src, NP, PL_SYY, g);
+        sS[2 * R3 + i] = ld_fld<PREC>(src, NP, PL_SXY, g);
     }
     __syncthreads();
 
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         const long long g = (long long)sYi[ly + 2] * nx + sXi[lx + 2];
         float d[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) d[n] = __ldg(src + n * NP + g);
+        for (int n = 0; n < 9; ++n) d[n] = ld_pop<PREC>(src, NP, n, g);
         float drho, ux, uy;
         moments(ph, d, Fx, Fy, drho, ux, uy);
         sM[i] = drho;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     const long long t = a.ctl->t;
     const bool readout = (t % a.every) == 0;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    float* __restrict__ dst = a.dst;
+    void* __restrict__ dst = a.dst;
     // D2Q9 (Sec. II A): c_n and w_n, n = 0..8
     const int c_cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int c_cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -298,13 +298,16 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         {
             float dn[9], D[9];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) dn[n] = __ldg(src + n * NP + g);
+            for (int n = 0; n < 9; ++n) dn[n] = ld_pop<PREC>(src, NP, n, g);
             collide(ph, dn, drho, ux, uy, Fx, Fy, D);
+            long long gd[9];
+            float out[9];
 #pragma unroll
             for (int n = 0; n < 9; ++n) {
-                const long long gd = (long long)sYi[ly + 4 + c_cy[n]] * nx + sXi[lx + 4 + c_cx[n]];
-                dst[n * NP + gd] = dn[n] + D[n];
+                gd[n] = (long long)sYi[ly + 4 + c_cy[n]] * nx + sXi[lx + 4 + c_cx[n]];
+                out[n] = dn[n] + D[n];
             }
+            st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
             if (readout) {
                 float dsum = 0.f;
                 double jxs = 0.0, jys = 0.0;
@@ -338,9 +341,10 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
             const int j3 = (ly + 3) * R3W + lx + 3;
             const int j4 = (ly + 4) * R4W + lx + 4;
             const float y0s[5] = {sS[j3], sS[R3 + j3], sS[2 * R3 + j3], sP[j4], sP[R4 + j4]};
+            float ynew[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c)
-                dst[(PL_SXX + c) * NP + g] = y0s[c] + 0.5f * (sR[c * R0 + i] + r[c]);
+            for (int c = 0; c < 5; ++c) ynew[c] = y0s[c] + 0.5f * (sR[c * R0 + i] + r[c]);
+            st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
         }
 
         // u(t) (and f^p(t) on readout steps) on the work box of every ring containing the cell
@@ -386,29 +390,29 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 
 int fused_ctas(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
+template <int MODE, int PREC>
+static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s)
+{
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<MODE, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_fused<MODE, PREC><<<grid, NT, SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas)
 {
-    static bool attr_done[2] = {false, false};
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
     if (grid_ctas) *grid_ctas = grid.x * grid.y;
-    if (mode == MODE_STEP) {
-        if (!attr_done[0]) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused<MODE_STEP>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            attr_done[0] = true;
-        }
-        k_fused<MODE_STEP><<<grid, NT, SMEM_BYTES, s>>>(a);
-    } else {
-        if (!attr_done[1]) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused<MODE_MOMENTS>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-            if (e != cudaSuccess) return e;
-            attr_done[1] = true;
-        }
-        k_fused<MODE_MOMENTS><<<grid, NT, SMEM_BYTES, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (a.prec == PREC_FP32)
+        return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_FP32>(a, grid, s)
+                                 : launch_one<MODE_MOMENTS, PREC_FP32>(a, grid, s);
+    return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_LP>(a, grid, s)
+                             : launch_one<MODE_MOMENTS, PREC_LP>(a, grid, s);
 }
 
 }  // namespace vlb

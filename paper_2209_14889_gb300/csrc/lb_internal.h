@@ -58,8 +58,9 @@ struct Ctl {
 };
 
 struct FusedArgs {
-    const float* src;            // state at t (N_PLANES planes)
-    float* dst;                  // state at t + 1
+    const void* src;             // state at t (N_PLANES planes: FP32, or FP16/BF16 in the precision form)
+    void* dst;                   // state at t + 1
+    int prec;                    // 0: FP32 state, 1: FP16 populations + BF16 sigma, dP
     long long plane;             // nx * ny
     int nx, ny;
     Phys ph;

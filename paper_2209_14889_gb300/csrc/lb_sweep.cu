@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
     const int e0 = yc0 - 2 * WARM;        // row of E at iteration 0
     const int K = WARM + (yend - yc0 + 1) / 2;
     const Phys ph = a.ph;
-    const float* __restrict__ src = a.src;
-    float* __restrict__ dst = a.dst;
+    const float* __restrict__ src = static_cast<const float*>(a.src);   // FP32 state only
+    float* __restrict__ dst = static_cast<float*>(a.dst);
     const int gx = wrapn(xs + c, nx);     // this thread's column
     const bool out_col = (c >= 4 && c < 4 + TW && x0 + c - 4 < nx);
     const long long t = a.ctl->t;

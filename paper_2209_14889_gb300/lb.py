@@ -18,6 +18,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EUNSTABLE, LB_EBODY, LB
     0, -1, -2, -3, -4, -5, -6, -7
 LB_ETIMEOUT = -8
 LB_FP32 = 0
+LB_FP16_BF16 = 1
 LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP = 0, 1, 2
 FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
 LB_FIELD_POP0 = 8

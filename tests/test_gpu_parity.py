@@ -225,3 +225,80 @@ def test_sweep_kernel_rejects_ineligible_lattice():
     with pytest.raises(lb.LBError):
         s.set_kernel(lb.LB_KERNEL_SWEEP)
     s.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Precision form: FP16 populations, BF16 sigma and P, FP32 arithmetic, stochastic rounding
+# ------------------------------------------------------------------------------------------
+
+def _lp_workload(steps, side=256):
+    # a periodic lattice with one ring of the 4096^2 precision workload's kind (128 nodes,
+    # radius 12), pulled with 5e-4 at 35 degrees; relaxation 200 steps, D_p 0.1
+    return W.make(side, side, rings=[W.ring(128, 12.0, (side / 2 + 0.3, side / 2 - 0.4), pull_force=5e-4,
+                                            pull_angle=math.radians(35))],
+                  seed=3, steps=steps, every=10, lambda_steps=200.0, Dp=0.1)
+
+
+def _run_prec(w, steps, precision):
+    lb = _gpu()
+    s = lb.Solver.from_workload(w, precision=precision)
+    s.step(steps)
+    s.sync()
+    out = dict(fields=s.fields(), series=s.series(), X=s.nodes())
+    s.close()
+    return out
+
+
+def test_precision_form_restoring_force_within_1pct_of_fp32():
+    """2000 steps on 256^2: the FP16/BF16 form's restoring-force series within 1 % (relative L2)
+    of the FP32 step on the same GPU; mass stays put (unbiased stochastic rounding)."""
+    lb = _gpu()
+    w = _lp_workload(2000)
+    lp = _run_prec(w, 2000, lb.LB_FP16_BF16)
+    f32 = _run_prec(w, 2000, lb.LB_FP32)
+    e = rel_l2(lp["series"][:, 6:8], f32["series"][:, 6:8])
+    errs = {k: rel_l2(lp["fields"][k], f32["fields"][k]) for k in f32["fields"]}
+    print("F_rest LP vs FP32 %.2e; fields %s" % (e, {k: "%.1e" % v for k, v in errs.items()}))
+    assert e <= 1e-2
+    assert np.abs(lp["series"][:, 1]).max() < 1e-4 * 256
+
+
+def test_precision_form_vs_oracle():
+    """300 steps on 128^2 against the FP64 oracle: restoring force within 1 %, fields within
+    3e-2 (FP16 populations and P, BF16 sigma, rounded stochastically)."""
+    lb = _gpu()
+    w = _lp_workload(300, side=128)
+    lp = _run_prec(w, 300, lb.LB_FP16_BF16)
+    sim = O.Sim.from_workload(w)
+    sim.step(300, every=10)
+    ref = np.array(sim.series)
+    e = rel_l2(lp["series"][:, 6:8], ref[:, 6:8])
+    rf = sim.fields()
+    errs = {k: rel_l2(lp["fields"][k], rf[k]) for k in rf}
+    print("F_rest LP vs FP64 %.2e; fields %s" % (e, {k: "%.1e" % v for k, v in errs.items()}))
+    assert e <= 1e-2
+    for k, v in errs.items():
+        assert v <= 3e-2, (k, v)
+
+
+def test_precision_form_round_trip_and_determinism():
+    lb = _gpu()
+    w = _lp_workload(0)
+    outs = []
+    for _ in range(2):
+        s = lb.Solver.from_workload(w, precision=lb.LB_FP16_BF16)
+        rng = np.random.default_rng(0)
+        a = (1e-4 * rng.standard_normal((256, 256))).astype(np.float32)
+        s.write_field("sxy", a)
+        back = s.readout("sxy", device=False)
+        assert np.abs(back - a).max() <= 2 ** -8 * np.abs(a).max()    # BF16 round to nearest
+        s.write_field("Py", a)
+        assert np.abs(s.readout("Py", device=False) - a).max() <= 2 ** -11 * np.abs(a).max()  # FP16
+        p = s.readout("Px", device=False)
+        assert abs(float(np.median(p)) - np.sqrt(0.9)) < 0.01
+        s.step(25)
+        s.sync()
+        outs.append((s.readout("pop5", device=False), s.readout("Py", device=False), s.series()))
+        s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
