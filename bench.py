@@ -170,6 +170,63 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def measure_forms(args, lb, W, torch):
+    """The 4096^2 workload with 16 rings (128 nodes, radius 12, seeded positions and pull angles)
+    in the FP32 and the FP16/BF16 storage forms (state 0.94-1.9 GB, larger than L2, so no flush),
+    and the precision form's restoring-force error against the FP32 step (256^2, 2000 steps)."""
+    import numpy as np
+    peaks, _ = measured_peaks()
+    out = {"workload": "4096x4096 periodic, 16 rings of 128 nodes (radius 12, seeded), pull 5e-4 "
+                       "at seeded angles in [0, 90] deg, D_p 0.1, relaxation 200 steps"}
+    w = W.cfg3()
+    cells = w["nx"] * w["ny"]
+    steps = max(3, min(args.steps, 10))
+    for name, prec in [("fp32", lb.LB_FP32), ("fp16_bf16", lb.LB_FP16_BF16)]:
+        s = lb.Solver.from_workload(w, precision=prec)
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            s.step(LB_STEPS_PER_STEP)
+        s.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            ev[k][0].record(stream)
+            s.step(LB_STEPS_PER_STEP)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        s.timing(True)
+        for k in range(steps):
+            s.step(LB_STEPS_PER_STEP)
+        kt = s.kernel_time()
+        s.timing(False)
+        fused_s = kt["fused_ms"] * 1e-3 / max(kt["fused_launches"], 1)
+        gbs = s.bytes_per_cell * cells / fused_s / 1e9
+        out[name] = {"value": cells * LB_STEPS_PER_STEP * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                     "bytes_per_cell_step": s.bytes_per_cell, "fused_mean_us": fused_s * 1e6,
+                     "node_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1),
+                     "roofline_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "steps": steps}
+        s.sync()
+        s.close()
+    # restoring-force error of the precision form against the FP32 step on this GPU
+    wr = W.make(256, 256, rings=[W.ring(128, 12.0, (128.3, 127.6), pull_force=5e-4,
+                                        pull_angle=math.radians(35))],
+                seed=3, steps=2000, every=10, lambda_steps=200.0, Dp=0.1)
+    series = {}
+    for name, prec in [("fp32", lb.LB_FP32), ("fp16_bf16", lb.LB_FP16_BF16)]:
+        s = lb.Solver.from_workload(wr, precision=prec)
+        s.step(2000)
+        s.sync()
+        series[name] = s.series()[:, 6:8]
+        s.close()
+    d = series["fp16_bf16"] - series["fp32"]
+    out["fp16_bf16"]["frest_err_vs_fp32"] = {
+        "value": float(np.linalg.norm(d) / np.linalg.norm(series["fp32"])),
+        "workload": "256x256, one ring of 128 nodes, 2000 steps, relative L2 over 200 readouts"}
+    return out
+
+
 def cpu_baseline_sample():
     """The oracle as it stands on one host core, on a bounded sample of the workload: one LB
     time step of the 1024 x 1024 lattice."""
@@ -235,10 +292,9 @@ def main():
         s.step(LB_STEPS_PER_STEP)
     s.sync()
 
-    # timed steps (device time), fused-kernel events inside
+    # timed steps (device time; lattice and node kernels overlap by programmatic dependent launch)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    s.timing(True)
     with Clocks(local) as clk:
         barrier()
         for k in range(args.steps):
@@ -248,9 +304,16 @@ def main():
             ev[k][1].record(stream)
         barrier()
     s.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    # per-kernel durations for the roofline: the same steps again with events around each
+    # launch (which serialises the kernels), L2 flushed between steps as above
+    s.timing(True)
+    for k in range(args.steps):
+        flush.zero_()
+        s.step(LB_STEPS_PER_STEP)
+    s.sync()
     kt = s.kernel_time()
     s.timing(False)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -307,6 +370,8 @@ def main():
 
     rc = lb.lib().lb_sync(s.h)
     s.close()
+    del flush
+    forms = None if world > 1 else measure_forms(args, lb, W, torch)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -323,7 +388,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": 2 * LB_STEPS_PER_STEP * args.steps,
+            "kernel_timing": "roofline durations from a second pass with events around each launch",
             "frest_err_vs_fp64": {"value": frest_err, "workload": "64x64, 200 steps, 20 readouts"},
+            "forms": forms,
             "status": int(rc)}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -46,6 +46,12 @@ struct lb_handle {
     float2* node_force = nullptr;
     float* ubox = nullptr;
     float* fpbox = nullptr;
+    int n_node_ctas = 1;
+    int2* node_work = nullptr;
+    int* ring_cta0 = nullptr;
+    int* ring_ctas = nullptr;
+    unsigned* ring_tickets = nullptr;
+    double* node_partials = nullptr;
     long long box_floats = 0;
     bool fields_ready = false;
     long long t = 0;
@@ -99,6 +105,12 @@ void free_rings(lb_handle* h)
     dfree(h->node_force);
     dfree(h->ubox);
     dfree(h->fpbox);
+    dfree(h->node_work);
+    dfree(h->ring_cta0);
+    dfree(h->ring_ctas);
+    dfree(h->ring_tickets);
+    dfree(h->node_partials);
+    h->n_node_ctas = 1;
     h->n_rings = h->n_total = 0;
     h->row_len = 6;
 }
@@ -159,6 +171,12 @@ NodeArgs node_args(lb_handle* h, int advance)
     a.nx = h->p.nx;
     a.ny = h->p.ny;
     a.advance = advance;
+    a.n_ctas = h->n_node_ctas;
+    a.work = h->node_work;
+    a.ring_cta0 = h->ring_cta0;
+    a.ring_ctas = h->ring_ctas;
+    a.ring_tickets = h->ring_tickets;
+    a.node_partials = h->node_partials;
     return a;
 }
 
@@ -341,6 +359,16 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
         rc = cuda_fail(nullptr, e, "cudaMalloc(series)");
         return bail(rc);
     }
+    {
+        const int2 w0 = make_int2(-1, 0);
+        if ((e = cudaMalloc(&h->node_work, sizeof(int2))) != cudaSuccess ||
+            (e = cudaMemcpy(h->node_work, &w0, sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMalloc(&h->node_partials, sizeof(double) * 8)) != cudaSuccess) {
+            rc = cuda_fail(nullptr, e, "cudaMalloc(node work)");
+            return bail(rc);
+        }
+        h->n_node_ctas = 1;
+    }
     *out = h;
     return LB_OK;
 }
@@ -430,7 +458,10 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
         d.l_eq = g.l_eq;
         d.pull_x = g.pull_force * std::cos(g.pull_angle) / g.n_nodes;
         d.pull_y = g.pull_force * std::sin(g.pull_angle) / g.n_nodes;
-        d.box_x0 = d.box_y0 = 0;
+        // until the first node-kernel pass the box is empty; its origin is node 0's cell, the
+        // reference from which the node kernel measures the ring's extent
+        d.box_x0 = (int)std::floor(X[off].x);
+        d.box_y0 = (int)std::floor(X[off].y);
         d.box_w = d.box_h = 0;
         d.cap_w = cw;
         d.cap_h = chh;
@@ -442,6 +473,25 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
     h->n_total = off;
     h->row_len = 6 + 4 * n_rings;
     h->box_floats = box_off;
+    // node-kernel work: NB owned nodes per CTA (one CTA with no ring when there are no rings)
+    std::vector<int2> work;
+    std::vector<int> cta0(std::max(n_rings, 1)), nctas(std::max(n_rings, 1));
+    for (int r = 0; r < n_rings; ++r) {
+        cta0[r] = (int)work.size();
+        for (int k0 = 0; k0 < rd[r].n_nodes; k0 += NB) work.push_back(make_int2(r, k0));
+        nctas[r] = (int)work.size() - cta0[r];
+    }
+    if (work.empty()) work.push_back(make_int2(-1, 0));
+    h->n_node_ctas = (int)work.size();
+    CK(h, cudaMalloc(&h->node_work, sizeof(int2) * work.size()));
+    CK(h, cudaMalloc(&h->ring_cta0, sizeof(int) * cta0.size()));
+    CK(h, cudaMalloc(&h->ring_ctas, sizeof(int) * nctas.size()));
+    CK(h, cudaMalloc(&h->ring_tickets, sizeof(unsigned) * nctas.size()));
+    CK(h, cudaMalloc(&h->node_partials, sizeof(double) * 8 * work.size()));
+    CK(h, cudaMemcpy(h->node_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->ring_cta0, cta0.data(), sizeof(int) * cta0.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->ring_ctas, nctas.data(), sizeof(int) * nctas.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->ring_tickets, 0, sizeof(unsigned) * nctas.size()));
     if (n_rings > 0) {
         CK(h, cudaMalloc(&h->rings, sizeof(RingDev) * n_rings));
         CK(h, cudaMalloc(&h->X, sizeof(double2) * off));
@@ -470,6 +520,7 @@ int lb_step(lb_handle* h, int64_t n)
     if (!h) return fail(nullptr, LB_EINVAL, "null handle");
     if (n < 0) return fail(h, LB_EINVAL, "n < 0");
     if (!h->fields_ready) return fail(h, LB_ESTATE, "lb_init_fields not called");
+    if (!h->node_work) return fail(h, LB_ESTATE, "no valid body: call lb_set_body again");
     for (int64_t k = 0; k < n; ++k) {
         FusedArgs fa = fused_args(h);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -481,11 +532,14 @@ int lb_step(lb_handle* h, int64_t n)
         // LB_KERNEL_AUTO takes the tile kernel: measured faster than the sweep on GB300 so far
         // (1024^2: 84 vs 121 us per launch; the sweep stalls on its per-row barriers)
         const bool sweep = h->kernel == LB_KERNEL_SWEEP;
+        // consecutive lattice and node kernels overlap by programmatic dependent launch, except
+        // when per-kernel timing brackets each launch with events
+        const bool pdl = !h->timing;
         if (sweep) {
             CK(h, launch_sweep(fa, h->sweep_chunk, h->stream));
             h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
         } else {
-            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials));
+            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl));
         }
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
         if (h->timing) {
@@ -493,7 +547,7 @@ int lb_step(lb_handle* h, int64_t n)
             e1 = ev_get(h->ev_nodes, h->ev_nodes_used);
             if (e0) cudaEventRecord(e0, h->stream);
         }
-        CK(h, launch_nodes(node_args(h, 1), h->stream));
+        CK(h, launch_nodes(node_args(h, 1), h->stream, pdl && !sweep));
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
         h->cur ^= 1;
         h->t += 1;

@@ -48,6 +48,14 @@ __device__ __forceinline__ void lut_eval(const float* __restrict__ L, const Phys
     }
 }
 
+// Programmatic dependent launch (the lattice and node kernels of consecutive steps overlap):
+// pdl_wait blocks until the preceding kernel in the stream has completed and its writes are
+// visible; pdl_trigger lets the following kernel start its prologue.  Each kernel triggers only
+// after its own wait, so a kernel's prologue may read anything written two kernels back.
+// Both are no-ops for a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Stencil values of one component: centre, east (+x), west, north (+y), south.
 struct St {
     float c, e, w, n, s;

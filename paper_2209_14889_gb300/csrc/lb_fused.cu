@@ -126,6 +126,11 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         }
     }
 
+    // The state at t was written two kernels back; the node forces, ring boxes, step counter and
+    // readout buffers come from the node kernel just before this one.
+    pdl_wait();
+    pdl_trigger();
+
     // ---- IB: gather f_IB on the halo-2 region from the nodes of every ring near the tile ----
     // A node at cell c with fraction f sits at (c - o) + f relative to the region origin o; the
     // integer part is kept apart from the fraction so that kernel arguments stay exact in FP32.
@@ -282,8 +287,6 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
     // D2Q9 (Sec. II A): c_n and w_n, n = 0..8
     const int c_cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int c_cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    const float w9[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
-                         1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
     for (int i = tid; i < R0; i += NT) {
         const int ly = i / TX, lx = i - ly * TX;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 int fused_ctas(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
 template <int MODE, int PREC>
-static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s)
+static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s, bool pdl)
 {
     static bool attr_done = false;
     if (!attr_done) {
@@ -400,19 +403,28 @@ static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_fused<MODE, PREC><<<grid, NT, SMEM_BYTES, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_fused<MODE, PREC>, a);
 }
 
-cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas)
+cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl)
 {
     dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
     if (grid_ctas) *grid_ctas = grid.x * grid.y;
     if (a.prec == PREC_FP32)
-        return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_FP32>(a, grid, s)
-                                 : launch_one<MODE_MOMENTS, PREC_FP32>(a, grid, s);
-    return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_LP>(a, grid, s)
-                             : launch_one<MODE_MOMENTS, PREC_LP>(a, grid, s);
+        return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_FP32>(a, grid, s, pdl)
+                                 : launch_one<MODE_MOMENTS, PREC_FP32>(a, grid, s, false);
+    return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_LP>(a, grid, s, pdl)
+                             : launch_one<MODE_MOMENTS, PREC_LP>(a, grid, s, false);
 }
 
 }  // namespace vlb

@@ -78,9 +78,19 @@ struct FusedArgs {
     float* moments_out;          // MOMENTS mode: drho, ux, uy planes
 };
 
+// Node kernel geometry: NB owned nodes per CTA, NODE_THREADS >= NB + 4 threads.
+constexpr int NB = 60;
+constexpr int NODE_THREADS = 64;
+
 struct NodeArgs {
     int n_rings;
     RingDev* rings;
+    int n_ctas;                  // node-kernel CTAs (>= 1)
+    const int2* work;            // per CTA: (ring or -1, first owned node)
+    const int* ring_cta0;        // per ring: first CTA, number of CTAs
+    const int* ring_ctas;
+    unsigned* ring_tickets;      // per ring: arrival counter
+    double* node_partials;       // per CTA: F_rest (2), COM (2), box min/max (4)
     double2* X;                  // FP64 master node positions, wrapped into [0, n)
     int2* node_cell;
     float2* node_frac;
@@ -98,13 +108,13 @@ struct NodeArgs {
 };
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas);
+cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl = false);
 // column-strip sweep (lb_sweep.cu): eligibility, rows per CTA chunk, CTA count, launch
 bool sweep_eligible(int nx, int ny);
 int sweep_chunk(int nx, int ny, int n_sm);
 int sweep_ctas(int nx, int ny, int chunk);
 cudaError_t launch_sweep(const FusedArgs& a, int chunk, cudaStream_t s);
-cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s);
+cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s, bool pdl = false);
 int fused_ctas(int nx, int ny);
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };

@@ -9,19 +9,23 @@
 //     R' = R + (v(R) + v(R*))/2, v interpolated with the cosine kernel (FP32 weights);
 //   * Lagrangian forces of R' (Eq. Const: springs, angle terms, constant pull split over the
 //     nodes), gathered per node without atomics, and the work box of R' for the next step.
-// Node positions are kept in FP64 (O(N_nodes) data); the lattice kernel sees them as int32 cell +
-// FP32 fraction with FP32 forces.  The last CTA to finish advances the step counter.
+// Node positions are kept in FP64 (O(N_nodes) data) and advanced in FP64; the forces are
+// evaluated in FP32 except the spring extension, whose l^2 - l_eq^2 is formed in FP64 (FP64 is
+// a narrow unit on this GPU, so it is kept to a few operations per node).  The lattice kernel
+// sees the nodes as int32 cell + FP32 fraction with FP32 forces.  One CTA owns NB nodes of one
+// ring and recomputes the advance of HALO neighbours on each side, so no CTA waits for
+// another; the last CTA of a ring writes the ring's box and readouts, the last CTA overall the
+// lattice readouts and the step counter.
 #include <cuda_runtime.h>
 
+#include "lb_cell.cuh"
 #include "lb_internal.h"
 
 namespace vlb {
 
 namespace {
 
-constexpr int NTN = 256;
-constexpr int MAXN = 1024;
-constexpr int NW = NTN / 32;
+constexpr int HALO = 2;                       // neighbours whose advance a CTA recomputes
 
 // Node positions are kept in [0, n); one step moves a node by less than one cell, and offsets
 // between nodes of a ring are below n/2, so single conditional corrections replace fmod.
@@ -46,9 +50,17 @@ __device__ __forceinline__ int wrapi1(int i, int n)
     return i;
 }
 
-__device__ __forceinline__ float phi(float r)
+// The four cosine-kernel weights phi(f + 1), phi(f), phi(f - 1), phi(f - 2) of a node at
+// fraction f in [0, 1) (App. A): with c = cos(pi f / 2), s = sin(pi f / 2) they are
+// (1 - s)/4, (1 + c)/4, (1 + s)/4, (1 - c)/4 (quarter-period shifts of the cosine).
+__device__ __forceinline__ void phi4(float f, float* w)
 {
-    return fabsf(r) < 2.f ? 0.25f * (1.f + cospif(0.5f * r)) : 0.f;
+    float sn, cs;
+    sincospif(0.5f * f, &sn, &cs);
+    w[0] = 0.25f * (1.f - sn);
+    w[1] = 0.25f * (1.f + cs);
+    w[2] = 0.25f * (1.f + sn);
+    w[3] = 0.25f * (1.f - cs);
 }
 
 // Interpolate a 2-component box field at the position (X, Y) in [0, n); returns false if a
@@ -58,19 +70,20 @@ __device__ __forceinline__ bool interp_box(const float* __restrict__ box, const 
                                            float& vx, float& vy)
 {
     const int cx = (int)X, cy = (int)Y;              // X, Y >= 0
-    const float fx = (float)(X - cx), fy = (float)(Y - cy);
     const long long cap = (long long)R.cap_w * R.cap_h;
     const int ox = wrapi1(cx - 1 - bx0, nx), oy = wrapi1(cy - 1 - by0, ny);
     vx = 0.f;
     vy = 0.f;
     if (ox + 3 >= bw || oy + 3 >= bh) return false;   // the box never wraps onto itself
+    float wx[4], wy[4];
+    phi4((float)(X - cx), wx);
+    phi4((float)(Y - cy), wy);
     const float* p = box + R.box_off + (long long)oy * R.cap_w + ox;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float wy = phi(fy - (float)(j - 1));
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float w = phi(fx - (float)(i - 1)) * wy;
+            const float w = wx[i] * wy[j];
             vx += w * p[j * R.cap_w + i];
             vy += w * p[j * R.cap_w + i + cap];
         }
@@ -78,43 +91,50 @@ __device__ __forceinline__ bool interp_box(const float* __restrict__ box, const 
     return true;
 }
 
-// Fixed-order block sums of K doubles per thread; results valid in thread 0.
-template <int K>
-__device__ void block_sums(double (&v)[K], double* red)
+__device__ __forceinline__ int half_wrap(int d, int n)   // d in (-n, n) -> [-n/2, n/2)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (d >= n - n / 2) d -= n;
+    else if (d < -(n / 2)) d += n;
+    return d;
+}
+
+// Fixed-order sums over the warps of a CTA (K values per thread); result valid in thread 0.
+template <int K, class T>
+__device__ void cta_reduce(T (&v)[K], T* red, bool is_min)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const T u = __shfl_down_sync(0xffffffffu, v[k], o);
+            v[k] = is_min ? (u < v[k] ? u : v[k]) : v[k] + u;
+        }
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[k * NW + wid] = v[k];
+        for (int k = 0; k < K; ++k) red[k * 32 + wid] = v[k];
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < NW; ++w) s += red[k * NW + w];
+            T s = red[k * 32];
+            for (int w = 1; w < nw; ++w) s = is_min ? (red[k * 32 + w] < s ? red[k * 32 + w] : s) : s + red[k * 32 + w];
             v[k] = s;
         }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NTN) k_nodes(const NodeArgs a)
+// One CTA per block of NB nodes of one ring, with a halo of HALO nodes on each side whose
+// advance is recomputed (identically) so that the forces of the owned nodes need no other CTA.
+__global__ void __launch_bounds__(NODE_THREADS) k_nodes(const NodeArgs a)
 {
-    extern __shared__ __align__(16) double smd[];
-    double* rx = smd;               // positions relative to node 0
-    double* ry = rx + MAXN;
-    double* tex = ry + MAXN;        // spring tension vectors per edge (a, a+1)
-    double* tey = tex + MAXN;
-    double* dpx = tey + MAXN;       // d cos(gamma_b) / d p and / d q per node b
-    double* dpy = dpx + MAXN;
-    double* dqx = dpy + MAXN;
-    double* dqy = dqx + MAXN;
-    __shared__ double red[5 * NW];
-    __shared__ int ired[4 * NW];
-    __shared__ double sX0[2];
+    __shared__ double sx[NODE_THREADS], sy[NODE_THREADS];     // new positions relative to node j = 0
+    __shared__ float tex[NODE_THREADS], tey[NODE_THREADS];    // spring tension vector of edge (j, j+1)
+    __shared__ float dpx[NODE_THREADS], dpy[NODE_THREADS];    // d cos(gamma_j) / d p, / d q
+    __shared__ float dqx[NODE_THREADS], dqy[NODE_THREADS];
+    __shared__ double dred[4 * 32];
+    __shared__ int ired[4 * 32];
+    __shared__ int s_last;
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -122,27 +142,37 @@ __global__ void __launch_bounds__(NTN) k_nodes(const NodeArgs a)
     const long long t = a.ctl->t;
     const bool readout = a.advance && (t % a.every) == 0;
     double* row = a.series + (long long)((t / a.every) % a.series_cap) * a.row_len;
+    const int2 wk = a.work[blockIdx.x];                    // (ring, first owned node)
 
-    if (blockIdx.x < a.n_rings) {
-        // the ring record is read once into registers (its box is written back at the end)
-        const RingDev R = a.rings[blockIdx.x];
+    if (wk.x >= 0) {
+        const RingDev R = a.rings[wk.x];
         const int n = R.n_nodes, off = R.node_off;
+        const int k0 = wk.y, n_own = min(NB, n - k0);
         const int bx0 = R.box_x0, by0 = R.box_y0, bw = R.box_w, bh = R.box_h;
-
-        if (a.advance) {
-            if (tid == 0) { sX0[0] = a.X[off].x; sX0[1] = a.X[off].y; }
-            __syncthreads();
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
-            int bad = 0;
-            for (int k = tid; k < n; k += NTN) {
-                const double2 X = a.X[off + k];
-                if (readout) {
+        const int j = tid;                                   // local slot: node k0 - HALO + j
+        const bool active = j < n_own + 2 * HALO;
+        const bool own = j >= HALO && j < HALO + n_own;
+        int k = k0 - HALO + j;
+        k %= n;
+        if (k < 0) k += n;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int bad = 0;
+        double2 Xn = make_double2(0.0, 0.0);
+        double2 X = make_double2(0.0, 0.0);
+        if (active) X = a.X[off + k];              // written by the previous node kernel
+        // u(t), f^p(t) and the lattice readout sums come from the lattice kernel just before
+        cell::pdl_wait();
+        cell::pdl_trigger();
+        if (active) {
+            Xn = X;
+            if (a.advance) {
+                if (readout && own) {
                     float fx, fy;
                     if (!interp_box(a.fpbox, R, bx0, by0, bw, bh, nx, ny, X.x, X.y, fx, fy)) bad = 1;
-                    acc[0] += (double)fx;
-                    acc[1] += (double)fy;
-                    acc[2] += mimg1(X.x - sX0[0], Lx);
-                    acc[3] += mimg1(X.y - sX0[1], Ly);
+                    acc[0] = (double)fx;
+                    acc[1] = (double)fy;
+                    acc[2] = mimg1(X.x - (double)bx0, Lx);        // centre of mass relative to the box
+                    acc[3] = mimg1(X.y - (double)by0, Ly);
                 }
                 float vx, vy, wx, wy;
                 if (!interp_box(a.ubox, R, bx0, by0, bw, bh, nx, ny, X.x, X.y, vx, vy)) bad = 1;
@@ -150,150 +180,166 @@ __global__ void __launch_bounds__(NTN) k_nodes(const NodeArgs a)
                 if (!interp_box(a.ubox, R, bx0, by0, bw, bh, nx, ny, Xs, Ys, wx, wy)) bad = 1;
                 const double dX = 0.5 * ((double)vx + (double)wx), dY = 0.5 * ((double)vy + (double)wy);
                 if (!(fabs(dX) < 1.0 && fabs(dY) < 1.0)) bad = 1;
-                a.X[off + k] = make_double2(wrap1(X.x + dX, Lx), wrap1(X.y + dY, Ly));
+                Xn = make_double2(wrap1(X.x + dX, Lx), wrap1(X.y + dY, Ly));
             }
-            if (bad) atomicExch(&a.ctl->err_body, 1);
-            if (readout) {
-                block_sums<4>(acc, red);
-                if (tid == 0) {
-                    double* rr = row + 6 + 4 * blockIdx.x;
-                    rr[0] = acc[0];
-                    rr[1] = acc[1];
-                    rr[2] = wrap1(sX0[0] + acc[2] / n, Lx);
-                    rr[3] = wrap1(sX0[1] + acc[3] / n, Ly);
-                    if (!isfinite(acc[0]) || !isfinite(acc[1]) || !isfinite(acc[2]) || !isfinite(acc[3]))
-                        atomicExch(&a.ctl->err_nonfinite, 1);
-                }
-            }
-            __syncthreads();
         }
-
-        // positions relative to node 0 (the ring spans less than half the lattice)
-        const double2 X0 = a.X[off];
-        for (int k = tid; k < n; k += NTN) {
-            const double2 X = a.X[off + k];
-            rx[k] = mimg1(X.x - X0.x, Lx);
-            ry[k] = mimg1(X.y - X0.y, Ly);
+        if (bad && own) atomicExch(&a.ctl->err_body, 1);
+        // positions relative to local slot 0 (the ring spans less than half the lattice)
+        if (tid == 0) { dred[0] = Xn.x; dred[1] = Xn.y; }
+        __syncthreads();
+        const double X0x = dred[0], X0y = dred[1];
+        __syncthreads();
+        if (active) {
+            sx[j] = mimg1(Xn.x - X0x, Lx);
+            sy[j] = mimg1(Xn.y - X0y, Ly);
         }
         __syncthreads();
-
-        // spring tension vectors and angle gradients (Eq. Const)
-        const double ks = R.k_spring, leq = R.l_eq, eps = R.eps_angle;
-        for (int k = tid; k < n; k += NTN) {
-            const int kp = (k + 1 == n) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
-            const double qx = rx[kp] - rx[k], qy = ry[kp] - ry[k];
-            const double px = rx[km] - rx[k], py = ry[km] - ry[k];
-            const double iq = rsqrt(qx * qx + qy * qy), ip = rsqrt(px * px + py * py);
-            const double lq = (qx * qx + qy * qy) * iq;
-            const double T = ks * (lq - leq) * iq;
-            tex[k] = T * qx;
-            tey[k] = T * qy;
-            const double ipq = ip * iq;
-            const double c = (px * qx + py * qy) * ipq;
-            const double cp = c * ip * ip, cq = c * iq * iq;
-            dpx[k] = qx * ipq - cp * px;
-            dpy[k] = qy * ipq - cp * py;
-            dqx[k] = px * ipq - cq * qx;
-            dqy[k] = py * ipq - cq * qy;
+        const int last = n_own + 2 * HALO - 1;
+        const float ks = (float)R.k_spring, leq = (float)R.l_eq, eps = (float)R.eps_angle;
+        if (j >= 1 && j < last) {
+            // Eq. Const.  Spring on the edge (j, j+1): the extension l - l_eq = (l^2 - l_eq^2) /
+            // (l + l_eq) with l^2 - l_eq^2 formed in FP64 from the FP64 edge vector, so it keeps
+            // its relative precision; the rest in FP32.
+            const double qxd = sx[j + 1] - sx[j], qyd = sy[j + 1] - sy[j];
+            const double ext2 = fma(qxd, qxd, fma(qyd, qyd, -R.l_eq * R.l_eq));
+            const float qx = (float)qxd, qy = (float)qyd;
+            const float px = (float)(sx[j - 1] - sx[j]), py = (float)(sy[j - 1] - sy[j]);
+            const float lq = sqrtf(qx * qx + qy * qy), lp = sqrtf(px * px + py * py);
+            const float T = ks * (float)ext2 / ((lq + leq) * lq);
+            tex[j] = T * qx;
+            tey[j] = T * qy;
+            // angle term at j: gradients of cos(gamma_j) = p.q / (|p||q|)
+            const float ip = 1.f / lp, iq = 1.f / lq;
+            const float ipq = ip * iq;
+            const float c = (px * qx + py * qy) * ipq;
+            const float cp = c * ip * ip, cq = c * iq * iq;
+            dpx[j] = qx * ipq - cp * px;
+            dpy[j] = qy * ipq - cp * py;
+            dqx[j] = px * ipq - cq * qx;
+            dqy[j] = py * ipq - cq * qy;
         }
         __syncthreads();
-
         int mm[4] = {1 << 30, 1 << 30, 1 << 30, 1 << 30};   // min x, -max x, min y, -max y
-        for (int k = tid; k < n; k += NTN) {
-            const int kp = (k + 1 == n) ? 0 : k + 1, km = (k == 0) ? n - 1 : k - 1;
+        if (own) {
             // f_a = -dU/dR_a: springs (a, a+1) and (a-1, a); angle terms at a-1 (a is its next),
             // a, a+1 (a is its prev); the pull
-            const double fx = tex[k] - tex[km] - eps * (dpx[kp] + dqx[km] - dpx[k] - dqx[k]) + R.pull_x;
-            const double fy = tey[k] - tey[km] - eps * (dpy[kp] + dqy[km] - dpy[k] - dqy[k]) + R.pull_y;
-            a.node_force[off + k] = make_float2((float)fx, (float)fy);
-            const double2 X = a.X[off + k];
-            int cx = (int)X.x, cy = (int)X.y;
-            float frx = (float)(X.x - cx), fry = (float)(X.y - cy);
+            const float fx = tex[j] - tex[j - 1] - eps * (dpx[j + 1] + dqx[j - 1] - dpx[j] - dqx[j]) + (float)R.pull_x;
+            const float fy = tey[j] - tey[j - 1] - eps * (dpy[j + 1] + dqy[j - 1] - dpy[j] - dqy[j]) + (float)R.pull_y;
+            a.node_force[off + k] = make_float2(fx, fy);
+            a.X[off + k] = Xn;
+            int cx = (int)Xn.x, cy = (int)Xn.y;
+            float frx = (float)(Xn.x - cx), fry = (float)(Xn.y - cy);
             if (frx >= 1.f) { frx = 0.f; cx += 1; }
             if (fry >= 1.f) { fry = 0.f; cy += 1; }
             a.node_cell[off + k] = make_int2(wrapi1(cx, nx), wrapi1(cy, ny));
             a.node_frac[off + k] = make_float2(frx, fry);
-            // unwrapped cell relative to node 0
-            const int ux = (int)floor(X0.x + rx[k]), uy = (int)floor(X0.y + ry[k]);
-            mm[0] = min(mm[0], ux); mm[1] = min(mm[1], -ux);
-            mm[2] = min(mm[2], uy); mm[3] = min(mm[3], -uy);
+            // cell offsets from the previous box origin, for the new box
+            const int ux = half_wrap(wrapi1(cx, nx) - bx0, nx), uy = half_wrap(wrapi1(cy, ny) - by0, ny);
+            mm[0] = ux; mm[1] = -ux; mm[2] = uy; mm[3] = -uy;
             if (!isfinite(fx) || !isfinite(fy)) atomicExch(&a.ctl->err_nonfinite, 1);
         }
-        {
-            const int lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                for (int o = 16; o > 0; o >>= 1) mm[q] = min(mm[q], __shfl_down_sync(0xffffffffu, mm[q], o));
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) ired[q * NW + wid] = mm[q];
-            __syncthreads();
-        }
+        cta_reduce<4, int>(mm, ired, true);
+        if (readout) cta_reduce<4, double>(acc, dred, false);
+        double* np_ = a.node_partials + (long long)blockIdx.x * 8;
         if (tid == 0) {
-            for (int q = 0; q < 4; ++q)
-                for (int w = 1; w < NW; ++w) mm[q] = min(mm[q], ired[q * NW + w]);
-            const int mnx = mm[0], mxx = -mm[1], mny = mm[2], mxy = -mm[3];
-            // cells min-2 .. max+3 cover the supports of R and of the Heun predictor R*
-            int w = mxx - mnx + 6, h = mxy - mny + 6;
+            for (int q = 0; q < 4; ++q) np_[q] = acc[q];
+            for (int q = 0; q < 4; ++q) np_[4 + q] = (double)mm[q];
+            __threadfence();
+            const unsigned prev = atomicAdd(&a.ring_tickets[wk.x], 1u);
+            s_last = (prev == (unsigned)(a.ring_ctas[wk.x] - 1));
+        }
+        __syncthreads();
+        if (s_last && tid == 0) {
+            // the ring's last CTA: box of the new positions and the ring's readouts
+            __threadfence();
+            const int c0 = a.ring_cta0[wk.x], nc = a.ring_ctas[wk.x];
+            double sum[4] = {0.0, 0.0, 0.0, 0.0};
+            int m[4] = {1 << 30, 1 << 30, 1 << 30, 1 << 30};
+            for (int c = 0; c < nc; ++c) {
+                const volatile double* p = a.node_partials + (long long)(c0 + c) * 8;
+                for (int q = 0; q < 4; ++q) {
+                    sum[q] += p[q];
+                    m[q] = min(m[q], (int)p[4 + q]);
+                }
+            }
+            int w = -m[1] - m[0] + 6, h = -m[3] - m[2] + 6;      // cells min-2 .. max+3
             if (w > R.cap_w || h > R.cap_h) {
                 atomicExch(&a.ctl->err_body, 1);
                 w = min(w, R.cap_w);
                 h = min(h, R.cap_h);
             }
-            RingDev& Rg = a.rings[blockIdx.x];
-            Rg.box_x0 = wrapi1(wrapi1(mnx - 2, nx), nx);
-            Rg.box_y0 = wrapi1(wrapi1(mny - 2, ny), ny);
+            RingDev& Rg = a.rings[wk.x];
+            Rg.box_x0 = wrapi1(wrapi1(bx0 + m[0] - 2, nx), nx);
+            Rg.box_y0 = wrapi1(wrapi1(by0 + m[2] - 2, ny), ny);
             Rg.box_w = w;
             Rg.box_h = h;
+            if (readout) {
+                double* rr = row + 6 + 4 * wk.x;
+                rr[0] = sum[0];
+                rr[1] = sum[1];
+                rr[2] = wrap1((double)bx0 + sum[2] / n, Lx);
+                rr[3] = wrap1((double)by0 + sum[3] / n, Ly);
+                for (int q = 0; q < 4; ++q)
+                    if (!isfinite(sum[q])) atomicExch(&a.ctl->err_nonfinite, 1);
+            }
+            a.ring_tickets[wk.x] = 0u;
         }
     }
 
-    if (blockIdx.x == 0 && readout) {
-        // fixed-order reduction of the lattice kernel's per-CTA sums
-        double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int k = tid; k < a.n_partials; k += NTN)
-#pragma unroll
-            for (int c = 0; c < 5; ++c) v[c] += a.partials[(long long)k * 5 + c];
-        block_sums<5>(v, red);
-        if (tid == 0) {
-            row[0] = (double)t;
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                row[1 + c] = v[c];
-                if (!isfinite(v[c])) atomicExch(&a.ctl->err_nonfinite, 1);
+    // the last CTA overall: lattice readout sums (fixed order) and the step counter
+    if (wk.x < 0) {
+        cell::pdl_wait();
+        cell::pdl_trigger();
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.ctl->ticket, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (readout) {
+            double v[4] = {0.0, 0.0, 0.0, 0.0};
+            double v4 = 0.0;
+            for (int k = tid; k < a.n_partials; k += blockDim.x) {
+                const volatile double* p = a.partials + (long long)k * 5;
+                v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3]; v4 += p[4];
+            }
+            double w1[1] = {v4};
+            cta_reduce<4, double>(v, dred, false);
+            cta_reduce<1, double>(w1, dred, false);
+            if (tid == 0) {
+                row[0] = (double)t;
+                for (int c = 0; c < 4; ++c) row[1 + c] = v[c];
+                row[5] = w1[0];
+                for (int c = 0; c < 5; ++c)
+                    if (!isfinite(row[1 + c])) atomicExch(&a.ctl->err_nonfinite, 1);
             }
         }
-    }
-
-    // the last CTA to arrive advances the step counter
-    if (a.advance) {
-        __syncthreads();
         if (tid == 0) {
+            a.ctl->ticket = 0u;
+            if (a.advance) a.ctl->t = t + 1;
             __threadfence();
-            const unsigned prev = atomicAdd(&a.ctl->ticket, 1u);
-            if (prev == gridDim.x - 1) {
-                a.ctl->ticket = 0u;
-                a.ctl->t = t + 1;
-                __threadfence();
-            }
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s)
+cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s, bool pdl)
 {
-    static bool attr = false;
-    const size_t smem = 8 * MAXN * sizeof(double);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const int grid = a.n_rings > 0 ? a.n_rings : 1;
-    k_nodes<<<grid, NTN, smem, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.n_ctas);
+    cfg.blockDim = dim3(NODE_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_nodes, a);
 }
 
 }  // namespace vlb
