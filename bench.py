@@ -227,6 +227,73 @@ def measure_forms(args, lb, W, torch):
     return out
 
 
+def measure_batched(args, lb, W, torch):
+    """The batched workload: 256 independent periodic lattices of sides {128, ..., 512} (28.9M
+    cells, 3.2 GB of FP32 state, larger than L2, so no flush) with one ring each, advanced by the
+    persistent kernel in graph-replayed chunks of 10 steps after the tile-shape autotuner; and
+    the restoring-force difference of batched instances against lb_step on the same inputs."""
+    import numpy as np
+    ws = W.cfg4()
+    cells = sum(w["nx"] * w["ny"] for w in ws)
+    ss = [lb.Solver.from_workload(w) for w in ws]
+    b = lb.Batch(ss)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    b.autotune(args.tune_cache, steps=3)
+    tune_s = time.perf_counter() - t0
+    shapes = {}
+    for i, w in enumerate(ws):
+        shapes["%dx%d" % (w["nx"], w["ny"])] = "%dx%d" % lb.TILE_SHAPES[b.shape(i)]
+    chunk = 10
+    steps = max(3, min(args.steps, 10))
+    b.step(2 * chunk)
+    b.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        b.step(chunk)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in ev)
+    b.sync()
+    out = {"workload": "256 periodic lattices, sides uniform over {128,192,256,384,512} (%.1fM "
+                       "cells), one ring each (r U[4,32], N=clamp(round(2 pi r/0.78),32,256), pull "
+                       "5e-4 at U[0,90] deg), D_p log-uniform [1e-3,1] with ceil(D_p/0.2) "
+                       "diffusion sub-steps above 0.2, relaxation U[20,500] steps" % (cells / 1e6),
+           "value": cells * chunk * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+           "ms_per_lb_step": ms / (chunk * steps), "graph": b.uses_graph, "grid_ctas": b.grid,
+           "tile_shapes": shapes, "autotune_s": tune_s, "steps": chunk * steps}
+    peaks, _ = measured_peaks()
+    gbs = 112.0 * cells * chunk * steps / (ms * 1e-3) / 1e9
+    out["roofline_frac"] = gbs / peaks["hbm_gbs"]
+    out["achieved_gbs"] = gbs
+    b.close()
+    for s_ in ss:
+        s_.close()
+    # batched instances against lb_step on the same inputs (restoring force over 500 steps)
+    errs = []
+    sub = [w for w in W.cfg4(n_instances=8)]
+    sb = [lb.Solver.from_workload(w) for w in sub]
+    bb = lb.Batch(sb)
+    bb.step(500)
+    bb.sync()
+    for w, s_ in zip(sub, sb):
+        r = lb.Solver.from_workload(w)
+        r.step(500)
+        r.sync()
+        a, c = s_.series()[:, 6:8], r.series()[:, 6:8]
+        errs.append(float(np.linalg.norm(a - c) / max(np.linalg.norm(c), 1e-300)))
+        r.close()
+    bb.close()
+    for s_ in sb:
+        s_.close()
+    out["frest_err_vs_fp32"] = {"value": max(errs), "workload": "first 8 instances, 500 steps, "
+                                "batched vs lb_step, relative L2 over 50 readouts"}
+    return out
+
+
 def cpu_baseline_sample():
     """The oracle as it stands on one host core, on a bounded sample of the workload: one LB
     time step of the 1024 x 1024 lattice."""
@@ -252,6 +319,9 @@ def main():
                     help="lattice side (profiling captures use 2048 so that the state exceeds L2)")
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "sweep"],
                     help="lattice kernel (auto: the sweep when eligible)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON cache of the batched tile-shape autotuner (default: none)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the device steps only (no e2e, parity check or CPU baseline)")
     args = ap.parse_args()
@@ -372,6 +442,8 @@ def main():
     s.close()
     del flush
     forms = None if world > 1 else measure_forms(args, lb, W, torch)
+    if forms is not None and not args.no_batched:
+        forms["batched"] = measure_batched(args, lb, W, torch)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

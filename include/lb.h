@@ -72,6 +72,9 @@ typedef struct lb_params {
     int32_t precision;              /* LB_FP32 or LB_FP16_BF16                                 */
     int32_t readout_every;          /* record readouts when t % readout_every == 0 (10)       */
     int32_t max_samples;            /* capacity of the readout ring buffer (rows)             */
+    int32_t diffusion_substeps;     /* 0: D_p inside the Heun step (needs 8 D_p <= 2); s > 0:  */
+    int32_t pad_;                   /*   the Heun step without diffusion, then s Heun sub-steps */
+                                    /*   of D_p / s on sigma (needs 8 D_p / s <= 2; FP32 only)  */
 } lb_params;
 
 typedef struct lb_ring {
@@ -86,7 +89,8 @@ typedef struct lb_handle lb_handle;
 
 /*
  * Create a solver.  Validates the parameters (stability: 0.5 < tau, 8 D_p <= 2 for the Heun
- * step of the diffusion term, Gamma*|alpha| linear rate <= 2, else LB_EUNSTABLE), allocates
+ * step of the diffusion term (8 D_p / s <= 2 with s diffusion sub-steps), Gamma*|alpha| linear
+ * rate <= 2, else LB_EUNSTABLE), allocates
  * the double-buffered state (2 x 14 FP32 planes of nx*ny) and builds the C~(P) table on the
  * host (FP64, Eq. Pk inverted numerically, App. B).  stream: a cudaStream_t (NULL = default).
  */
@@ -196,6 +200,48 @@ int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries);
 
 const char* lb_last_error(const lb_handle* h);
 void lb_destroy(lb_handle* h);
+
+/*
+ * Batched form.  Many independent lattices (each with its own size, parameters, rings and
+ * diffusion sub-steps; Sec. II with the parameters of Tables I-IV varied per instance) advanced
+ * together: one persistent cooperative kernel runs all instances' lattice tiles, then their
+ * diffusion sub-steps, then their node blocks, with a grid barrier between phases, for a chunk
+ * of readout_every steps per launch; the chunk is captured once as a CUDA graph and replayed.
+ * Each instance computes exactly what lb_step computes for its handle (fields and nodes bitwise
+ * equal; the readout sums of the lattice may differ in the last bits with the tile shape).
+ *
+ * lb_batch_create: handles[0..n-1] (n >= 1) must be distinct, have their fields and bodies set
+ *   (lb_init_fields, lb_set_body), use the FP32 state, share one stream and be at the same
+ *   buffer parity (an equal step count mod 2).  The batch keeps the pointers: the handles must
+ *   outlive it and must not be stepped with lb_step while it exists.  Readouts (lb_readout,
+ *   lb_series, ...) on the handles stay valid and are ordered after the batch's steps.
+ *   Returns LB_ESTATE for a handle not ready, LB_EINVAL for a mismatch.
+ * lb_batch_step: queue n >= 0 steps of every instance (asynchronous, on the handles' stream
+ *   order).  lb_batch_sync: wait, then report LB_ETIMEOUT if a grid barrier gave up (the
+ *   states are then undefined) or the first instance error of lb_sync.
+ * lb_batch_set_shape: tile shape of instance inst (-1: all): 0 = 32x16, 1 = 32x8, 2 = 64x8,
+ *   3 = 16x16 cells.  lb_batch_shape returns it (-1 for a bad index).
+ * lb_batch_autotune: time `steps` steps with each shape per distinct lattice size and keep the
+ *   fastest; the states are saved and restored, so the simulation does not advance.  cache_path
+ *   (or NULL) is a flat JSON object "<gpu name>|<nx>x<ny>": shape, read first and rewritten.
+ * lb_batch_set_wait_limit: limit of one barrier wait in ms (default 2000) and an arrival-count
+ *   offset that is 0 in normal use; a positive offset makes every barrier wait run out, which
+ *   exercises the LB_ETIMEOUT path.
+ * lb_batch_grid: CTAs of the persistent launch; lb_batch_uses_graph: 1 if chunks are replayed
+ *   from a captured graph.
+ */
+typedef struct lb_batch lb_batch;
+int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out);
+int lb_batch_step(lb_batch* b, int64_t n);
+int lb_batch_sync(lb_batch* b);
+int lb_batch_set_shape(lb_batch* b, int32_t inst, int32_t shape);
+int32_t lb_batch_shape(const lb_batch* b, int32_t inst);
+int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps);
+int lb_batch_set_wait_limit(lb_batch* b, double wait_ms, int32_t extra_arrivals);
+int32_t lb_batch_grid(const lb_batch* b);
+int32_t lb_batch_uses_graph(const lb_batch* b);
+const char* lb_batch_last_error(const lb_batch* b);
+void lb_batch_destroy(lb_batch* b);
 
 #ifdef __cplusplus
 }

@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
-SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu"]
+SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu", "lb_diffuse.cu",
+           "lb_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          "--expt-relaxed-constexpr"]
@@ -27,6 +28,7 @@ def nvcc() -> str:
 def _deps():
     return [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_cell.cuh"),
+        os.path.join(CSRC, "lb_tile.cuh"), os.path.join(CSRC, "lb_node.cuh"), os.path.join(CSRC, "lb_diffuse.cuh"),
         os.path.join(ROOT, "include", "lb.h"),
         os.path.abspath(__file__)]
 

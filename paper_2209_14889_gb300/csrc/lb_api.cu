@@ -13,54 +13,10 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lb.h"
-#include "lb_internal.h"
+#include "lb_handle.h"
 
 using namespace vlb;
 
-struct lb_handle {
-    lb_params p;
-    cudaStream_t stream = nullptr;
-    Phys ph;
-    double eta_p = 0.0;
-    long long plane = 0;
-    void* state[2] = {nullptr, nullptr};    // N_PLANES planes each (FP32, or 2-byte in LB_FP16_BF16)
-    int esz = 4;                            // bytes per stored value
-    int cur = 0;
-    float2* lut = nullptr;
-    Ctl* ctl = nullptr;
-    double* partials = nullptr;
-    int n_partials = 0;                     // partial sums written by the last lattice launch
-    int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP
-    int sweep_chunk = 0;
-    double* series = nullptr;
-    int series_cap = 0;
-    int row_len = 6;
-    float* moments = nullptr;               // 3 planes, allocated on first use
-    // rings
-    int n_rings = 0, n_total = 0;
-    RingDev* rings = nullptr;
-    double2* X = nullptr;
-    int2* node_cell = nullptr;
-    float2* node_frac = nullptr;
-    float2* node_force = nullptr;
-    float* ubox = nullptr;
-    float* fpbox = nullptr;
-    int n_node_ctas = 1;
-    int2* node_work = nullptr;
-    int* ring_cta0 = nullptr;
-    int* ring_ctas = nullptr;
-    unsigned* ring_tickets = nullptr;
-    double* node_partials = nullptr;
-    long long box_floats = 0;
-    bool fields_ready = false;
-    long long t = 0;
-    // timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_fused, ev_nodes;
-    size_t ev_fused_used = 0, ev_nodes_used = 0;
-    std::string err;
-};
 
 namespace {
 
@@ -264,6 +220,11 @@ cudaError_t f32_to_plane(const lb_handle* h, int b, int plane, const float* src)
 
 }  // namespace
 
+namespace vlb {
+FusedArgs handle_fused_args(lb_handle* h) { return fused_args(h); }
+NodeArgs handle_node_args(lb_handle* h, int advance) { return node_args(h, advance); }
+}  // namespace vlb
+
 extern "C" {
 
 int lb_create(const lb_params* pin, void* stream, lb_handle** out)
@@ -283,8 +244,13 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     if (!(eta > 0.0)) eta = p.lambda_steps * S8;
     if (!(eta > 0.0) || !std::isfinite(eta)) return fail(nullptr, LB_EINVAL, "need eta_p > 0 or lambda_steps > 0");
     // explicit stability bounds of the Heun steps (|z| <= 2 on the negative real axis)
-    if (p.Dp < 0.0 || 8.0 * p.Dp > 2.0)
-        return fail(nullptr, LB_EUNSTABLE, "D_p = %g outside [0, 0.25] (Heun + 5-point Laplacian)", p.Dp);
+    if (p.diffusion_substeps < 0) return fail(nullptr, LB_EINVAL, "diffusion_substeps < 0");
+    if (p.diffusion_substeps > 0 && p.precision != LB_FP32)
+        return fail(nullptr, LB_EINVAL, "diffusion sub-steps need the FP32 state");
+    const int dsub = p.diffusion_substeps;
+    if (p.Dp < 0.0 || 8.0 * p.Dp / (dsub > 0 ? dsub : 1) > 2.0)
+        return fail(nullptr, LB_EUNSTABLE, "D_p = %g with %d sub-steps outside the Heun bound 8 D_p / s <= 2",
+                    p.Dp, dsub);
     const double be_rate = p.Gamma * (2.0 * std::fabs(p.alpha) + 8.0 * p.kappa);
     if (p.Gamma < 0.0 || p.kappa < 0.0 || be_rate > 2.0)
         return fail(nullptr, LB_EUNSTABLE, "Gamma (2|alpha| + 8 kappa) = %g > 2", be_rate);
@@ -306,7 +272,7 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     ph.xi = (float)p.xi;
     ph.Gamma = (float)p.Gamma;
     ph.kappa = (float)p.kappa;
-    ph.Dp = (float)p.Dp;
+    ph.Dp = p.diffusion_substeps > 0 ? 0.f : (float)p.Dp;    // sub-stepped separately
     ph.inv_eta = (float)(1.0 / eta);
     {
         const double Peq = (p.alpha < 0.0 && p.beta > 0.0) ? std::sqrt(-p.alpha / p.beta) : 0.0;
@@ -540,6 +506,13 @@ int lb_step(lb_handle* h, int64_t n)
             h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
         } else {
             CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl));
+        }
+        if (h->p.diffusion_substeps > 0) {
+            // sigma of the new state; the old state's sigma planes serve as the other buffer
+            float* sig_new = static_cast<float*>(h->state[h->cur ^ 1]) + (size_t)PL_SXX * h->plane;
+            float* sig_old = static_cast<float*>(h->state[h->cur]) + (size_t)PL_SXX * h->plane;
+            CK(h, launch_diffusion(sig_new, sig_old, h->plane, h->p.nx, h->p.ny,
+                                   (float)(h->p.Dp / h->p.diffusion_substeps), h->p.diffusion_substeps, h->stream));
         }
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
         if (h->timing) {

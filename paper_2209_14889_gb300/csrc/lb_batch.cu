@@ -1,0 +1,624 @@
+// lb_batch.cu -- batched sweeps: many independent lattices of uneven sizes advanced by one
+// persistent cooperative launch per chunk of steps, replayed from a captured CUDA graph.
+//
+// Each step of the persistent kernel has three phases separated by a grid barrier:
+//   lattice  the fused step of every tile of every instance (tile shape per instance, chosen by
+//            the autotuner among 32x16, 32x8, 64x8, 16x16), the tile code of lb_tile.cuh;
+//   sigma    diffusion sub-steps of the instances whose D_p exceeds the Heun bound;
+//   nodes    the node blocks of every ring of every instance (lb_node.cuh).
+// Work items are assigned to CTAs round-robin, so the schedule and every result are the same
+// from run to run.  The barrier spins with an iteration limit and reports LB_ETIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lb_diffuse.cuh"
+#include "lb_handle.h"
+#include "lb_node.cuh"
+#include "lb_tile.cuh"
+
+namespace vlb {
+namespace {
+
+constexpr int BT = 256;     // threads per CTA
+constexpr int N_SHAPES = 4;
+__host__ __device__ constexpr int shape_tx(int s) { return s == 0 ? 32 : (s == 1 ? 32 : (s == 2 ? 64 : 16)); }
+__host__ __device__ constexpr int shape_ty(int s) { return s == 0 ? 16 : (s == 1 ? 8 : (s == 2 ? 8 : 16)); }
+
+constexpr size_t cmaxz(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t BATCH_SMEM =
+    cmaxz(cmaxz(tile::TileGeo<32, 16>::SMEM_BYTES, tile::TileGeo<32, 8>::SMEM_BYTES),
+          cmaxz(cmaxz(tile::TileGeo<64, 8>::SMEM_BYTES, tile::TileGeo<16, 16>::SMEM_BYTES),
+                sizeof(float) * dif::SMEM));
+
+struct BatchInst {
+    FusedArgs fa[2];            // lattice step from buffer p to buffer p^1, p = 0, 1
+    NodeArgs na;
+    float* sig[2];              // sigma planes of buffer 0 and 1
+    int shape, tiles_x, tiles_y;
+    int dsub;                   // diffusion sub-steps (0: none)
+    float dsub_D;               // D_p / dsub
+    int dif_tx, dif_ty;
+};
+
+struct BatchArgs {
+    const BatchInst* inst;
+    int n_inst;
+    const int* tile_begin;      // prefix sums of lattice tiles over instances (n_inst + 1)
+    const int* node_begin;      // prefix sums of node blocks
+    const int* dif_begin;       // prefix sums of diffusion tiles (instances with dsub > 0)
+    int max_dsub;
+    int* cur;                   // buffer parity of the current state (device)
+    unsigned* bar;              // [0] arrivals, [1] generation
+    int* err;                   // barrier timeout flag
+    unsigned extra_arrivals;    // 0; > 0 only to exercise the timeout path
+    unsigned long long wait_ns; // limit of one barrier wait
+};
+
+__device__ __forceinline__ int find_inst(const int* begin, int n, int item)
+{
+    int lo = 0, hi = n;          // begin[lo] <= item < begin[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (begin[mid] <= item) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs are co-resident).  The wait gives up after
+// B.wait_ns (or 2^26 polls), sets the error flag and returns false; the caller then stops.
+__device__ bool grid_sync(const BatchArgs& B)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = B.bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(B.bar, 1u) == gridDim.x - 1 + B.extra_arrivals) {
+            B.bar[0] = 0u;
+            __threadfence();
+            atomicAdd(B.bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned it = 0;
+            while (*gen == g) {
+                if (++it > (1u << 26) || global_ns() - t0 > B.wait_ns) {
+                    atomicExch(B.err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int cur0 = *B.cur;
+    const int n_tiles = __ldg(B.tile_begin + B.n_inst), n_nodes = __ldg(B.node_begin + B.n_inst);
+    const int n_dif = __ldg(B.dif_begin + B.n_inst);
+    bool ok = true;
+    for (int s = 0; s < nsteps && ok; ++s) {
+        const int par = (cur0 + s) & 1;
+        for (int item = blockIdx.x; item < n_tiles; item += gridDim.x) {
+            const int i = find_inst(B.tile_begin, B.n_inst, item);
+            const BatchInst& I = B.inst[i];
+            const int local = item - __ldg(B.tile_begin + i);
+            const int by = local / I.tiles_x, bx = local - by * I.tiles_x;
+            // coherent loads: the state was written by the previous step of this launch
+            switch (I.shape) {
+                case 0: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 16, true>(I.fa[par], bx, by, local, sm); break;
+                case 1: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 8, true>(I.fa[par], bx, by, local, sm); break;
+                case 2: tile::tile_step<MODE_STEP, cell::PREC_FP32, 64, 8, true>(I.fa[par], bx, by, local, sm); break;
+                default: tile::tile_step<MODE_STEP, cell::PREC_FP32, 16, 16, true>(I.fa[par], bx, by, local, sm); break;
+            }
+            __syncthreads();     // shared memory is reused by the next item
+        }
+        ok = grid_sync(B);
+        // diffusion sub-steps: sigma of the new buffer (par^1) and the old one as the other buffer
+        for (int k = 0; k <= B.max_dsub && ok && n_dif > 0; ++k) {
+            for (int item = blockIdx.x; item < n_dif; item += gridDim.x) {
+                const int i = find_inst(B.dif_begin, B.n_inst, item);
+                const BatchInst& I = B.inst[i];
+                const int local = item - __ldg(B.dif_begin + i);
+                const int by = local / I.dif_tx, bx = local - by * I.dif_tx;
+                float* sn = I.sig[par ^ 1];
+                float* so = I.sig[par];
+                const long long NP = I.fa[0].plane;
+                if (k < I.dsub) {
+                    const bool even = (k & 1) == 0;
+                    dif::diffuse_tile(even ? sn : so, even ? so : sn, NP, I.fa[0].nx, I.fa[0].ny, I.dsub_D, bx, by, sm);
+                } else if (k == I.dsub && (I.dsub & 1)) {
+                    // odd number of sub-steps: the result is in the other buffer; copy it back
+                    for (int q = threadIdx.x; q < dif::DX * dif::DY; q += blockDim.x) {
+                        const int ly = q / dif::DX, lx = q - ly * dif::DX;
+                        const int gx = bx * dif::DX + lx, gy = by * dif::DY + ly;
+                        if (gx < I.fa[0].nx && gy < I.fa[0].ny) {
+                            const long long g = (long long)gy * I.fa[0].nx + gx;
+                            for (int c = 0; c < 3; ++c) sn[c * NP + g] = __ldcg(so + c * NP + g);
+                        }
+                    }
+                }
+            }
+            ok = grid_sync(B);
+        }
+        if (!ok) break;
+        for (int item = blockIdx.x; item < n_nodes; item += gridDim.x) {
+            const int i = find_inst(B.node_begin, B.n_inst, item);
+            node::node_block(B.inst[i].na, item - __ldg(B.node_begin + i));
+            __syncthreads();
+        }
+        ok = grid_sync(B);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *B.cur = (cur0 + nsteps) & 1;
+}
+
+}  // namespace
+}  // namespace vlb
+
+using namespace vlb;
+
+struct lb_batch {
+    std::vector<lb_handle*> h;
+    cudaStream_t user = nullptr;            // the handles' stream
+    cudaStream_t stream = nullptr;          // the batch's own stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<int> shape;                 // per instance
+    BatchInst* d_inst = nullptr;
+    int *d_tile_begin = nullptr, *d_node_begin = nullptr, *d_dif_begin = nullptr;
+    int* d_cur = nullptr;
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    std::vector<double*> partials;          // per instance: readout partial sums sized for any shape
+    int max_dsub = 0, grid = 0, chunk = 10;
+    unsigned extra_arrivals = 0;
+    unsigned long long wait_ns = 2000000000ull;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_tried = false;
+    std::string err;
+};
+
+namespace {
+
+int bfail(lb_batch* b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+#define BCK(b, call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            if (b) b->err = std::string(#call) + ": " + cudaGetErrorString(e_);        \
+            return e_ == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA;             \
+        }                                                                              \
+    } while (0)
+
+void drop_graph(lb_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_tried = false;
+}
+
+// (re)build the per-instance descriptors for the current tile shapes
+int build_plan(lb_batch* b)
+{
+    const int n = (int)b->h.size();
+    std::vector<BatchInst> inst(n);
+    std::vector<int> tb(n + 1, 0), nb(n + 1, 0), db(n + 1, 0);
+    b->max_dsub = 0;
+    for (int i = 0; i < n; ++i) {
+        lb_handle* h = b->h[i];
+        BatchInst& I = inst[i];
+        const int save = h->cur;
+        for (int p = 0; p < 2; ++p) {
+            h->cur = p;
+            I.fa[p] = handle_fused_args(h);
+            I.fa[p].partials = b->partials[i];
+        }
+        h->cur = save;
+        I.na = handle_node_args(h, 1);
+        I.na.partials = b->partials[i];
+        I.shape = b->shape[i];
+        I.tiles_x = (h->p.nx + shape_tx(I.shape) - 1) / shape_tx(I.shape);
+        I.tiles_y = (h->p.ny + shape_ty(I.shape) - 1) / shape_ty(I.shape);
+        I.na.n_partials = I.tiles_x * I.tiles_y;
+        for (int p = 0; p < 2; ++p) I.sig[p] = static_cast<float*>(h->state[p]) + (size_t)PL_SXX * h->plane;
+        I.dsub = h->p.diffusion_substeps;
+        I.dsub_D = I.dsub > 0 ? (float)(h->p.Dp / I.dsub) : 0.f;
+        I.dif_tx = diffuse_tiles_x(h->p.nx);
+        I.dif_ty = diffuse_tiles_y(h->p.ny);
+        b->max_dsub = std::max(b->max_dsub, I.dsub);
+        tb[i + 1] = tb[i] + I.tiles_x * I.tiles_y;
+        nb[i + 1] = nb[i] + h->n_node_ctas;
+        db[i + 1] = db[i] + (I.dsub > 0 ? I.dif_tx * I.dif_ty : 0);
+    }
+    BCK(b, cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_node_begin, nb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_dif_begin, db.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    drop_graph(b);
+    return LB_OK;
+}
+
+BatchArgs batch_args(const lb_batch* b)
+{
+    BatchArgs a;
+    a.inst = b->d_inst;
+    a.n_inst = (int)b->h.size();
+    a.tile_begin = b->d_tile_begin;
+    a.node_begin = b->d_node_begin;
+    a.dif_begin = b->d_dif_begin;
+    a.max_dsub = b->max_dsub;
+    a.cur = b->d_cur;
+    a.bar = b->d_bar;
+    a.err = b->d_err;
+    a.extra_arrivals = b->extra_arrivals;
+    a.wait_ns = b->wait_ns;
+    return a;
+}
+
+cudaError_t launch_batch(const lb_batch* b, int nsteps)
+{
+    BatchArgs a = batch_args(b);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(BT);
+    cfg.dynamicSmemBytes = BATCH_SMEM;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch, a, nsteps);
+}
+
+// Capture one persistent launch of `chunk` steps as a graph (once per plan).  If capture or
+// instantiation is refused, the batch keeps launching the kernel directly.
+void capture(lb_batch* b)
+{
+    b->graph_tried = true;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const cudaError_t e = launch_batch(b, b->chunk);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess)
+        b->graph = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
+// n steps on the batch stream, ordered after the work already queued on the handles' stream and
+// before anything queued there later
+int run_steps(lb_batch* b, long long n)
+{
+    if (n == 0) return LB_OK;
+    if (!b->graph_tried) capture(b);
+    BCK(b, cudaEventRecord(b->ev_in, b->user));
+    BCK(b, cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    long long left = n;
+    while (b->graph && left >= b->chunk) {
+        BCK(b, cudaGraphLaunch(b->graph, b->stream));
+        left -= b->chunk;
+    }
+    while (left > 0) {
+        const int k = (int)std::min<long long>(left, b->chunk);
+        BCK(b, launch_batch(b, k));
+        left -= k;
+    }
+    BCK(b, cudaEventRecord(b->ev_out, b->stream));
+    BCK(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    for (lb_handle* h : b->h) {
+        h->t += n;
+        h->cur ^= (int)(n & 1);
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
+{
+    if (!handles || n < 1 || !out) return LB_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const lb_handle* h = handles[i];
+        if (!h || !h->fields_ready || !h->node_work) return LB_ESTATE;
+        if (h->p.precision != LB_FP32 || h->cur != handles[0]->cur || h->stream != handles[0]->stream)
+            return LB_EINVAL;
+        for (int k = 0; k < i; ++k)
+            if (handles[k] == h) return LB_EINVAL;
+    }
+    lb_batch* b = new lb_batch();
+    b->h.assign(handles, handles + n);
+    b->user = handles[0]->stream;
+    b->chunk = std::max(1, handles[0]->p.readout_every);
+    b->shape.assign(n, 0);
+    auto cleanup = [&](int code) { lb_batch_destroy(b); return code; };
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(LB_ECUDA);
+    if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_tile_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_node_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_dif_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_cur, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess)
+        return cleanup(LB_ENOMEM);
+    for (int i = 0; i < n; ++i) {
+        // enough partial sums for the smallest tile (16 x 8 cells covers every shape's count)
+        double* p = nullptr;
+        const long long tiles = ((long long)b->h[i]->p.nx / 16 + 1) * ((long long)b->h[i]->p.ny / 8 + 1);
+        if (cudaMalloc(&p, sizeof(double) * 5 * tiles) != cudaSuccess) return cleanup(LB_ENOMEM);
+        b->partials.push_back(p);
+    }
+    // the handles' queued work must be done before the batch's control words are set
+    if (cudaStreamSynchronize(b->user) != cudaSuccess) return cleanup(LB_ECUDA);
+    const int c0 = handles[0]->cur;
+    if (cudaMemcpy(b->d_cur, &c0, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess)
+        return cleanup(LB_ECUDA);
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM) != cudaSuccess)
+        return cleanup(LB_ECUDA);
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, BATCH_SMEM) != cudaSuccess || per_sm < 1)
+        return cleanup(LB_ECUDA);
+    b->grid = n_sm * per_sm;
+    const int rc = build_plan(b);
+    if (rc != LB_OK) return cleanup(rc);
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_set_shape(lb_batch* b, int32_t inst, int32_t shape)
+{
+    if (!b) return LB_EINVAL;
+    if (inst < -1 || inst >= (int)b->h.size() || shape < 0 || shape >= N_SHAPES)
+        return bfail(b, LB_EINVAL, "bad instance or shape");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (inst < 0) std::fill(b->shape.begin(), b->shape.end(), shape);
+    else b->shape[inst] = shape;
+    return build_plan(b);
+}
+
+int32_t lb_batch_shape(const lb_batch* b, int32_t inst)
+{
+    return b && inst >= 0 && inst < (int)b->h.size() ? b->shape[inst] : -1;
+}
+
+int lb_batch_step(lb_batch* b, int64_t n)
+{
+    if (!b) return LB_EINVAL;
+    if (n < 0) return bfail(b, LB_EINVAL, "n < 0");
+    return run_steps(b, n);
+}
+
+int lb_batch_sync(lb_batch* b)
+{
+    if (!b) return LB_EINVAL;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    BCK(b, cudaStreamSynchronize(b->user));
+    int e = 0;
+    BCK(b, cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        const int z = 0;
+        unsigned zb[2] = {0u, 0u};
+        BCK(b, cudaMemcpy(b->d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_bar, zb, sizeof zb, cudaMemcpyHostToDevice));
+        return bfail(b, LB_ETIMEOUT, "a grid barrier of the batched kernel timed out; the states are undefined");
+    }
+    for (size_t i = 0; i < b->h.size(); ++i) {
+        const int rc = lb_sync(b->h[i]);
+        if (rc != LB_OK) return bfail(b, rc, "instance " + std::to_string(i) + ": " + lb_last_error(b->h[i]));
+    }
+    return LB_OK;
+}
+
+int32_t lb_batch_grid(const lb_batch* b) { return b ? b->grid : 0; }
+
+int32_t lb_batch_uses_graph(const lb_batch* b) { return b && b->graph ? 1 : 0; }
+
+int lb_batch_set_wait_limit(lb_batch* b, double wait_ms, int32_t extra_arrivals)
+{
+    if (!b) return LB_EINVAL;
+    if (!(wait_ms > 0.0 && wait_ms <= 60000.0) || extra_arrivals < 0)
+        return bfail(b, LB_EINVAL, "need 0 < wait_ms <= 60000 and extra_arrivals >= 0");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->wait_ns = (unsigned long long)(wait_ms * 1e6);
+    b->extra_arrivals = (unsigned)extra_arrivals;
+    drop_graph(b);
+    return LB_OK;
+}
+
+// Autotuner: for every distinct lattice size of the batch, time `steps` batch steps with each
+// tile shape applied to that size (the others unchanged) and keep the fastest.  The state is
+// saved before and restored after, so tuning does not advance the simulation.  With a cache
+// path, sizes already tuned on this GPU model are read from it and new results written back.
+int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps)
+{
+    if (!b) return LB_EINVAL;
+    if (steps < 1) return bfail(b, LB_EINVAL, "steps < 1");
+    BCK(b, cudaStreamSynchronize(b->user));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    cudaDeviceProp prop;
+    int dev = 0;
+    BCK(b, cudaGetDevice(&dev));
+    BCK(b, cudaGetDeviceProperties(&prop, dev));
+    std::map<std::string, int> cache;
+    if (cache_path) {
+        // flat JSON object, one entry per line:  "<gpu>|<nx>x<ny>": <shape>
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[512];
+            while (fgets(line, sizeof line, f)) {
+                char* q1 = strchr(line, '"');
+                char* q2 = q1 ? strchr(q1 + 1, '"') : nullptr;
+                int v = -1;
+                if (q1 && q2 && sscanf(q2 + 1, " : %d", &v) == 1 && v >= 0 && v < N_SHAPES)
+                    cache[std::string(q1 + 1, q2)] = v;
+            }
+            fclose(f);
+        }
+    }
+    auto key_of = [&](const lb_handle* h) {
+        return std::string(prop.name) + "|" + std::to_string(h->p.nx) + "x" + std::to_string(h->p.ny);
+    };
+    std::map<std::string, std::vector<int>> classes;
+    for (int i = 0; i < (int)b->h.size(); ++i) classes[key_of(b->h[i])].push_back(i);
+    bool need_tune = false;
+    for (auto& kv : classes)
+        if (!cache.count(kv.first)) need_tune = true;
+    // snapshot everything a step writes: both state buffers, control words, series, nodes, rings
+    std::vector<std::pair<void*, void*>> saved;      // (live, copy)
+    std::vector<size_t> saved_bytes;
+    auto release = [&]() {
+        for (auto& s : saved) cudaFree(s.second);
+        saved.clear();
+    };
+    if (need_tune) {
+        for (lb_handle* h : b->h) {
+            const size_t sb = (size_t)h->esz * N_PLANES * h->plane;
+            std::vector<std::pair<void*, size_t>> items = {
+                {h->state[0], sb}, {h->state[1], sb}, {h->ctl, sizeof(Ctl)},
+                {h->series, sizeof(double) * (size_t)h->series_cap * h->row_len}};
+            if (h->n_total > 0) {
+                items.push_back({h->X, sizeof(double2) * h->n_total});
+                items.push_back({h->node_cell, sizeof(int2) * h->n_total});
+                items.push_back({h->node_frac, sizeof(float2) * h->n_total});
+                items.push_back({h->node_force, sizeof(float2) * h->n_total});
+                items.push_back({h->rings, sizeof(RingDev) * h->n_rings});
+            }
+            for (auto& it : items) {
+                void* d = nullptr;
+                if (cudaMalloc(&d, it.second) != cudaSuccess) {
+                    release();
+                    return bfail(b, LB_ENOMEM, "autotune snapshot");
+                }
+                saved.push_back({it.first, d});
+                saved_bytes.push_back(it.second);
+                if (cudaMemcpy(d, it.first, it.second, cudaMemcpyDeviceToDevice) != cudaSuccess) {
+                    release();
+                    return bfail(b, LB_ECUDA, "autotune snapshot copy");
+                }
+            }
+        }
+    }
+    int dcur = 0;
+    BCK(b, cudaMemcpy(&dcur, b->d_cur, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = LB_OK;
+    for (auto& kv : classes) {
+        auto hit = cache.find(kv.first);
+        if (hit != cache.end()) {
+            for (int i : kv.second) b->shape[i] = hit->second;
+            continue;
+        }
+        float best = 3.0e38f;
+        int best_s = 0;
+        for (int sh = 0; sh < N_SHAPES && rc == LB_OK; ++sh) {
+            for (int i : kv.second) b->shape[i] = sh;
+            if ((rc = build_plan(b)) != LB_OK) break;
+            cudaError_t e = launch_batch(b, 1);     // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = launch_batch(b, steps);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = bfail(b, LB_ECUDA, std::string("autotune launch: ") + cudaGetErrorString(e));
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_s = sh;
+            }
+        }
+        for (int i : kv.second) b->shape[i] = best_s;
+        cache[kv.first] = best_s;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the states, the device parity and the barrier words
+    for (size_t k = 0; k < saved.size(); ++k)
+        cudaMemcpy(saved[k].first, saved[k].second, saved_bytes[k], cudaMemcpyDeviceToDevice);
+    release();
+    cudaMemcpy(b->d_cur, &dcur, sizeof(int), cudaMemcpyHostToDevice);
+    int berr = 0;
+    cudaMemcpy(&berr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (rc != LB_OK) return rc;
+    if (berr) return bfail(b, LB_ETIMEOUT, "a grid barrier timed out while tuning");
+    rc = build_plan(b);
+    if (rc != LB_OK) return rc;
+    if (cache_path && need_tune) {
+        if (FILE* f = fopen(cache_path, "w")) {
+            fprintf(f, "{\n");
+            size_t k = 0;
+            for (auto& kv : cache)
+                fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < cache.size() ? "," : "");
+            fprintf(f, "}\n");
+            fclose(f);
+        } else {
+            return bfail(b, LB_EINVAL, std::string("cannot write the tuning cache ") + cache_path);
+        }
+    }
+    return LB_OK;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void lb_batch_destroy(lb_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_tile_begin);
+    cudaFree(b->d_node_begin);
+    cudaFree(b->d_dif_begin);
+    cudaFree(b->d_cur);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    for (double* p : b->partials) cudaFree(p);
+    delete b;
+}
+
+}  // extern "C"

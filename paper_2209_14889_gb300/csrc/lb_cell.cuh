@@ -258,19 +258,28 @@ __device__ __forceinline__ float pop_unscale(int n)   // w_n / 2^POP_SHIFT
     return n == 0 ? (4.f / 9.f) / 4096.f : (n < 5 ? (1.f / 9.f) / 4096.f : (1.f / 36.f) / 4096.f);
 }
 
-template <int PREC>
+// COH: the state was written earlier in the same launch (persistent kernel) -- load through L2
+// (ld.global.cg) instead of the non-coherent read-only path
+template <class T, bool COH>
+__device__ __forceinline__ T ld_state(const T* p)
+{
+    if (COH) return __ldcg(p);
+    return __ldg(p);
+}
+
+template <int PREC, bool COH = false>
 __device__ __forceinline__ float ld_pop(const void* src, long long NP, int n, long long g)
 {
-    if (PREC == PREC_FP32) return __ldg(reinterpret_cast<const float*>(src) + n * NP + g);
-    const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(src) + n * NP + g);
+    if (PREC == PREC_FP32) return ld_state<float, COH>(reinterpret_cast<const float*>(src) + n * NP + g);
+    const unsigned short b = ld_state<unsigned short, COH>(reinterpret_cast<const unsigned short*>(src) + n * NP + g);
     return __half2float(__ushort_as_half(b)) * pop_unscale(n);
 }
 
-template <int PREC>
+template <int PREC, bool COH = false>
 __device__ __forceinline__ float ld_fld(const void* src, long long NP, int plane, long long g)
 {
-    if (PREC == PREC_FP32) return __ldg(reinterpret_cast<const float*>(src) + plane * NP + g);
-    const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(src) + plane * NP + g);
+    if (PREC == PREC_FP32) return ld_state<float, COH>(reinterpret_cast<const float*>(src) + plane * NP + g);
+    const unsigned short b = ld_state<unsigned short, COH>(reinterpret_cast<const unsigned short*>(src) + plane * NP + g);
     if (plane >= PL_PX) return __half2float(__ushort_as_half(b));      // dP: FP16
     return __uint_as_float((unsigned)b << 16);                         // sigma: BF16
 }

@@ -1,0 +1,64 @@
+// lb_handle.h -- the solver handle behind the C ABI (host side; shared by lb_api.cu and
+// lb_batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lb.h"
+#include "lb_internal.h"
+
+using vlb::Ctl;
+using vlb::Phys;
+using vlb::RingDev;
+
+struct lb_handle {
+    lb_params p;
+    cudaStream_t stream = nullptr;
+    Phys ph;
+    double eta_p = 0.0;
+    long long plane = 0;
+    void* state[2] = {nullptr, nullptr};    // N_PLANES planes each (FP32, or 2-byte in LB_FP16_BF16)
+    int esz = 4;                            // bytes per stored value
+    int cur = 0;
+    float2* lut = nullptr;
+    Ctl* ctl = nullptr;
+    double* partials = nullptr;
+    int n_partials = 0;                     // partial sums written by the last lattice launch
+    int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP
+    int sweep_chunk = 0;
+    double* series = nullptr;
+    int series_cap = 0;
+    int row_len = 6;
+    float* moments = nullptr;               // 3 planes, allocated on first use
+    // rings
+    int n_rings = 0, n_total = 0;
+    RingDev* rings = nullptr;
+    double2* X = nullptr;
+    int2* node_cell = nullptr;
+    float2* node_frac = nullptr;
+    float2* node_force = nullptr;
+    float* ubox = nullptr;
+    float* fpbox = nullptr;
+    int n_node_ctas = 1;
+    int2* node_work = nullptr;
+    int* ring_cta0 = nullptr;
+    int* ring_ctas = nullptr;
+    unsigned* ring_tickets = nullptr;
+    double* node_partials = nullptr;
+    long long box_floats = 0;
+    bool fields_ready = false;
+    long long t = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_fused, ev_nodes;
+    size_t ev_fused_used = 0, ev_nodes_used = 0;
+    std::string err;
+};
+
+namespace vlb {
+// argument blocks of the two kernels of a step for the handle's current buffers (lb_api.cu)
+FusedArgs handle_fused_args(lb_handle* h);
+NodeArgs handle_node_args(lb_handle* h, int advance);
+}  // namespace vlb

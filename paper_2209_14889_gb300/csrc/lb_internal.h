@@ -119,6 +119,14 @@ int fused_ctas(int nx, int ny);
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 
+// Stress-diffusion sub-steps (lb_diffuse.cu): s Heun sub-steps of D_p/s on the sigma planes of
+// sig_new (3 planes of NP), using sig_tmp (3 planes) as the other buffer.
+int diffuse_smem_floats();
+int diffuse_tiles_x(int nx);
+int diffuse_tiles_y(int ny);
+cudaError_t launch_diffusion(float* sig_new, float* sig_tmp, long long NP, int nx, int ny, float D, int substeps,
+                             cudaStream_t s);
+
 // Host-side table builder (FP64): fills lut[2*(LUT_N+1)] with (a2, a4) pairs.
 void build_lut(double P_cap, float* lut);
 

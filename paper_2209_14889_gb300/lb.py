@@ -42,7 +42,8 @@ class lb_params(ctypes.Structure):
                 ("Gamma", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("P_cap", ctypes.c_double), ("director_angle", ctypes.c_double),
                 ("ericksen", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32)]
+                ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32),
+                ("diffusion_substeps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class lb_ring(ctypes.Structure):
@@ -54,6 +55,7 @@ class lb_ring(ctypes.Structure):
 
 _lib = None
 _H = ctypes.c_void_p
+_B = ctypes.c_void_p
 
 
 def library_path() -> str:
@@ -91,6 +93,17 @@ def lib():
             "lb_bytes_per_cell": (ctypes.c_double, [_H]),
             "lb_last_error": (ctypes.c_char_p, [_H]),
             "lb_destroy": (None, [_H]),
+            "lb_batch_create": (ctypes.c_int, [ctypes.POINTER(_H), i32, ctypes.POINTER(_B)]),
+            "lb_batch_step": (ctypes.c_int, [_B, i64]),
+            "lb_batch_sync": (ctypes.c_int, [_B]),
+            "lb_batch_set_shape": (ctypes.c_int, [_B, i32, i32]),
+            "lb_batch_shape": (i32, [_B, i32]),
+            "lb_batch_autotune": (ctypes.c_int, [_B, ctypes.c_char_p, i32]),
+            "lb_batch_set_wait_limit": (ctypes.c_int, [_B, ctypes.c_double, i32]),
+            "lb_batch_grid": (i32, [_B]),
+            "lb_batch_uses_graph": (i32, [_B]),
+            "lb_batch_last_error": (ctypes.c_char_p, [_B]),
+            "lb_batch_destroy": (None, [_B]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -113,7 +126,8 @@ def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4
                      beta=w["beta"], xi=w["xi"], Gamma=w["Gamma"], kappa=w["kappa"],
                      P_cap=w.get("P_cap", 0.99), director_angle=w["director_angle"],
                      ericksen=w.get("ericksen", 1), precision=precision,
-                     readout_every=w.get("every", 10), max_samples=max_samples)
+                     readout_every=w.get("every", 10), max_samples=max_samples,
+                     diffusion_substeps=w.get("diffusion_substeps", 0))
 
 
 def stiffness_table(P_cap: float = 0.99) -> np.ndarray:
@@ -259,3 +273,64 @@ class Solver:
     @property
     def launches_per_step(self) -> int:
         return lib().lb_launches_per_step(self.h)
+
+
+TILE_SHAPES = {0: (32, 16), 1: (32, 8), 2: (64, 8), 3: (16, 16)}
+
+
+class Batch:
+    """Independent lattices advanced together by the persistent batched kernel (lb_batch_*).
+
+    The solvers stay usable for readouts; they must not be stepped on their own while the batch
+    exists, and must outlive it (the batch keeps references to them)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        L = lib()
+        arr = (_H * len(self.solvers))(*[s.h for s in self.solvers])
+        self.b = _B()
+        rc = L.lb_batch_create(arr, len(self.solvers), ctypes.byref(self.b))
+        if rc != LB_OK:
+            raise LBError(rc, "lb_batch_create failed")
+
+    def _check(self, rc):
+        if rc != LB_OK:
+            raise LBError(rc, lib().lb_batch_last_error(self.b).decode())
+
+    def close(self):
+        if self.b:
+            lib().lb_batch_destroy(self.b)
+            self.b = _B()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        self._check(lib().lb_batch_step(self.b, int(n)))
+
+    def sync(self):
+        self._check(lib().lb_batch_sync(self.b))
+
+    def set_shape(self, shape: int, inst: int = -1):
+        self._check(lib().lb_batch_set_shape(self.b, int(inst), int(shape)))
+
+    def shape(self, inst: int) -> int:
+        return lib().lb_batch_shape(self.b, int(inst))
+
+    def autotune(self, cache_path=None, steps: int = 5):
+        self._check(lib().lb_batch_autotune(self.b, None if cache_path is None else
+                                            os.fsencode(cache_path), int(steps)))
+
+    def set_wait_limit(self, wait_ms: float, extra_arrivals: int = 0):
+        self._check(lib().lb_batch_set_wait_limit(self.b, float(wait_ms), int(extra_arrivals)))
+
+    @property
+    def grid(self) -> int:
+        return lib().lb_batch_grid(self.b)
+
+    @property
+    def uses_graph(self) -> bool:
+        return bool(lib().lb_batch_uses_graph(self.b))

@@ -102,3 +102,32 @@ def small(nx: int, ny: int, seed: int = 7, n_nodes: int = 24, radius: float = 5.
     rings = [ring(n_nodes, radius, centre, pull_force=1e-3, pull_angle=pull_angle, phase=0.1)] \
         if n_nodes > 0 else []
     return make(nx, ny, rings=rings, seed=seed, steps=steps, every=10, **physics)
+
+
+def cfg4(seed: int = 4, n_instances: int = 256, sides=(128, 192, 256, 384, 512),
+         steps: int = 5000) -> list:
+    """Batched workload: n_instances independent square periodic lattices, each with one ring.
+
+    Per instance, drawn from one PCG64 stream: side uniform over `sides`; ring radius
+    r ~ U[4, min(32, side/4 - 6)] (the upper bound keeps the ring with its supports within half
+    the lattice); N = clamp(round(2 pi r / 0.78), 32, 256) nodes; pull 5e-4 at an angle
+    U[0, 90] degrees; D_p log-uniform on [1e-3, 1], with ceil(D_p / 0.2) diffusion sub-steps
+    when D_p > 0.2; relaxation time lambda ~ U[20, 500] steps; the ring centred at a uniform
+    position; orientation noise from a per-instance seed.  The rest as in DEFAULT_PHYSICS.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed + 4000))
+    out = []
+    for i in range(n_instances):
+        side = int(sides[int(rng.integers(0, len(sides)))])
+        r = float(rng.uniform(4.0, min(32.0, side / 4 - 6)))
+        n_nodes = int(min(256, max(32, round(2 * math.pi * r / 0.78))))
+        angle = float(rng.uniform(0.0, math.pi / 2))
+        Dp = float(math.exp(rng.uniform(math.log(1e-3), math.log(1.0))))
+        lam = float(rng.uniform(20.0, 500.0))
+        centre = tuple(float(c) for c in rng.uniform(0.0, side, size=2))
+        sub = int(math.ceil(Dp / 0.2)) if Dp > 0.2 else 0
+        w = make(side, side, rings=[ring(n_nodes, r, centre, pull_force=5e-4, pull_angle=angle)],
+                 seed=seed * 100000 + i, steps=steps, every=10, lambda_steps=lam, Dp=Dp,
+                 diffusion_substeps=sub)
+        out.append(w)
+    return out

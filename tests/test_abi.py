@@ -36,9 +36,9 @@ def test_binding_names_match_header():
 
 
 def test_struct_layout_matches_header():
-    # lb_params: 2 int32, 16 doubles, 4 int32 ; lb_ring: 2 int32 + 5 doubles
+    # lb_params: 2 int32, 16 doubles, 6 int32 ; lb_ring: 2 int32 + 5 doubles
     from paper_2209_14889_gb300 import lb
-    assert ctypes.sizeof(lb.lb_params) == 8 + 16 * 8 + 16
+    assert ctypes.sizeof(lb.lb_params) == 8 + 16 * 8 + 24
     assert ctypes.sizeof(lb.lb_ring) == 8 + 5 * 8
 
 
@@ -95,3 +95,22 @@ def test_library_stiffness_table_matches_oracle():
         a4 = O.bessel_i(4, k) / I0 / q ** 2
         assert abs(tab[i, 0] - a2) < 2e-7 * a2, i
         assert abs(tab[i, 1] - a4) < 2e-7 * a4, i
+
+
+def test_batch_entry_points_validate_without_gpu():
+    # argument checks come before any CUDA call
+    from paper_2209_14889_gb300 import lb
+    L = lb.lib()
+    b = ctypes.c_void_p()
+    assert L.lb_batch_create(None, 0, ctypes.byref(b)) == lb.LB_EINVAL
+    assert not b.value
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.lb_batch_create(arr, 1, ctypes.byref(b)) == lb.LB_ESTATE
+    assert L.lb_batch_step(None, 1) == lb.LB_EINVAL
+    assert L.lb_batch_sync(None) == lb.LB_EINVAL
+    assert L.lb_batch_set_shape(None, 0, 0) == lb.LB_EINVAL
+    assert L.lb_batch_shape(None, 0) == -1
+    assert L.lb_batch_autotune(None, None, 1) == lb.LB_EINVAL
+    assert L.lb_batch_set_wait_limit(None, 1.0, 0) == lb.LB_EINVAL
+    assert L.lb_batch_grid(None) == 0
+    L.lb_batch_destroy(None)

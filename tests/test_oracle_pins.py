@@ -392,6 +392,26 @@ def test_stress_mode_diffusion_exact():
     assert np.abs(sim.sigma - ref).max() < 1e-12 * np.abs(sig0).max()
 
 
+def test_stress_mode_diffusion_substeps_exact():
+    # Diffusion beyond the Heun bound (8 D_p > 2) taken as s Heun sub-steps of D_p / s after a
+    # step without diffusion: with C = 0 and no flow the Airy mode decays per step by
+    # (1 - z/s + (z/s)^2 / 2)^s, z as above; without sub-steps that factor would exceed 1 in
+    # magnitude for this mode (the plain step is unstable there).
+    n, D, s = 16, 0.6, 3
+    kx, ky = 2 * np.pi * 4 / n, 2 * np.pi * 7 / n
+    p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, Dp=D, ericksen=0, diffusion_substeps=s)
+    sig0 = 1e-3 * _airy_mode(n, kx, ky)
+    sim = O.Sim(p, [], O.equilibrium(np.ones((n, n)), np.zeros((2, n, n))), sig0.copy(),
+                np.zeros((2, n, n)), np.zeros((0, 2)))
+    steps = 12
+    sim.step(steps)
+    z = D * (4 * math.sin(kx / 2) ** 2 + 4 * math.sin(ky / 2) ** 2)
+    g = (1 - z / s + (z / s) ** 2 / 2) ** s
+    assert abs(1 - z + z * z / 2) > 1.0 > abs(g)
+    ref = g ** steps * sig0
+    assert np.abs(sim.sigma - ref).max() < 1e-12 * np.abs(sig0).max()
+
+
 def test_stress_pulse_second_moment_grows_4Dt():
     # Heun + 5-point Laplacian: sum x^2 s grows by exactly 4 D sum s per step (2D).
     n, D = 48, 0.1
