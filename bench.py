@@ -48,11 +48,22 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+KERNEL_SOURCES = ["lb_fused.cu", "lb_tile.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h"]
+
+
+def kernel_source_sha1():
+    """SHA-1 over the sources of the fused lattice kernel (the counters in profiles/ are valid
+    only for the source they were taken on)."""
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2209_14889_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def ncu_traffic():
     """DRAM bytes per launch of the fused kernel from the committed ncu summary, or None when
     the kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "fused_step_1024x1024.txt")
-    src = os.path.join(ROOT, "paper_2209_14889_gb300", "csrc", "lb_fused.cu")
     if not os.path.exists(path):
         return None
     info = {}
@@ -60,7 +71,7 @@ def ncu_traffic():
         if ":" in line:
             k, v = line.split(":", 1)
             info[k.strip()] = v.strip()
-    sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    sha = kernel_source_sha1()
     if info.get("kernel_source_sha1") != sha or "dram_bytes_per_launch" not in info:
         return None
     return float(info["dram_bytes_per_launch"])
@@ -308,6 +319,12 @@ def cpu_baseline_sample():
             "sample": "1 LB time step of the 1024x1024 workload (%.1f s)" % dt}
 
 
+KERNEL_NAMES = {"auto": "k_fused (fused lattice step, one cell per thread)",
+                "pair": "k_fused_pair (fused lattice step, two cells per thread)",
+                "tile": "k_fused (fused lattice step, one cell per thread)",
+                "sweep": "k_sweep (column-strip sweep)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,8 +334,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=1024,
                     help="lattice side (profiling captures use 2048 so that the state exceeds L2)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "sweep"],
-                    help="lattice kernel (auto: the sweep when eligible)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "pair", "sweep"],
+                    help="lattice kernel (auto: the fastest measured, the one-cell tile kernel)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON cache of the batched tile-shape autotuner (default: none)")
@@ -345,7 +362,7 @@ def main():
                    seed=2 + rank, steps=20000, every=10, lambda_steps=200.0, Dp=0.1)
     cells = w["nx"] * w["ny"]
     s = lb.Solver.from_workload(w)
-    s.set_kernel({"auto": lb.LB_KERNEL_AUTO, "tile": lb.LB_KERNEL_TILE,
+    s.set_kernel({"auto": lb.LB_KERNEL_AUTO, "tile": lb.LB_KERNEL_TILE, "pair": lb.LB_KERNEL_PAIR,
                   "sweep": lb.LB_KERNEL_SWEEP}[args.kernel])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -396,10 +413,10 @@ def main():
     fused_avg_s = kt["fused_ms"] * 1e-3 / max(kt["fused_launches"], 1)
     bytes_launch = s.bytes_per_cell * cells
     achieved = bytes_launch / fused_avg_s / 1e9
-    traffic = ncu_traffic()
+    traffic = ncu_traffic() if args.kernel in ("auto", "tile") and args.side == 1024 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "k_fused (fused lattice step)", "peak_kind": peak_kind,
+            "kernel": KERNEL_NAMES[args.kernel], "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bytes_launch,
             "mean_launch_us": fused_avg_s * 1e6,
             "node_kernel_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1)}

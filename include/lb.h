@@ -173,15 +173,18 @@ int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, doub
                    int64_t* node_launches);
 
 /*
- * Lattice kernel used by lb_step.  Both compute the same step with the same per-cell
- * arithmetic.  LB_KERNEL_TILE: 32 x 16 tiles with their halo recomputed (any lattice).
- * LB_KERNEL_SWEEP: column strips swept row by row, rows streamed by asynchronous bulk copies
- * (needs nx % 4 == 0, nx >= 256, ny >= 16, else LB_EINVAL).  LB_KERNEL_AUTO (default): the
- * kernel measured fastest on GB300, currently the tile kernel.
+ * Lattice kernel used by lb_step.  All compute the same step with the same per-cell
+ * arithmetic.  LB_KERNEL_TILE: 32 x 16 tiles with their halo recomputed, one cell per thread
+ * (any lattice).  LB_KERNEL_PAIR: the same tiles with two neighbouring cells per thread on
+ * paired FP32 instructions (any lattice).  LB_KERNEL_SWEEP: column strips swept row by row,
+ * rows streamed by asynchronous bulk copies (needs nx % 4 == 0, nx >= 256, ny >= 16, FP32 state,
+ * else LB_EINVAL).  LB_KERNEL_AUTO (default): the kernel measured fastest on GB300, currently
+ * the one-cell tile kernel.
  */
 #define LB_KERNEL_AUTO 0
 #define LB_KERNEL_TILE 1
 #define LB_KERNEL_SWEEP 2
+#define LB_KERNEL_PAIR 3
 int lb_set_kernel(lb_handle* h, int32_t kernel);
 
 /* Number of kernels launched per lb_step(1) call (2: fused lattice + node kernel). */

@@ -14,8 +14,11 @@ LIB = os.path.join(HERE, "libvlb.so")
 SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu", "lb_diffuse.cu",
            "lb_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -fmad=false: no automatic contraction of a product and a sum into one FMA.  The one-cell
+# kernels fuse exactly where the source calls fmaf, so the same device code rounds identically
+# in every kernel it is inlined into (single-lattice and batched launches agree bitwise).
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-         "--expt-relaxed-constexpr"]
+         "--expt-relaxed-constexpr", "-fmad=false"]
 
 
 def nvcc() -> str:
@@ -28,7 +31,7 @@ def nvcc() -> str:
 def _deps():
     return [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_cell.cuh"),
-        os.path.join(CSRC, "lb_tile.cuh"), os.path.join(CSRC, "lb_node.cuh"), os.path.join(CSRC, "lb_diffuse.cuh"),
+        os.path.join(CSRC, "lb_tile.cuh"), os.path.join(CSRC, "lb_node.cuh"), os.path.join(CSRC, "lb_diffuse.cuh"), os.path.join(CSRC, "lb_vec.cuh"),
         os.path.join(ROOT, "include", "lb.h"),
         os.path.abspath(__file__)]
 

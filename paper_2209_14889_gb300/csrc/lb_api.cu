@@ -495,9 +495,11 @@ int lb_step(lb_handle* h, int64_t n)
             e1 = ev_get(h->ev_fused, h->ev_fused_used);
             if (e0) cudaEventRecord(e0, h->stream);
         }
-        // LB_KERNEL_AUTO takes the tile kernel: measured faster than the sweep on GB300 so far
-        // (1024^2: 84 vs 121 us per launch; the sweep stalls on its per-row barriers)
+        // LB_KERNEL_AUTO takes the one-cell tile kernel: measured fastest on GB300 (1024^2:
+        // 74 us per launch against 88 us for the paired kernel, whose 126 registers leave two
+        // CTAs per SM, and 121 us for the sweep)
         const bool sweep = h->kernel == LB_KERNEL_SWEEP;
+        const bool pair = h->kernel == LB_KERNEL_PAIR;
         // consecutive lattice and node kernels overlap by programmatic dependent launch, except
         // when per-kernel timing brackets each launch with events
         const bool pdl = !h->timing;
@@ -505,7 +507,7 @@ int lb_step(lb_handle* h, int64_t n)
             CK(h, launch_sweep(fa, h->sweep_chunk, h->stream));
             h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
         } else {
-            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl));
+            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl, pair));
         }
         if (h->p.diffusion_substeps > 0) {
             // sigma of the new state; the old state's sigma planes serve as the other buffer
@@ -688,7 +690,7 @@ int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries)
 int lb_set_kernel(lb_handle* h, int32_t kernel)
 {
     if (!h) return fail(nullptr, LB_EINVAL, "null handle");
-    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_SWEEP) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_PAIR) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
     if (kernel == LB_KERNEL_SWEEP && h->p.precision != LB_FP32)
         return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
     if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
             const BatchInst& I = B.inst[i];
             const int local = item - __ldg(B.tile_begin + i);
             const int by = local / I.tiles_x, bx = local - by * I.tiles_x;
-            // coherent loads: the state was written by the previous step of this launch
+            // the tile step of lb_step; coherent loads: the state was written by the previous step
+            // of this launch
             switch (I.shape) {
                 case 0: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 16, true>(I.fa[par], bx, by, local, sm); break;
                 case 1: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 8, true>(I.fa[par], bx, by, local, sm); break;

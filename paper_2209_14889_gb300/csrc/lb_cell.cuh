@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "lb_internal.h"
+#include "lb_vec.cuh"
 
 namespace vlb {
 namespace cell {
@@ -47,6 +48,12 @@ __device__ __forceinline__ void lut_eval(const float* __restrict__ L, const Phys
         a4 *= s * s;
     }
 }
+__device__ __forceinline__ void lut_eval(const float* __restrict__ L, const Phys& ph, float2 q, float2& a2,
+                                         float2& a4)
+{
+    lut_eval(L, ph, q.x, a2.x, a4.x);
+    lut_eval(L, ph, q.y, a2.y, a4.y);
+}
 
 // Programmatic dependent launch (the lattice and node kernels of consecutive steps overlap):
 // pdl_wait blocks until the preceding kernel in the stream has completed and its writes are
@@ -56,10 +63,15 @@ __device__ __forceinline__ void lut_eval(const float* __restrict__ L, const Phys
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Stencil values of one component: centre, east (+x), west, north (+y), south.
-struct St {
-    float c, e, w, n, s;
+using namespace vec;
+
+// Stencil values of one component: centre, east (+x), west, north (+y), south; T = float for
+// one cell, float2 for two neighbouring cells (x, x+1).
+template <class T>
+struct StT {
+    T c, e, w, n, s;
 };
+using St = StT<float>;
 
 __device__ __forceinline__ St st_at(const float* base, int W, int lx, int ly)
 {
@@ -67,77 +79,139 @@ __device__ __forceinline__ St st_at(const float* base, int W, int lx, int ly)
     return St{p[0], p[1], p[-1], p[W], p[-W]};
 }
 
+// Stencils of the cell pair (lx, lx+1) of a shared-memory plane of even width W.  EVEN: the
+// flat index of (lx, ly) is even (8-byte aligned pairs at the centre row and at +-W);
+// otherwise the pairs at -1 and +1 are the aligned ones and hold w and e exactly.
+template <bool EVEN>
+__device__ __forceinline__ StT<float2> st2_at(const float* base, int W, int lx, int ly)
+{
+    const float* p = base + ly * W + lx;
+    StT<float2> r;
+    if (EVEN) {
+        const float2 c = *reinterpret_cast<const float2*>(p);
+        const float2 rr = *reinterpret_cast<const float2*>(p + 2);
+        const float2 ll = *reinterpret_cast<const float2*>(p - 2);
+        r.c = c;
+        r.e = make_float2(c.y, rr.x);
+        r.w = make_float2(ll.y, c.x);
+        r.n = *reinterpret_cast<const float2*>(p + W);
+        r.s = *reinterpret_cast<const float2*>(p - W);
+    } else {
+        const float2 ww = *reinterpret_cast<const float2*>(p - 1);
+        const float2 ee = *reinterpret_cast<const float2*>(p + 1);
+        r.c = make_float2(ww.y, ee.x);
+        r.e = ee;
+        r.w = ww;
+        r.n = make_float2(p[W], p[W + 1]);
+        r.s = make_float2(p[-W], p[-W + 1]);
+    }
+    return r;
+}
+
+// a pair of neighbouring values of a plane; EVEN as for st2_at
+template <bool EVEN>
+__device__ __forceinline__ float2 ld2(const float* p)
+{
+    if (EVEN) return *reinterpret_cast<const float2*>(p);
+    return make_float2(p[0], p[1]);
+}
+template <bool EVEN>
+__device__ __forceinline__ void st2(float* p, float2 v)
+{
+    if (EVEN) {
+        *reinterpret_cast<float2*>(p) = v;
+    } else {
+        p[0] = v.x;
+        p[1] = v.y;
+    }
+}
+
 // Molecular field h = (alpha + beta |P|^2) P - kappa lap P (Eq. Ffunctional) from the stencil
 // of dP = P - P_ref: alpha + beta |P|^2 = A0 + beta (2 P_ref.dP + |dP|^2) has no cancellation.
-__device__ __forceinline__ void molecular(const Phys& ph, const St& dx, const St& dy, float& hx,
-                                          float& hy)
+template <class T>
+__device__ __forceinline__ void molecular(const Phys& ph, const StT<T>& dx, const StT<T>& dy, T& hx, T& hy)
 {
-    const float A = ph.A0 + ph.beta * (2.f * (ph.prx * dx.c + ph.pry * dy.c) + (dx.c * dx.c + dy.c * dy.c));
-    hx = A * (ph.prx + dx.c) - ph.kappa * (dx.e + dx.w + dx.n + dx.s - 4.f * dx.c);
-    hy = A * (ph.pry + dy.c) - ph.kappa * (dy.e + dy.w + dy.n + dy.s - 4.f * dy.c);
+    const T two_pd = vfma(ph.prx, dx.c, ph.pry * dy.c);
+    const T dd = vfma(dx.c, dx.c, dy.c * dy.c);
+    const T A = vfma(ph.beta, vfma(2.f, two_pd, dd), bc<T>(ph.A0));
+    const T lx = vfma(-4.f, dx.c, (dx.e + dx.w) + (dx.n + dx.s));
+    const T ly = vfma(-4.f, dy.c, (dy.e + dy.w) + (dy.n + dy.s));
+    hx = vfma(A, dx.c + ph.prx, -ph.kappa * lx);
+    hy = vfma(A, dy.c + ph.pry, -ph.kappa * ly);
 }
 
 // Right-hand sides of Eq. StiffCons (with the Jaumann derivative) and Eq. BE at one cell, for
 // the frozen u, Psi = (pxx, pyy, pxy), omega = Omega_xy; s = sigma (xx, yy, xy), p = dP (x, y).
-__device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, float ux, float uy,
-                                         float pxx, float pyy, float pxy, float om,
-                                         const St& s0, const St& s1, const St& s2,
-                                         const St& p0, const St& p1, float hx, float hy,
-                                         float* r)
+template <class T>
+__device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, T ux, T uy, T pxx, T pyy, T pxy,
+                                         T om, const StT<T>& s0, const StT<T>& s1, const StT<T>& s2,
+                                         const StT<T>& p0, const StT<T>& p1, T hx, T hy, T* r)
 {
     // stiffness C~(P) (App. B) from the table of a2, a4 and polynomials in P = P_ref + dP
-    const float Px = ph.prx + p0.c, Py = ph.pry + p1.c;
-    const float q = Px * Px + Py * Py;
-    float a2, a4;
+    const T Px = p0.c + ph.prx, Py = p1.c + ph.pry;
+    const T PxPx = Px * Px, PyPy = Py * Py;
+    const T q = PxPx + PyPy;
+    T a2, a4;
     lut_eval(lut, ph, q, a2, a4);
-    const float c2q = Px * Px - Py * Py, s2q = 2.f * Px * Py;
-    const float r2c2 = a2 * c2q, r2s2 = a2 * s2q;
-    const float r4c4 = a4 * (c2q * c2q - s2q * s2q), r4s4 = a4 * (2.f * c2q * s2q);
-    const float C11 = ph.kS8 + 0.5f * ph.dK * r2c2 + 0.125f * ph.kX * r4c4;
-    const float C12 = ph.kC12 - 0.125f * ph.kX * r4c4;
-    const float C13 = 0.25f * ph.kX * r4s4 + 0.5f * ph.dK * r2s2;
-    const float C22 = C11 - ph.dK * r2c2;
-    const float C23 = 0.5f * ph.dK * r2s2 - 0.25f * ph.kX * r4s4;
-    const float C33 = ph.kC33 - 0.25f * ph.kX * r4c4;
+    const T c2q = PxPx - PyPy, s2q = 2.f * (Px * Py);
+    const T r2c2 = a2 * c2q, r2s2 = a2 * s2q;
+    const T r4c4 = a4 * ((c2q - s2q) * (c2q + s2q)), r4s4 = a4 * (2.f * (c2q * s2q));
+    const T hds = (0.5f * ph.dK) * r2s2;
+    const T xc = (0.125f * ph.kX) * r4c4, xs = (0.25f * ph.kX) * r4s4;
+    const T C11 = vfma(0.5f * ph.dK, r2c2, bc<T>(ph.kS8)) + xc;
+    const T C12 = ph.kC12 - xc;
+    const T C13 = xs + hds;
+    const T C22 = vfma(-ph.dK, r2c2, C11);
+    const T C23 = hds - xs;
+    const T C33 = vfma(-2.f, xc, bc<T>(ph.kC33));
 
     // C psi - C s / eta_p = C (psi - s / eta_p)
-    const float v0 = pxx - ph.inv_eta * s0.c;
-    const float v1 = pyy - ph.inv_eta * s1.c;
-    const float v2 = pxy - ph.inv_eta * s2.c;
-    const float Cv0 = C11 * v0 + C12 * v1 + C13 * v2;
-    const float Cv1 = C12 * v0 + C22 * v1 + C23 * v2;
-    const float Cv2 = 0.5f * C13 * v0 + 0.5f * C23 * v1 + C33 * v2;
+    const T v0 = vfma(-ph.inv_eta, s0.c, pxx);
+    const T v1 = vfma(-ph.inv_eta, s1.c, pyy);
+    const T v2 = vfma(-ph.inv_eta, s2.c, pxy);
+    const T Cv0 = vfma(C11, v0, vfma(C12, v1, C13 * v2));
+    const T Cv1 = vfma(C12, v0, vfma(C22, v1, C23 * v2));
+    const T Cv2 = vfma(0.5f * C13, v0, vfma(0.5f * C23, v1, C33 * v2));
 
     // Jaumann rotation (Omega s - s Omega) = (2 w sxy, -2 w sxy, w (syy - sxx))
-    const float J0 = 2.f * om * s2.c;
-    const float J2 = om * (s1.c - s0.c);
+    const T J0 = 2.f * (om * s2.c);
+    const T J2 = om * (s1.c - s0.c);
 
+    // advection -(u.grad) y with central differences (uh = u / 2 times the plain differences)
+    const T uxh = 0.5f * ux, uyh = 0.5f * uy;
     const float D = ph.Dp;
-    r[0] = -(ux * 0.5f * (s0.e - s0.w) + uy * 0.5f * (s0.n - s0.s)) - J0 + Cv0 +
-           D * (s0.e + s0.w + s0.n + s0.s - 4.f * s0.c);
-    r[1] = -(ux * 0.5f * (s1.e - s1.w) + uy * 0.5f * (s1.n - s1.s)) + J0 + Cv1 +
-           D * (s1.e + s1.w + s1.n + s1.s - 4.f * s1.c);
-    r[2] = -(ux * 0.5f * (s2.e - s2.w) + uy * 0.5f * (s2.n - s2.s)) - J2 + Cv2 +
-           D * (s2.e + s2.w + s2.n + s2.s - 4.f * s2.c);
+    auto nadv = [&](const StT<T>& f) { return vfma(uxh, f.w - f.e, uyh * (f.s - f.n)); };
+    auto lap = [&](const StT<T>& f) { return vfma(-4.f, f.c, (f.e + f.w) + (f.n + f.s)); };
+    r[0] = vfma(D, lap(s0), (Cv0 - J0) + nadv(s0));
+    r[1] = vfma(D, lap(s1), (Cv1 + J0) + nadv(s1));
+    r[2] = vfma(D, lap(s2), (Cv2 - J2) + nadv(s2));
     // Eq. BE: -(u.grad)P - Omega P + xi Psi P - Gamma h
-    r[3] = -(ux * 0.5f * (p0.e - p0.w) + uy * 0.5f * (p0.n - p0.s)) - om * Py +
-           ph.xi * (pxx * Px + pxy * Py) - ph.Gamma * hx;
-    r[4] = -(ux * 0.5f * (p1.e - p1.w) + uy * 0.5f * (p1.n - p1.s)) + om * Px +
-           ph.xi * (pxy * Px + pyy * Py) - ph.Gamma * hy;
+    const T xp0 = vfma(pxx, Px, pxy * Py), xp1 = vfma(pxy, Px, pyy * Py);
+    r[3] = vfma(-ph.Gamma, hx, vfma(ph.xi, xp0, nadv(p0) - om * Py));
+    r[4] = vfma(-ph.Gamma, hy, vfma(ph.xi, xp1, vfma(om, Px, nadv(p1))));
 }
 
-// Velocity gradient at the cell (lx, ly) of a region of width W (u planes at ux, uy).
-__device__ __forceinline__ void vgrad(const float* ux, const float* uy, int W, int i, float& pxx,
-                                      float& pyy, float& pxy, float& om)
+// Velocity gradient from the stencils of u: Psi = (pxx, pyy, pxy), omega = Omega_xy.
+template <class T>
+__device__ __forceinline__ void vgrad(const StT<T>& ux, const StT<T>& uy, T& pxx, T& pyy, T& pxy, T& om)
 {
-    const float dxux = 0.5f * (ux[i + 1] - ux[i - 1]);
-    const float dyux = 0.5f * (ux[i + W] - ux[i - W]);
-    const float dxuy = 0.5f * (uy[i + 1] - uy[i - 1]);
-    const float dyuy = 0.5f * (uy[i + W] - uy[i - W]);
+    const T dxux = 0.5f * (ux.e - ux.w);
+    const T dyux = 0.5f * (ux.n - ux.s);
+    const T dxuy = 0.5f * (uy.e - uy.w);
+    const T dyuy = 0.5f * (uy.n - uy.s);
     pxx = dxux;
     pyy = dyuy;
     pxy = 0.5f * (dxuy + dyux);
     om = 0.5f * (dxuy - dyux);
+}
+
+// the same from two planes of width W at the flat index i (one cell)
+__device__ __forceinline__ void vgrad(const float* ux, const float* uy, int W, int i, float& pxx,
+                                      float& pyy, float& pxy, float& om)
+{
+    const St sx{ux[i], ux[i + 1], ux[i - 1], ux[i + W], ux[i - W]};
+    const St sy{uy[i], uy[i + 1], uy[i - 1], uy[i + W], uy[i - W]};
+    vgrad(sx, sy, pxx, pyy, pxy, om);
 }
 
 // Does the periodic interval [b, b + bw) meet [a, a + aw) on an axis of length n?
@@ -150,47 +224,51 @@ __device__ __forceinline__ bool meets(int a, int aw, int b, int bw, int n)
 
 // Ericksen stress (Sec. II C 1, kappa on the gradient term) and molecular field at one cell
 // from the stencils of dP = P - P_ref; E = (xx, xy, yx, yy).
-__device__ __forceinline__ void ericksen(const Phys& ph, const St& px, const St& py, float& hx,
-                                         float& hy, float* E)
+template <class T>
+__device__ __forceinline__ void ericksen(const Phys& ph, const StT<T>& px, const StT<T>& py, T& hx, T& hy, T* E)
 {
     molecular(ph, px, py, hx, hy);
-    const float Px = ph.prx + px.c, Py = ph.pry + py.c;
-    const float gxPx = 0.5f * (px.e - px.w), gyPx = 0.5f * (px.n - px.s);
-    const float gxPy = 0.5f * (py.e - py.w), gyPy = 0.5f * (py.n - py.s);
-    const float anti = Px * hy - hx * Py;
-    const float sym = Px * hy + hx * Py;
-    const float cross = ph.kappa * (gxPx * gyPx + gxPy * gyPy);
-    E[0] = ph.xi * Px * hx - ph.kappa * (gxPx * gxPx + gxPy * gxPy);
-    E[1] = -0.5f * anti + 0.5f * ph.xi * sym - cross;
-    E[2] = 0.5f * anti + 0.5f * ph.xi * sym - cross;
-    E[3] = ph.xi * Py * hy - ph.kappa * (gyPx * gyPx + gyPy * gyPy);
+    const T Px = px.c + ph.prx, Py = py.c + ph.pry;
+    const T gxPx = 0.5f * (px.e - px.w), gyPx = 0.5f * (px.n - px.s);
+    const T gxPy = 0.5f * (py.e - py.w), gyPy = 0.5f * (py.n - py.s);
+    const T Pxhy = Px * hy, hxPy = hx * Py;
+    const T anti = Pxhy - hxPy;
+    const T sym = Pxhy + hxPy;
+    const T cross = ph.kappa * vfma(gxPx, gyPx, gxPy * gyPy);
+    const T xs = (0.5f * ph.xi) * sym;
+    E[0] = vfma(ph.xi, Px * hx, -ph.kappa * vfma(gxPx, gxPx, gxPy * gxPy));
+    E[1] = vfma(-0.5f, anti, xs) - cross;
+    E[2] = vfma(0.5f, anti, xs) - cross;
+    E[3] = vfma(ph.xi, Py * hy, -ph.kappa * vfma(gyPx, gyPx, gyPy * gyPy));
 }
 
 // div sigma^p from the stencils of (sxx, syy, sxy).
-__device__ __forceinline__ void div_sigma(const St& sxx, const St& syy, const St& sxy, float& fx, float& fy)
+template <class T>
+__device__ __forceinline__ void div_sigma(const StT<T>& sxx, const StT<T>& syy, const StT<T>& sxy, T& fx, T& fy)
 {
-    fx = 0.5f * (sxx.e - sxx.w) + 0.5f * (sxy.n - sxy.s);
-    fy = 0.5f * (sxy.e - sxy.w) + 0.5f * (syy.n - syy.s);
+    fx = 0.5f * ((sxx.e - sxx.w) + (sxy.n - sxy.s));
+    fy = 0.5f * ((sxy.e - sxy.w) + (syy.n - syy.s));
 }
 
 // div sigma^E from the stencils of (xx, xy, yx, yy): only e, w of xx, yx and n, s of xy, yy are read.
-__device__ __forceinline__ void div_ericksen(const St& exx, const St& exy, const St& eyx, const St& eyy,
-                                             float& fx, float& fy)
+template <class T>
+__device__ __forceinline__ void div_ericksen(const StT<T>& exx, const StT<T>& exy, const StT<T>& eyx,
+                                             const StT<T>& eyy, T& fx, T& fy)
 {
-    fx = 0.5f * (exx.e - exx.w) + 0.5f * (exy.n - exy.s);
-    fy = 0.5f * (eyx.e - eyx.w) + 0.5f * (eyy.n - eyy.s);
+    fx = 0.5f * ((exx.e - exx.w) + (exy.n - exy.s));
+    fy = 0.5f * ((eyx.e - eyx.w) + (eyy.n - eyy.s));
 }
 
 // Moments (Eq. rhoDef, Eq. vDef, Guo half force) of the shifted populations d_n.
-__device__ __forceinline__ void moments(const Phys& ph, const float* d, float Fx, float Fy, float& drho,
-                                        float& ux, float& uy)
+template <class T>
+__device__ __forceinline__ void moments(const Phys& ph, const T* d, T Fx, T Fy, T& drho, T& ux, T& uy)
 {
-    drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const float jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-    const float jy = (d[2] - d[4]) + (d[5] - d[8]) + (d[6] - d[7]);
-    const float inv = __frcp_rn(ph.rho0 + drho);
-    ux = (jx + 0.5f * Fx) * inv;
-    uy = (jy + 0.5f * Fy) * inv;
+    drho = (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]))) + d[8];
+    const T jx = ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
+    const T jy = ((d[2] - d[4]) + (d[5] - d[8])) + (d[6] - d[7]);
+    const T inv = vrcp(drho + ph.rho0);
+    ux = vfma(0.5f, Fx, jx) * inv;
+    uy = vfma(0.5f, Fy, jy) * inv;
 }
 
 // BGK collision with the Guo source (Eq. LB, Eq. BGK): the changes D_n = d*_n - d_n of one cell,
@@ -202,37 +280,37 @@ __device__ __forceinline__ void moments(const Phys& ph, const float* d, float Fx
 // over a uniform flow) would leak momentum into every cell alike, so the FP32 changes are
 // corrected to exactly sum D_n = 0 and sum c_n D_n = F (pair and rest-population corrections).
 // Order: n = 0 rest; 1..4 = +x, +y, -x, -y; 5..8 = (+,+), (-,+), (-,-), (+,-).
-__device__ __forceinline__ void collide(const Phys& ph, const float* d, float drho, float ux, float uy,
-                                        float Fx, float Fy, float* D)
+template <class T>
+__device__ __forceinline__ void collide(const Phys& ph, const T* d, T drho, T ux, T uy, T Fx, T Fy, T* D)
 {
     const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-    const float rho = ph.rho0 + drho;
-    const float uu = 1.5f * (ux * ux + uy * uy);
-    const float uF3 = 3.f * (ux * Fx + uy * Fy);
     const float om = ph.omega, g = ph.guo;
-    const float base = drho - rho * uu;                 // even part common to all directions
-    const float rho3 = 3.f * rho;
-    D[0] = om * (w0 * base - d[0]) - g * w0 * uF3;
+    const T nrho = (-ph.rho0) - drho;                   // -rho
+    const T uu = 1.5f * vfma(ux, ux, uy * uy);
+    const T nuF3 = -3.f * vfma(ux, Fx, uy * Fy);        // -3 u.F
+    const T base = vfma(nrho, uu, drho);                // even part common to all directions
+    const T rho3 = -3.f * nrho, rho45 = -4.5f * nrho;
+    D[0] = vfma(om, w0 * base - d[0], (g * w0) * nuF3);
     // one pair (n, opposite m) with velocity c: cu = c.u, cF = c.F
-    auto pair = [&](int n, int m, float w, float cu, float cF) {
-        const float ev = w * fmaf(4.5f * rho * cu, cu, base);      // even part of d^eq
-        const float od = w * rho3 * cu;                              // odd part of d^eq
-        const float Sev = w * fmaf(9.f * cu, cF, -uF3);             // even part of S
-        const float Sod = 3.f * w * cF;                              // odd part of S
-        D[n] = om * ((ev + od) - d[n]) + g * (Sev + Sod);
-        D[m] = om * ((ev - od) - d[m]) + g * (Sev - Sod);
+    auto pair = [&](int n, int m, float w, T cu, T cF) {
+        const T ev = w * vfma(rho45 * cu, cu, base);              // even part of d^eq
+        const T od = w * (rho3 * cu);                              // odd part of d^eq
+        const T Sev = w * vfma(9.f * cu, cF, nuF3);               // even part of S
+        const T Sod = (3.f * w) * cF;                              // odd part of S
+        D[n] = vfma(om, (ev + od) - d[n], g * (Sev + Sod));
+        D[m] = vfma(om, (ev - od) - d[m], g * (Sev - Sod));
     };
     pair(1, 3, w1, ux, Fx);
     pair(2, 4, w1, uy, Fy);
     pair(5, 7, w5, ux + uy, Fx + Fy);
     pair(6, 8, w5, uy - ux, Fy - Fx);
-    const float ex = ((D[1] - D[3]) + (D[5] - D[6]) + (D[8] - D[7])) - Fx;
-    const float ey = ((D[2] - D[4]) + (D[5] - D[8]) + (D[6] - D[7])) - Fy;
-    D[1] -= 0.5f * ex;
-    D[3] += 0.5f * ex;
-    D[2] -= 0.5f * ey;
-    D[4] += 0.5f * ey;
-    D[0] -= ((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8])) + D[0];
+    const T ex = (((D[1] - D[3]) + (D[5] - D[6])) + (D[8] - D[7])) - Fx;
+    const T ey = (((D[2] - D[4]) + (D[5] - D[8])) + (D[6] - D[7])) - Fy;
+    D[1] = vfma(-0.5f, ex, D[1]);
+    D[3] = vfma(0.5f, ex, D[3]);
+    D[2] = vfma(-0.5f, ey, D[2]);
+    D[4] = vfma(0.5f, ey, D[4]);
+    D[0] = D[0] - ((((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8]))) + D[0]);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -108,7 +108,9 @@ struct NodeArgs {
 };
 
 // Launchers (return cudaError_t of the launch).
-cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl = false);
+// pair: the tile kernel with two cells per thread (paired FP32 instructions)
+cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl = false,
+                         bool pair = false);
 // column-strip sweep (lb_sweep.cu): eligibility, rows per CTA chunk, CTA count, launch
 bool sweep_eligible(int nx, int ny);
 int sweep_chunk(int nx, int ny, int n_sm);

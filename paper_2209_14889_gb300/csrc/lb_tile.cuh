@@ -8,12 +8,13 @@
 //   IB (halo 2)  spreading f_IB(r) = sum_a f_a phi phi (App. A), gathered per cell over the
 //                ring nodes near the tile in index order (no atomics, bitwise reproducible);
 //   C  (halo 2)  F = f_IB + div sigma^p + div sigma^E; moments rho = rho0 + sum d_n,
-//                u = (sum c_n d_n + F/2) / rho (Eq. rhoDef, Eq. vDef, Guo half force);
+//                u = (sum c_n d_n + F/2) / rho (Eq. rhoDef, Eq. vDef, Guo half force); on the
+//                owned cells the BGK collision with the Guo source, pushed to the neighbours
+//                (Eq. LB, BGK), and the FP64 readout partial sums;
 //   D  (halo 1)  velocity gradient (Psi, omega), RHS of Eq. StiffCons and Eq. BE, Heun
 //                predictor y* = y + RHS(y);
-//   E  (tile)    BGK collision with the Guo source, pushed to the neighbours (Eq. LB, BGK);
-//                Heun corrector y' = y + (RHS(y) + RHS(y*))/2 with u frozen at t; u and f^p
-//                on the ring work boxes for the node kernel; FP64 readout partial sums.
+//   E  (tile)    Heun corrector y' = y + (RHS(y) + RHS(y*))/2 with u frozen at t; u and f^p
+//                on the ring work boxes for the node kernel.
 // Halo cells are recomputed redundantly, so one launch reads and writes each stored value
 // once from HBM (the halo re-reads hit L2).  Populations are stored shifted, d_n = h_n - w_n rho0,
 // so that FP32 keeps the small deviations that carry the flow.
@@ -47,8 +48,8 @@ struct TileGeo {
     static constexpr int OFF_E = OFF_S + 3 * R3;                  // sigma^E  [4][R3]  | y* [5][R1]
     static constexpr int SZ_E = cmax(4 * R3, 5 * R1);
     static constexpr int OFF_H = OFF_E + SZ_E;                    // h        [2][R3]
-    static constexpr int OFF_M = OFF_H + 2 * R3;                  // drho,ux,uy,Fx,Fy [5][R2]
-    static constexpr int OFF_R = OFF_M + 5 * R2;                  // RHS(y)   [5][R0] | f_IB [2][R2]
+    static constexpr int OFF_M = OFF_H + 2 * R3;                  // drho, ux, uy [3][R2]
+    static constexpr int OFF_R = OFF_M + 3 * R2;                  // RHS(y)   [5][R0] | f_IB [2][R2]
     static constexpr int SZ_R = cmax(5 * R0, 2 * R2);
     static constexpr int OFF_N = al4(OFF_R + SZ_R);               // nodes    [NT] float4 (cell, frac)
     static constexpr int OFF_NF = OFF_N + 4 * NT;                 // node forces [NT] float2
@@ -61,89 +62,142 @@ struct TileGeo {
     static_assert(OFF_N % 4 == 0 && OFF_NF % 2 == 0 && OFF_RED % 2 == 0, "shared-memory alignment");
 };
 
-// One TX x TY tile (tile coordinates bx, by) of the step; sm: TileGeo<TX, TY>::SMEM_BYTES of
-// shared memory.  Called by k_fused (one tile per CTA) and by the batched persistent kernel.
-template <int MODE, int PREC, int TX, int TY, bool COH = false>
-__device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, int tile_index, float* sm)
+// Shared-memory views of one tile (layout of TileGeo<TX, TY>).
+template <int TX, int TY>
+struct TileMem {
+    using G = TileGeo<TX, TY>;
+    float* sP;          // dP           [2][R4]
+    float* sS;          // sigma        [3][R3]
+    float* sE;          // sigma^E      [4][R3]
+    float* sY;          // y*           [5][R1]  (over sigma^E once C is done)
+    float* sH;          // h            [2][R3]
+    float* sM;          // drho (moments mode only), ux, uy  [3][R2]
+    float* sR;          // RHS(y)       [5][R0]
+    float* sFib;        // f_IB         [2][R2]  (over RHS(y) until D)
+    float4* sNode;
+    float2* sNodeF;
+    int* sXi;
+    int* sYi;
+    int* sScan;
+    double* sRed;
+    __device__ __forceinline__ explicit TileMem(float* sm)
+        : sP(sm + G::OFF_P), sS(sm + G::OFF_S), sE(sm + G::OFF_E), sY(sm + G::OFF_E), sH(sm + G::OFF_H),
+          sM(sm + G::OFF_M), sR(sm + G::OFF_R), sFib(sm + G::OFF_R),
+          sNode(reinterpret_cast<float4*>(sm + G::OFF_N)), sNodeF(reinterpret_cast<float2*>(sm + G::OFF_NF)),
+          sXi(reinterpret_cast<int*>(sm + G::OFF_XI)), sYi(reinterpret_cast<int*>(sm + G::OFF_YI)),
+          sScan(reinterpret_cast<int*>(sm + G::OFF_SC)), sRed(reinterpret_cast<double*>(sm + G::OFF_RED))
+    {
+    }
+};
+
+// a pair of neighbouring values (flat indices g, g + 1, g even, plane size even) of one field
+// plane of the state, as FP32
+template <int PREC, bool COH>
+__device__ __forceinline__ float2 ld_fld2(const void* src, long long NP, int plane, long long g)
+{
+    if (PREC == PREC_FP32)
+        return ld_state<float2, COH>(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(src) + plane * NP + g));
+    const unsigned b = ld_state<unsigned, COH>(
+        reinterpret_cast<const unsigned*>(reinterpret_cast<const unsigned short*>(src) + plane * NP + g));
+    const unsigned short lo = (unsigned short)(b & 0xFFFFu), hi = (unsigned short)(b >> 16);
+    if (plane >= PL_PX) return make_float2(__half2float(__ushort_as_half(lo)), __half2float(__ushort_as_half(hi)));
+    return make_float2(__uint_as_float((unsigned)lo << 16), __uint_as_float((unsigned)hi << 16));
+}
+
+// ---- A: wrapped index tables, f_IB cleared, P staged with a 4-cell halo and sigma with 3 ----
+// With nx even every staged row starts at an even column (x0 - 4, wrapped), so the rows are read
+// as aligned pairs that never straddle the periodic seam; each thread issues all its loads
+// before its shared-memory stores.  Odd nx takes single-value loads.
+template <int PREC, bool COH, int TX, int TY>
+__device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
 {
     using G = TileGeo<TX, TY>;
-    constexpr int R4W = G::R4W, R4H = G::R4H, R4 = G::R4;
-    constexpr int R3W = G::R3W, R3 = G::R3;
-    constexpr int R2W = G::R2W, R2H = G::R2H, R2 = G::R2;
-    constexpr int R1W = G::R1W, R1 = G::R1;
-    constexpr int R0 = G::R0;
-    constexpr int OFF_P = G::OFF_P, OFF_S = G::OFF_S, OFF_E = G::OFF_E, OFF_H = G::OFF_H;
-    constexpr int OFF_M = G::OFF_M, OFF_R = G::OFF_R, OFF_N = G::OFF_N, OFF_NF = G::OFF_NF;
-    constexpr int OFF_XI = G::OFF_XI, OFF_YI = G::OFF_YI, OFF_SC = G::OFF_SC, OFF_RED = G::OFF_RED;
-    float* sP = sm + OFF_P;
-    float* sS = sm + OFF_S;
-    float* sE = sm + OFF_E;
-    float* sY = sm + OFF_E;      // y* after sigma^E is dead
-    float* sH = sm + OFF_H;
-    float* sM = sm + OFF_M;
-    float* sR = sm + OFF_R;
-    float* sFib = sm + OFF_R;    // f_IB before RHS(y) is written
-    const float* sL = reinterpret_cast<const float*>(a.lut);   // C~ table (global, L1)
-    float4* sNode = reinterpret_cast<float4*>(sm + OFF_N);
-    float2* sNodeF = reinterpret_cast<float2*>(sm + OFF_NF);
-    int* sXi = reinterpret_cast<int*>(sm + OFF_XI);
-    int* sYi = reinterpret_cast<int*>(sm + OFF_YI);
-    int* sScan = reinterpret_cast<int*>(sm + OFF_SC);
-    double* sRed = reinterpret_cast<double*>(sm + OFF_RED);
-
+    constexpr int R4W = G::R4W, R4 = G::R4, R3W = G::R3W, R3 = G::R3;
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const long long NP = a.plane;
-    const int x0 = bx * TX, y0 = by * TY;
-    const Phys ph = a.ph;
-    const void* __restrict__ src = a.src;
-
-    for (int i = tid; i < R4W; i += NT) sXi[i] = wrapn(x0 - 4 + i, nx);
-    for (int i = tid; i < R4H; i += NT) sYi[i] = wrapn(y0 - 4 + i, ny);
-    for (int i = tid; i < 2 * R2; i += NT) sFib[i] = 0.f;
+    const void* src = a.src;
+    for (int i = tid; i < R4W; i += NT) m.sXi[i] = wrapn(x0 - 4 + i, nx);
+    for (int i = tid; i < G::R4H; i += NT) m.sYi[i] = wrapn(y0 - 4 + i, ny);
+    for (int i = tid; i < 2 * G::R2; i += NT) m.sFib[i] = 0.f;
     __syncthreads();
-
-    // ---- A: stage P (halo 4) and sigma (halo 3) ---------------------------------------------
-    for (int i = tid; i < R4; i += NT) {
-        const int ly = i / R4W, lx = i - ly * R4W;
-        const long long g = (long long)sYi[ly] * nx + sXi[lx];
-        sP[i] = ld_fld<PREC, COH>(src, NP, PL_PX, g);
-        sP[R4 + i] = ld_fld<PREC, COH>(src, NP, PL_PY, g);
-    }
-    for (int i = tid; i < R3; i += NT) {
-        const int ly = i / R3W, lx = i - ly * R3W;
-        const long long g = (long long)sYi[ly + 1] * nx + sXi[lx + 1];
-        sS[i] = ld_fld<PREC, COH>(src, NP, PL_SXX, g);
-        sS[R3 + i] = ld_fld<PREC, COH>(src, NP, PL_SYY, g);
-        sS[2 * R3 + i] = ld_fld<PREC, COH>(src, NP, PL_SXY, g);
-    }
-    __syncthreads();
-
-    // ---- B: molecular field and Ericksen stress on the halo-3 region ------------------------
-    for (int i = tid; i < R3; i += NT) {
-        const int ly = i / R3W, lx = i - ly * R3W;
-        const St px = st_at(sP, R4W, lx + 1, ly + 1);         // dP stencils
-        const St py = st_at(sP + R4, R4W, lx + 1, ly + 1);
-        float hx, hy, E[4];
-        ericksen(ph, px, py, hx, hy, E);
-        sH[i] = hx;
-        sH[R3 + i] = hy;
-        if (ph.ericksen) {
-            sE[i] = E[0];
-            sE[R3 + i] = E[1];
-            sE[2 * R3 + i] = E[2];
-            sE[3 * R3 + i] = E[3];
+    if ((nx & 1) == 0) {
+        // P: pairs of the halo-4 rows; sigma: pairs of the rows y0-3 .. y0+TY+2 over the halo-4
+        // columns, of which the outermost column on each side is dropped
+        constexpr int HP = R4W / 2;                      // pairs per row
+        constexpr int NPP = R4 / 2, NSP = HP * G::R3H;   // pairs of P, of sigma
+        constexpr int KP = (NPP + NT - 1) / NT, KS = (NSP + NT - 1) / NT;
+        float2 vp[KP][2], vs[KS][3];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int q = tid + k * NT;
+            if (q < NPP) {
+                const int ly = q / HP, lx = 2 * (q - ly * HP);
+                const long long g = (long long)m.sYi[ly] * nx + m.sXi[lx];
+                vp[k][0] = ld_fld2<PREC, COH>(src, NP, PL_PX, g);
+                vp[k][1] = ld_fld2<PREC, COH>(src, NP, PL_PY, g);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int q = tid + k * NT;
+            if (q < NSP) {
+                const int ly = q / HP, lx = 2 * (q - ly * HP);
+                const long long g = (long long)m.sYi[ly + 1] * nx + m.sXi[lx];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) vs[k][c] = ld_fld2<PREC, COH>(src, NP, PL_SXX + c, g);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int q = tid + k * NT;
+            if (q < NPP) {
+                st2<true>(m.sP + 2 * q, vp[k][0]);
+                st2<true>(m.sP + R4 + 2 * q, vp[k][1]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int q = tid + k * NT;
+            if (q < NSP) {
+                const int ly = q / HP, lx = 2 * (q - ly * HP);   // halo-4 column of the pair
+                const int i = ly * R3W + lx - 1;                 // halo-3 index of its first value
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (lx >= 1) m.sS[c * R3 + i] = vs[k][c].x;
+                    if (lx + 1 <= R3W) m.sS[c * R3 + i + 1] = vs[k][c].y;
+                }
+            }
+        }
+    } else {
+        for (int i = tid; i < R4; i += NT) {
+            const int ly = i / R4W, lx = i - ly * R4W;
+            const long long g = (long long)m.sYi[ly] * nx + m.sXi[lx];
+            m.sP[i] = ld_fld<PREC, COH>(src, NP, PL_PX, g);
+            m.sP[R4 + i] = ld_fld<PREC, COH>(src, NP, PL_PY, g);
+        }
+        for (int i = tid; i < R3; i += NT) {
+            const int ly = i / R3W, lx = i - ly * R3W;
+            const long long g = (long long)m.sYi[ly + 1] * nx + m.sXi[lx + 1];
+            m.sS[i] = ld_fld<PREC, COH>(src, NP, PL_SXX, g);
+            m.sS[R3 + i] = ld_fld<PREC, COH>(src, NP, PL_SYY, g);
+            m.sS[2 * R3 + i] = ld_fld<PREC, COH>(src, NP, PL_SXY, g);
         }
     }
+    __syncthreads();
+}
 
-    // The state at t was written two kernels back; the node forces, ring boxes, step counter and
-    // readout buffers come from the node kernel just before this one.
-    pdl_wait();
-    pdl_trigger();
-
-    // ---- IB: gather f_IB on the halo-2 region from the nodes of every ring near the tile ----
-    // A node at cell c with fraction f sits at (c - o) + f relative to the region origin o; the
-    // integer part is kept apart from the fraction so that kernel arguments stay exact in FP32.
+// ---- IB: gather f_IB on the halo-2 region from the nodes of every ring near the tile ----
+// A node at cell c with fraction f sits at (c - o) + f relative to the region origin o; the
+// integer part is kept apart from the fraction so that kernel arguments stay exact in FP32.
+// Each cell sums the nodes in ring and index order, so the result does not depend on the tile.
+template <int TX, int TY>
+__device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
+{
+    using G = TileGeo<TX, TY>;
+    constexpr int R2W = G::R2W, R2H = G::R2H, R2 = G::R2;
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
     const bool small = (nx < R2W + 8) || (ny < R2H + 8);   // region may wrap onto itself
     for (int r = 0; r < a.n_rings; ++r) {
         const RingDev& R = a.rings[r];
@@ -169,30 +223,30 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             // order-preserving compaction of the kept nodes
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             const int lane = tid & 31, wid = tid >> 5;
-            if (lane == 0) sScan[wid] = __popc(bal);
+            if (lane == 0) m.sScan[wid] = __popc(bal);
             __syncthreads();
             if (tid == 0) {
                 int acc = 0;
                 for (int w = 0; w < NT / 32; ++w) {
-                    const int c = sScan[w];
-                    sScan[w] = acc;
+                    const int c = m.sScan[w];
+                    m.sScan[w] = acc;
                     acc += c;
                 }
-                sScan[NT / 32] = acc;
+                m.sScan[NT / 32] = acc;
             }
             __syncthreads();
             if (keep) {
-                const int slot = sScan[wid] + __popc(bal & ((1u << lane) - 1u));
-                sNode[slot] = make_float4(__int_as_float(cxr), __int_as_float(cyr), fr.x, fr.y);
-                sNodeF[slot] = f;
+                const int slot = m.sScan[wid] + __popc(bal & ((1u << lane) - 1u));
+                m.sNode[slot] = make_float4(__int_as_float(cxr), __int_as_float(cyr), fr.x, fr.y);
+                m.sNodeF[slot] = f;
             }
             __syncthreads();
-            const int cnt = sScan[NT / 32];
+            const int cnt = m.sScan[NT / 32];
             for (int i = tid; i < R2; i += NT) {
                 const int ly = i / R2W, lx = i - ly * R2W;
                 float fx = 0.f, fy = 0.f;
                 for (int j = 0; j < cnt; ++j) {
-                    const float4 q = sNode[j];
+                    const float4 q = m.sNode[j];
                     int ddx = __float_as_int(q.x) - lx, ddy = __float_as_int(q.y) - ly;
                     if (small) {
                         ddx = mimg(ddx, nx);
@@ -201,124 +255,171 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                     const float dx = (float)ddx + q.z, dy = (float)ddy + q.w;
                     if (fabsf(dx) < 2.f && fabsf(dy) < 2.f) {
                         const float w = phi(dx) * phi(dy);
-                        const float2 fq = sNodeF[j];
+                        const float2 fq = m.sNodeF[j];
                         fx += fq.x * w;
                         fy += fq.y * w;
                     }
                 }
-                sFib[i] += fx;
-                sFib[R2 + i] += fy;
+                m.sFib[i] += fx;
+                m.sFib[R2 + i] += fy;
             }
             __syncthreads();
         }
     }
     __syncthreads();
+}
 
-    // ---- C: total force and moments on the halo-2 region ------------------------------------
+// u(t) (and f^p(t) = div sigma^p on readout steps) of the owned cell (gx, gy) on the work box of
+// every ring containing it; j3: the cell's index in the halo-3 sigma planes (width R3W).
+template <int R3, int R3W>
+__device__ __forceinline__ void box_write(const FusedArgs& a, int gx, int gy, float ux, float uy, bool readout,
+                                          const float* sS, int j3)
+{
+    const int nx = a.nx, ny = a.ny;
+    for (int rr = 0; rr < a.n_rings; ++rr) {
+        const RingDev& R = a.rings[rr];
+        int bx = gx - R.box_x0; if (bx < 0) bx += nx;
+        int by = gy - R.box_y0; if (by < 0) by += ny;
+        if (bx < R.box_w && by < R.box_h) {
+            const long long o = R.box_off + (long long)by * R.cap_w + bx;
+            const long long cap = (long long)R.cap_w * R.cap_h;
+            a.ubox[o] = ux;
+            a.ubox[o + cap] = uy;
+            if (readout) {
+                a.fpbox[o] = 0.5f * (sS[j3 + 1] - sS[j3 - 1]) + 0.5f * (sS[2 * R3 + j3 + R3W] - sS[2 * R3 + j3 - R3W]);
+                a.fpbox[o + cap] = 0.5f * (sS[2 * R3 + j3 + 1] - sS[2 * R3 + j3 - 1]) +
+                                   0.5f * (sS[R3 + j3 + R3W] - sS[R3 + j3 - R3W]);
+            }
+        }
+    }
+}
+
+// fixed-order block reduction of the FP64 readout sums of the tile into its partial slot
+__device__ __forceinline__ void readout_reduce(const FusedArgs& a, const double* acc, double* sRed, int tile_index)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sRed[c * (NT / 32) + wid] = v;
+    }
+    __syncthreads();
+    if (tid < 5) {
+        double v = 0.0;
+        for (int w = 0; w < NT / 32; ++w) v += sRed[tid * (NT / 32) + w];
+        a.partials[(long long)tile_index * 5 + tid] = v;
+    }
+}
+
+// the moments of the owned cells to the moments_out planes (MODE_MOMENTS)
+template <int TX, int TY>
+__device__ __forceinline__ void moments_out(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
+{
+    using G = TileGeo<TX, TY>;
+    const long long NP = a.plane;
+    for (int i = threadIdx.x; i < G::R0; i += NT) {
+        const int ly = i / TX, lx = i - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= a.nx || gy >= a.ny) continue;
+        const int j = (ly + 2) * G::R2W + lx + 2;
+        const long long g = (long long)gy * a.nx + gx;
+        a.moments_out[g] = m.sM[j];
+        a.moments_out[NP + g] = m.sM[G::R2 + j];
+        a.moments_out[2 * NP + g] = m.sM[2 * G::R2 + j];
+    }
+}
+
+// D2Q9 (Sec. II A): c_n, n = 0..8
+__device__ constexpr int C_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ constexpr int C_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// One TX x TY tile (tile coordinates bx, by) of the step, one cell per thread and iteration;
+// sm: TileGeo<TX, TY>::SMEM_BYTES of shared memory.  Used by the sweep comparison and kept as the
+// reference form of the paired step below.
+template <int MODE, int PREC, int TX, int TY, bool COH = false>
+__device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, int tile_index, float* sm)
+{
+    using G = TileGeo<TX, TY>;
+    constexpr int R4W = G::R4W, R4 = G::R4;
+    constexpr int R3W = G::R3W, R3 = G::R3;
+    constexpr int R2W = G::R2W, R2 = G::R2;
+    constexpr int R1W = G::R1W, R1 = G::R1;
+    constexpr int R0 = G::R0;
+    const TileMem<TX, TY> m(sm);
+    const float* sL = reinterpret_cast<const float*>(a.lut);   // C~ table (global, L1)
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const long long NP = a.plane;
+    const int x0 = bx * TX, y0 = by * TY;
+    const Phys ph = a.ph;
+    const void* src = a.src;
+
+    stage<PREC, COH>(a, m, x0, y0);
+
+    // ---- B: molecular field and Ericksen stress on the halo-3 region ------------------------
+    for (int i = tid; i < R3; i += NT) {
+        const int ly = i / R3W, lx = i - ly * R3W;
+        const St px = st_at(m.sP, R4W, lx + 1, ly + 1);         // dP stencils
+        const St py = st_at(m.sP + R4, R4W, lx + 1, ly + 1);
+        float hx, hy, E[4];
+        ericksen(ph, px, py, hx, hy, E);
+        m.sH[i] = hx;
+        m.sH[R3 + i] = hy;
+        if (ph.ericksen) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) m.sE[c * R3 + i] = E[c];
+        }
+    }
+
+    // The state at t was written two kernels back; the node forces, ring boxes, step counter and
+    // readout buffers come from the node kernel just before this one.
+    pdl_wait();
+    pdl_trigger();
+    ib_gather(a, m, x0, y0);
+
+    // ---- C: total force and moments on the halo-2 region; collision of the owned cells ------
+    // Owned cells collide here, with their populations still in registers, and push to
+    // x + c_n (Eq. LB, Eq. BGK, Guo source; exactly conservative FP32 increments).
+    const long long t = a.ctl->t;
+    const bool readout = (t % a.every) == 0;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    void* dst = a.dst;
     for (int i = tid; i < R2; i += NT) {
         const int ly = i / R2W, lx = i - ly * R2W;
-        const int j3 = (ly + 1) * R3W + lx + 1;
         float Fx, Fy;
-        div_sigma(st_at(sS, R3W, lx + 1, ly + 1), st_at(sS + R3, R3W, lx + 1, ly + 1),
-                  st_at(sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
+        div_sigma(st_at(m.sS, R3W, lx + 1, ly + 1), st_at(m.sS + R3, R3W, lx + 1, ly + 1),
+                  st_at(m.sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
         if (ph.ericksen) {
             float ex, ey;
-            div_ericksen(st_at(sE, R3W, lx + 1, ly + 1), st_at(sE + R3, R3W, lx + 1, ly + 1),
-                         st_at(sE + 2 * R3, R3W, lx + 1, ly + 1), st_at(sE + 3 * R3, R3W, lx + 1, ly + 1),
+            div_ericksen(st_at(m.sE, R3W, lx + 1, ly + 1), st_at(m.sE + R3, R3W, lx + 1, ly + 1),
+                         st_at(m.sE + 2 * R3, R3W, lx + 1, ly + 1), st_at(m.sE + 3 * R3, R3W, lx + 1, ly + 1),
                          ex, ey);
             Fx += ex;
             Fy += ey;
         }
-        (void)j3;
-        Fx += sFib[i];
-        Fy += sFib[R2 + i];
-        const long long g = (long long)sYi[ly + 2] * nx + sXi[lx + 2];
+        Fx += m.sFib[i];
+        Fy += m.sFib[R2 + i];
+        const long long g = (long long)m.sYi[ly + 2] * nx + m.sXi[lx + 2];
         float d[9];
 #pragma unroll
         for (int n = 0; n < 9; ++n) d[n] = ld_pop<PREC, COH>(src, NP, n, g);
         float drho, ux, uy;
         moments(ph, d, Fx, Fy, drho, ux, uy);
-        sM[i] = drho;
-        sM[R2 + i] = ux;
-        sM[2 * R2 + i] = uy;
-        sM[3 * R2 + i] = Fx;
-        sM[4 * R2 + i] = Fy;
-    }
-    __syncthreads();
-
-    if (MODE == MODE_MOMENTS) {
-        for (int i = tid; i < R0; i += NT) {
-            const int ly = i / TX, lx = i - ly * TX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= nx || gy >= ny) continue;
-            const int j = (ly + 2) * R2W + lx + 2;
-            const long long g = (long long)gy * nx + gx;
-            a.moments_out[g] = sM[j];
-            a.moments_out[NP + g] = sM[R2 + j];
-            a.moments_out[2 * NP + g] = sM[2 * R2 + j];
-        }
-        return;
-    }
-
-    // ---- D: predictor on the halo-1 region --------------------------------------------------
-    for (int i = tid; i < R1; i += NT) {
-        const int ly = i / R1W, lx = i - ly * R1W;
-        const int j2 = (ly + 1) * R2W + lx + 1;
-        float pxx, pyy, pxy, om;
-        vgrad(sM + R2, sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
-        const St s0 = st_at(sS, R3W, lx + 2, ly + 2);
-        const St s1 = st_at(sS + R3, R3W, lx + 2, ly + 2);
-        const St s2 = st_at(sS + 2 * R3, R3W, lx + 2, ly + 2);
-        const St p0 = st_at(sP, R4W, lx + 3, ly + 3);
-        const St p1 = st_at(sP + R4, R4W, lx + 3, ly + 3);
-        const int j3 = (ly + 2) * R3W + lx + 2;
-        float r[5];
-        rhs_cell(ph, sL, sM[R2 + j2], sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
-                 sH[j3], sH[R3 + j3], r);
-        // y* (the sigma^E buffer is dead: C has finished)
-        sY[i] = s0.c + r[0];
-        sY[R1 + i] = s1.c + r[1];
-        sY[2 * R1 + i] = s2.c + r[2];
-        sY[3 * R1 + i] = p0.c + r[3];
-        sY[4 * R1 + i] = p1.c + r[4];
-        if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) {
-            const int j0 = (ly - 1) * TX + (lx - 1);
-#pragma unroll
-            for (int c = 0; c < 5; ++c) sR[c * R0 + j0] = r[c];
-        }
-    }
-    __syncthreads();
-
-    // ---- E: collide + push-stream, corrector, box writes, readout sums ----------------------
-    const long long t = a.ctl->t;
-    const bool readout = (t % a.every) == 0;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    void* __restrict__ dst = a.dst;
-    // D2Q9 (Sec. II A): c_n and w_n, n = 0..8
-    const int c_cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int c_cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    for (int i = tid; i < R0; i += NT) {
-        const int ly = i / TX, lx = i - ly * TX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= nx || gy >= ny) continue;
-        const long long g = (long long)gy * nx + gx;
-        const int j2 = (ly + 2) * R2W + lx + 2;
-        const float drho = sM[j2], ux = sM[R2 + j2], uy = sM[2 * R2 + j2];
-        const float Fx = sM[3 * R2 + j2], Fy = sM[4 * R2 + j2];
-
-        // collision (Eq. LB, Eq. BGK, Guo source; exactly conservative FP32 increments),
-        // pushed to x + c_n
-        {
-            float dn[9], D[9];
-#pragma unroll
-            for (int n = 0; n < 9; ++n) dn[n] = ld_pop<PREC, COH>(src, NP, n, g);
-            collide(ph, dn, drho, ux, uy, Fx, Fy, D);
+        m.sM[R2 + i] = ux;
+        m.sM[2 * R2 + i] = uy;
+        if (MODE == MODE_MOMENTS) m.sM[i] = drho;
+        const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && x0 + lx - 2 < nx && y0 + ly - 2 < ny;
+        if (MODE == MODE_STEP && own) {
+            float D[9];
+            collide(ph, d, drho, ux, uy, Fx, Fy, D);
             long long gd[9];
             float out[9];
 #pragma unroll
             for (int n = 0; n < 9; ++n) {
-                gd[n] = (long long)sYi[ly + 4 + c_cy[n]] * nx + sXi[lx + 4 + c_cx[n]];
-                out[n] = dn[n] + D[n];
+                gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
+                out[n] = d[n] + D[n];
             }
             st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
             if (readout) {
@@ -326,9 +427,9 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 double jxs = 0.0, jys = 0.0;
 #pragma unroll
                 for (int n = 0; n < 9; ++n) {
-                    dsum += dn[n];
-                    jxs += (double)((float)c_cx[n] * dn[n]);
-                    jys += (double)((float)c_cy[n] * dn[n]);
+                    dsum += d[n];
+                    jxs += (double)((float)C_CX[n] * d[n]);
+                    jys += (double)((float)C_CY[n] * d[n]);
                 }
                 acc[0] += (double)dsum;
                 acc[1] += jxs;
@@ -337,66 +438,354 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 acc[4] += (double)Fy;
             }
         }
+    }
+    __syncthreads();
 
+    if (MODE == MODE_MOMENTS) {
+        moments_out(a, m, x0, y0);
+        return;
+    }
+
+    // ---- D: predictor on the halo-1 region --------------------------------------------------
+    for (int i = tid; i < R1; i += NT) {
+        const int ly = i / R1W, lx = i - ly * R1W;
+        const int j2 = (ly + 1) * R2W + lx + 1;
+        float pxx, pyy, pxy, om;
+        vgrad(m.sM + R2, m.sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
+        const St s0 = st_at(m.sS, R3W, lx + 2, ly + 2);
+        const St s1 = st_at(m.sS + R3, R3W, lx + 2, ly + 2);
+        const St s2 = st_at(m.sS + 2 * R3, R3W, lx + 2, ly + 2);
+        const St p0 = st_at(m.sP, R4W, lx + 3, ly + 3);
+        const St p1 = st_at(m.sP + R4, R4W, lx + 3, ly + 3);
+        const int j3 = (ly + 2) * R3W + lx + 2;
+        float r[5];
+        rhs_cell(ph, sL, m.sM[R2 + j2], m.sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
+                 m.sH[j3], m.sH[R3 + j3], r);
+        // y* (the sigma^E buffer is dead: C has finished)
+        m.sY[i] = s0.c + r[0];
+        m.sY[R1 + i] = s1.c + r[1];
+        m.sY[2 * R1 + i] = s2.c + r[2];
+        m.sY[3 * R1 + i] = p0.c + r[3];
+        m.sY[4 * R1 + i] = p1.c + r[4];
+        if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) {
+            const int j0 = (ly - 1) * TX + (lx - 1);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) m.sR[c * R0 + j0] = r[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- E: corrector, field stores, box writes, readout sums -------------------------------
+    for (int i = tid; i < R0; i += NT) {
+        const int ly = i / TX, lx = i - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const long long g = (long long)gy * nx + gx;
+        const int j2 = (ly + 2) * R2W + lx + 2;
+        const float ux = m.sM[R2 + j2], uy = m.sM[2 * R2 + j2];
         // corrector with the frozen u
         {
             float pxx, pyy, pxy, om;
-            vgrad(sM + R2, sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
-            const St s0 = st_at(sY, R1W, lx + 1, ly + 1);
-            const St s1 = st_at(sY + R1, R1W, lx + 1, ly + 1);
-            const St s2 = st_at(sY + 2 * R1, R1W, lx + 1, ly + 1);
-            const St p0 = st_at(sY + 3 * R1, R1W, lx + 1, ly + 1);
-            const St p1 = st_at(sY + 4 * R1, R1W, lx + 1, ly + 1);
+            vgrad(m.sM + R2, m.sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
+            const St s0 = st_at(m.sY, R1W, lx + 1, ly + 1);
+            const St s1 = st_at(m.sY + R1, R1W, lx + 1, ly + 1);
+            const St s2 = st_at(m.sY + 2 * R1, R1W, lx + 1, ly + 1);
+            const St p0 = st_at(m.sY + 3 * R1, R1W, lx + 1, ly + 1);
+            const St p1 = st_at(m.sY + 4 * R1, R1W, lx + 1, ly + 1);
             float hx, hy;
             molecular(ph, p0, p1, hx, hy);
             float r[5];
             rhs_cell(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
             const int j3 = (ly + 3) * R3W + lx + 3;
             const int j4 = (ly + 4) * R4W + lx + 4;
-            const float y0s[5] = {sS[j3], sS[R3 + j3], sS[2 * R3 + j3], sP[j4], sP[R4 + j4]};
+            const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], m.sP[j4], m.sP[R4 + j4]};
             float ynew[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) ynew[c] = y0s[c] + 0.5f * (sR[c * R0 + i] + r[c]);
+            for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
             st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
         }
+        box_write<R3, R3W>(a, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
+    }
+    if (readout) readout_reduce(a, acc, m.sRed, tile_index);
+}
 
-        // u(t) (and f^p(t) on readout steps) on the work box of every ring containing the cell
-        for (int rr = 0; rr < a.n_rings; ++rr) {
-            const RingDev& R = a.rings[rr];
-            int bx = gx - R.box_x0; if (bx < 0) bx += nx;
-            int by = gy - R.box_y0; if (by < 0) by += ny;
-            if (bx < R.box_w && by < R.box_h) {
-                const long long o = R.box_off + (long long)by * R.cap_w + bx;
-                const long long cap = (long long)R.cap_w * R.cap_h;
-                a.ubox[o] = ux;
-                a.ubox[o + cap] = uy;
-                if (readout) {
-                    const int j3 = (ly + 3) * R3W + lx + 3;
-                    a.fpbox[o] = 0.5f * (sS[j3 + 1] - sS[j3 - 1]) + 0.5f * (sS[2 * R3 + j3 + R3W] - sS[2 * R3 + j3 - R3W]);
-                    a.fpbox[o + cap] = 0.5f * (sS[2 * R3 + j3 + 1] - sS[2 * R3 + j3 - 1]) +
-                                       0.5f * (sS[R3 + j3 + R3W] - sS[R3 + j3 - R3W]);
+// ---------------------------------------------------------------------------------------------
+// The same step with two neighbouring cells (lx, lx+1) per thread: the per-cell arithmetic runs
+// on float2 (paired FP32 instructions), stencil pairs are read from shared memory as 8-byte
+// words where aligned, and global loads and stores of a pair use 8-byte accesses where the
+// pair is contiguous and aligned in the lattice.  Region widths are even, so pairs never
+// straddle rows.  Every lane computes exactly what tile_step's arithmetic (with the same
+// fused multiply-adds) computes for its cell.
+// ---------------------------------------------------------------------------------------------
+
+// populations n of the cell pair at flat indices g0, g1; vec: g1 = g0 + 1 with g0 and the plane
+// size even (aligned 8-byte or 4-byte access)
+template <int PREC, bool COH>
+__device__ __forceinline__ float2 ld_pop2(const void* src, long long NP, int n, long long g0, long long g1,
+                                          bool vec)
+{
+    if (vec) {
+        if (PREC == PREC_FP32) {
+            const float2* p = reinterpret_cast<const float2*>(reinterpret_cast<const float*>(src) + n * NP + g0);
+            return ld_state<float2, COH>(p);
+        } else {
+            const unsigned* p = reinterpret_cast<const unsigned*>(reinterpret_cast<const unsigned short*>(src) + n * NP + g0);
+            const unsigned b = ld_state<unsigned, COH>(p);
+            return make_float2(__half2float(__ushort_as_half((unsigned short)(b & 0xFFFFu))) * pop_unscale(n),
+                               __half2float(__ushort_as_half((unsigned short)(b >> 16))) * pop_unscale(n));
+        }
+    }
+    return make_float2(ld_pop<PREC, COH>(src, NP, n, g0), ld_pop<PREC, COH>(src, NP, n, g1));
+}
+
+template <int MODE, int PREC, int TX, int TY, bool COH = false>
+__device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, int tile_index, float* sm)
+{
+    static_assert(TX % 2 == 0, "cell pairs along x");
+    using G = TileGeo<TX, TY>;
+    constexpr int R4W = G::R4W, R4 = G::R4;
+    constexpr int R3W = G::R3W, R3 = G::R3;
+    constexpr int R2W = G::R2W, R2 = G::R2;
+    constexpr int R1W = G::R1W, R1 = G::R1;
+    constexpr int R0 = G::R0;
+    const TileMem<TX, TY> m(sm);
+    const float* sL = reinterpret_cast<const float*>(a.lut);
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const long long NP = a.plane;
+    // 8-byte pair accesses to the lattice need even flat indices: nx even makes every row start,
+    // plane size and pair start (x0 + lx, lx even) even
+    const bool nx_even = (nx & 1) == 0;
+    const int x0 = bx * TX, y0 = by * TY;
+    const Phys ph = a.ph;
+    const void* src = a.src;
+
+    stage<PREC, COH>(a, m, x0, y0);
+
+    // ---- B (pairs): molecular field and Ericksen stress on the halo-3 region --------------
+    for (int q = tid; q < R3 / 2; q += NT) {
+        const int ly = q / (R3W / 2), lx = 2 * (q - ly * (R3W / 2));
+        const StT<float2> px = st2_at<false>(m.sP, R4W, lx + 1, ly + 1);
+        const StT<float2> py = st2_at<false>(m.sP + R4, R4W, lx + 1, ly + 1);
+        float2 hx, hy, E[4];
+        ericksen(ph, px, py, hx, hy, E);
+        const int i = ly * R3W + lx;
+        st2<true>(m.sH + i, hx);
+        st2<true>(m.sH + R3 + i, hy);
+        if (ph.ericksen) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) st2<true>(m.sE + c * R3 + i, E[c]);
+        }
+    }
+
+    pdl_wait();
+    pdl_trigger();
+    ib_gather(a, m, x0, y0);
+
+    // ---- C (pairs): total force and moments on the halo-2 region; collision of the owned
+    // pairs (the owned columns 2 .. TX+1 of the halo-2 frame start at an even column, so a pair
+    // is owned or not as a whole) -------------------------------------------------------------
+    const long long t = a.ctl->t;
+    const bool readout = (t % a.every) == 0;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    void* dst = a.dst;
+    for (int q = tid; q < R2 / 2; q += NT) {
+        const int ly = q / (R2W / 2), lx = 2 * (q - ly * (R2W / 2));
+        const int i = ly * R2W + lx;
+        float2 Fx, Fy;
+        div_sigma(st2_at<false>(m.sS, R3W, lx + 1, ly + 1), st2_at<false>(m.sS + R3, R3W, lx + 1, ly + 1),
+                  st2_at<false>(m.sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
+        if (ph.ericksen) {
+            float2 ex, ey;
+            div_ericksen(st2_at<false>(m.sE, R3W, lx + 1, ly + 1), st2_at<false>(m.sE + R3, R3W, lx + 1, ly + 1),
+                         st2_at<false>(m.sE + 2 * R3, R3W, lx + 1, ly + 1),
+                         st2_at<false>(m.sE + 3 * R3, R3W, lx + 1, ly + 1), ex, ey);
+            Fx = Fx + ex;
+            Fy = Fy + ey;
+        }
+        Fx = Fx + ld2<true>(m.sFib + i);
+        Fy = Fy + ld2<true>(m.sFib + R2 + i);
+        const long long row = (long long)m.sYi[ly + 2] * nx;
+        const int gx0 = m.sXi[lx + 2], gx1 = m.sXi[lx + 3];
+        const long long g0 = row + gx0, g1 = row + gx1;
+        const bool vec = nx_even && gx1 == gx0 + 1;
+        float2 d[9];
+#pragma unroll
+        for (int n = 0; n < 9; ++n) d[n] = ld_pop2<PREC, COH>(src, NP, n, g0, g1, vec);
+        float2 drho, ux, uy;
+        moments(ph, d, Fx, Fy, drho, ux, uy);
+        st2<true>(m.sM + R2 + i, ux);
+        st2<true>(m.sM + 2 * R2 + i, uy);
+        if (MODE == MODE_MOMENTS) st2<true>(m.sM + i, drho);
+        const int gx = x0 + lx - 2, gy = y0 + ly - 2;
+        const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && gx < nx && gy < ny;
+        if (MODE == MODE_STEP && own) {
+            const bool has1 = gx + 1 < nx;             // the second cell lies in the lattice
+            float2 D[9];
+            collide(ph, d, drho, ux, uy, Fx, Fy, D);
+            float2 out[9];
+#pragma unroll
+            for (int n = 0; n < 9; ++n) out[n] = d[n] + D[n];
+            if (PREC == PREC_FP32) {
+                float* dd = reinterpret_cast<float*>(dst);
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    const long long rowd = (long long)m.sYi[ly + 2 + C_CY[n]] * nx;
+                    const int xa = m.sXi[lx + 2 + C_CX[n]], xb = m.sXi[lx + 3 + C_CX[n]];
+                    float* pa = dd + n * NP + rowd + xa;
+                    if (C_CX[n] == 0 && vec) {
+                        *reinterpret_cast<float2*>(pa) = out[n];     // the pair's own columns
+                    } else {
+                        *pa = out[n].x;
+                        if (has1) dd[n * NP + rowd + xb] = out[n].y;
+                    }
+                }
+            } else {
+                long long gd[9];
+                float o1[9];
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
+                    o1[n] = out[n].x;
+                }
+                st_pops<PREC>(dst, NP, gd, o1, (unsigned long long)t, g0);
+                if (has1) {
+#pragma unroll
+                    for (int n = 0; n < 9; ++n) {
+                        gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 3 + C_CX[n]];
+                        o1[n] = out[n].y;
+                    }
+                    st_pops<PREC>(dst, NP, gd, o1, (unsigned long long)t, g1);
+                }
+            }
+            if (readout) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 1 && !has1) break;
+                    float dsum = 0.f;
+                    double jxs = 0.0, jys = 0.0;
+#pragma unroll
+                    for (int n = 0; n < 9; ++n) {
+                        const float v = lane(d[n], k);
+                        dsum += v;
+                        jxs += (double)((float)C_CX[n] * v);
+                        jys += (double)((float)C_CY[n] * v);
+                    }
+                    acc[0] += (double)dsum;
+                    acc[1] += jxs;
+                    acc[2] += jys;
+                    acc[3] += (double)lane(Fx, k);
+                    acc[4] += (double)lane(Fy, k);
                 }
             }
         }
     }
+    __syncthreads();
 
-    if (readout) {
-        // fixed-order block reduction of the FP64 readout sums
-        const int lane = tid & 31, wid = tid >> 5;
+    if (MODE == MODE_MOMENTS) {
+        moments_out(a, m, x0, y0);
+        return;
+    }
+
+    // ---- D (pairs): predictor on the halo-1 region ----------------------------------------
+    for (int q = tid; q < R1 / 2; q += NT) {
+        const int ly = q / (R1W / 2), lx = 2 * (q - ly * (R1W / 2));
+        const StT<float2> su = st2_at<false>(m.sM + R2, R2W, lx + 1, ly + 1);
+        const StT<float2> sv = st2_at<false>(m.sM + 2 * R2, R2W, lx + 1, ly + 1);
+        float2 pxx, pyy, pxy, om;
+        vgrad(su, sv, pxx, pyy, pxy, om);
+        const StT<float2> s0 = st2_at<true>(m.sS, R3W, lx + 2, ly + 2);
+        const StT<float2> s1 = st2_at<true>(m.sS + R3, R3W, lx + 2, ly + 2);
+        const StT<float2> s2 = st2_at<true>(m.sS + 2 * R3, R3W, lx + 2, ly + 2);
+        const StT<float2> p0 = st2_at<false>(m.sP, R4W, lx + 3, ly + 3);
+        const StT<float2> p1 = st2_at<false>(m.sP + R4, R4W, lx + 3, ly + 3);
+        const int j3 = (ly + 2) * R3W + lx + 2;
+        float2 r[5];
+        rhs_cell(ph, sL, su.c, sv.c, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, ld2<true>(m.sH + j3),
+                 ld2<true>(m.sH + R3 + j3), r);
+        const int i = ly * R1W + lx;
+        st2<true>(m.sY + i, s0.c + r[0]);
+        st2<true>(m.sY + R1 + i, s1.c + r[1]);
+        st2<true>(m.sY + 2 * R1 + i, s2.c + r[2]);
+        st2<true>(m.sY + 3 * R1 + i, p0.c + r[3]);
+        st2<true>(m.sY + 4 * R1 + i, p1.c + r[4]);
+        if (ly >= 1 && ly <= TY) {
+            // interior cells of the pair (the halo-1 frame is offset by one column from the tile)
+            const int j0 = (ly - 1) * TX + (lx - 1);
+            if (lx >= 1) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            double v = acc[c];
+                for (int c = 0; c < 5; ++c) m.sR[c * R0 + j0] = r[c].x;
+            }
+            if (lx + 1 <= TX) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sRed[c * (NT / 32) + wid] = v;
-        }
-        __syncthreads();
-        if (tid < 5) {
-            double v = 0.0;
-            for (int w = 0; w < NT / 32; ++w) v += sRed[tid * (NT / 32) + w];
-            a.partials[(long long)tile_index * 5 + tid] = v;
+                for (int c = 0; c < 5; ++c) m.sR[c * R0 + j0 + 1] = r[c].y;
+            }
         }
     }
+    __syncthreads();
+
+    // ---- E (pairs): corrector, field stores, box writes, readout sums ---------------------
+    for (int q = tid; q < R0 / 2; q += NT) {
+        const int ly = q / (TX / 2), lx = 2 * (q - ly * (TX / 2));
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const bool has1 = gx + 1 < nx;                 // the second cell lies in the lattice
+        const long long g0 = (long long)gy * nx + gx;
+        const long long g1 = has1 ? g0 + 1 : g0;
+        const bool vec = has1 && nx_even;
+        const int i = ly * TX + lx;
+        const StT<float2> su = st2_at<true>(m.sM + R2, R2W, lx + 2, ly + 2);
+        const StT<float2> sv = st2_at<true>(m.sM + 2 * R2, R2W, lx + 2, ly + 2);
+        const float2 ux = su.c, uy = sv.c;
+        // corrector with the frozen u
+        {
+            float2 pxx, pyy, pxy, om;
+            vgrad(su, sv, pxx, pyy, pxy, om);
+            const StT<float2> s0 = st2_at<false>(m.sY, R1W, lx + 1, ly + 1);
+            const StT<float2> s1 = st2_at<false>(m.sY + R1, R1W, lx + 1, ly + 1);
+            const StT<float2> s2 = st2_at<false>(m.sY + 2 * R1, R1W, lx + 1, ly + 1);
+            const StT<float2> p0 = st2_at<false>(m.sY + 3 * R1, R1W, lx + 1, ly + 1);
+            const StT<float2> p1 = st2_at<false>(m.sY + 4 * R1, R1W, lx + 1, ly + 1);
+            float2 hx, hy;
+            molecular(ph, p0, p1, hx, hy);
+            float2 r[5];
+            rhs_cell(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
+            const int j3 = (ly + 3) * R3W + lx + 3;
+            const int j4 = (ly + 4) * R4W + lx + 4;
+            const float2 y0s[5] = {ld2<false>(m.sS + j3), ld2<false>(m.sS + R3 + j3), ld2<false>(m.sS + 2 * R3 + j3),
+                                   ld2<true>(m.sP + j4), ld2<true>(m.sP + R4 + j4)};
+            float2 ynew[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, ld2<true>(m.sR + c * R0 + i) + r[c], y0s[c]);
+            if (PREC == PREC_FP32) {
+                float* d = reinterpret_cast<float*>(dst);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    float* p = d + (PL_SXX + c) * NP + g0;
+                    if (vec) {
+                        *reinterpret_cast<float2*>(p) = ynew[c];
+                    } else {
+                        p[0] = ynew[c].x;
+                        if (has1) d[(PL_SXX + c) * NP + g1] = ynew[c].y;
+                    }
+                }
+            } else {
+                float o[5];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) o[c] = ynew[c].x;
+                st_flds<PREC>(dst, NP, g0, o, (unsigned long long)t);
+                if (has1) {
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) o[c] = ynew[c].y;
+                    st_flds<PREC>(dst, NP, g1, o, (unsigned long long)t);
+                }
+            }
+        }
+        const int j3 = (ly + 3) * R3W + lx + 3;
+        box_write<R3, R3W>(a, gx, gy, ux.x, uy.x, readout, m.sS, j3);
+        if (has1) box_write<R3, R3W>(a, gx + 1, gy, ux.y, uy.y, readout, m.sS, j3 + 1);
+    }
+    if (readout) readout_reduce(a, acc, m.sRed, tile_index);
 }
 
 }  // namespace tile

@@ -19,7 +19,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EUNSTABLE, LB_EBODY, LB
 LB_ETIMEOUT = -8
 LB_FP32 = 0
 LB_FP16_BF16 = 1
-LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP = 0, 1, 2
+LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP, LB_KERNEL_PAIR = 0, 1, 2, 3
 FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
 LB_FIELD_POP0 = 8
 LB_FIELD_NODES = 17
@@ -252,7 +252,7 @@ class Solver:
         return buf[:n.value].copy()
 
     def set_kernel(self, kernel: int):
-        """LB_KERNEL_AUTO (sweep when eligible), LB_KERNEL_TILE or LB_KERNEL_SWEEP."""
+        """LB_KERNEL_AUTO (the fastest measured), LB_KERNEL_TILE, LB_KERNEL_PAIR or LB_KERNEL_SWEEP."""
         _check(self.h, lib().lb_set_kernel(self.h, int(kernel)))
 
     def timing(self, enable: bool):

@@ -155,7 +155,9 @@ def test_invariants_on_gpu():
     N = 64 * 64
     assert np.abs(ser[:, 1]).max() < 1e-3 * 1e-7 * N * 10         # mass: FP32 rounding only
     pull = 1e-3 * np.array([math.cos(0.3), math.sin(0.3)])
-    assert np.abs(ser[:, 4:6] - pull).max() < 2e-6 * 1e-3 * N ** 0.5
+    # sum F = pull up to the FP32 rounding of the divergence differences, which telescope to 0:
+    # about sqrt(N) ulp(|sigma^E|) with |sigma^E| ~ 0.1 for the orientation noise at t = 0
+    assert np.abs(ser[:, 4:6] - pull).max() < 2 * N ** 0.5 * 2.0 ** -27
     dm = np.diff(ser[:, 2:4], axis=0) / 10.0
     assert np.abs(dm - pull).max() < 1e-3 * 1e-3
 
@@ -302,3 +304,25 @@ def test_precision_form_round_trip_and_determinism():
         s.close()
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("nx,ny,centre", [(51, 37, (49.7, 2.2)), (64, 48, (1.1, 40.3)),
+                                          (98, 34, (60.4, 15.5))])
+def test_pair_and_single_cell_tile_kernels_vs_oracle(nx, ny, centre):
+    """The two-cells-per-thread tile kernel against the one-cell tile kernel and the oracle.
+    The same expressions, but the paired path lets the compiler fuse some products with the
+    following sum into one rounding, so the two agree to FP32 rounding, not bitwise; odd nx
+    takes the unpaired global accesses and a half-filled last pair of every row."""
+    lb = _gpu()
+    w = W.small(nx, ny, n_nodes=20, radius=4.0, centre=centre, steps=40)
+    pa = _run_gpu(w, 40, lb.LB_KERNEL_PAIR)
+    ti = _run_gpu(w, 40, lb.LB_KERNEL_TILE)
+    for k in ti["fields"]:
+        assert rel_l2(pa["fields"][k], ti["fields"][k]) <= 1e-6, k
+    sim = O.Sim.from_workload(w)
+    sim.step(40, every=10)
+    ref = dict(fields=sim.fields(), series=np.array(sim.series), X=sim.X.copy())
+    for got in (pa, ti):
+        check_fields(got, ref)
+        check_nodes(got, ref, w)
+        check_series(got, ref, 1)
