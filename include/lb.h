@@ -246,6 +246,62 @@ int32_t lb_batch_uses_graph(const lb_batch* b);
 const char* lb_batch_last_error(const lb_batch* b);
 void lb_batch_destroy(lb_batch* b);
 
+/*
+ * The network of the learned stepper (no counterpart in the paper's method: a convolutional
+ * surrogate trained on the method's own trajectories).  A 4-level U-Net on NHWC activations:
+ * per level two 3x3 convolutions + LeakyReLU (slope 0.1) with 32, 64, 96, 128 channels at full,
+ * 1/2, 1/4, 1/8 resolution, 2x2 average pooling down, nearest 2x upsampling + concatenation
+ * with the skip up, and a final 3x3 convolution to 16 channels.  Input x: BF16 [B][H][W][16]
+ * (H, W multiples of 8); output: FP32 [B][H][W][16].  BF16 weights and activations on the tensor
+ * cores, FP32 accumulation, FP32 master weights and Adam.
+ *
+ * Parameters are one flat FP32 array, layer by layer in execution order (e0a, e0b, e1a, e1b,
+ * e2a, e2b, bta, btb, d2a, d2b, d1a, d1b, d0a, d0b, head), each as w[9][Co][Ci] (tap
+ * t = (dy + 1) * 3 + (dx + 1)) then b[Co].
+ * lb_net_create: initialises He-normal weights from seed; all work on `stream`.
+ * lb_net_forward: x is a device pointer; the output stays on the device (lb_net_output, owned by
+ *   the network) and is copied to y (device FP32, or NULL); the activations are kept for
+ *   lb_net_backward.
+ * lb_net_backward: gradients of sum(g * output) for every parameter (overwritten, FP32;
+ *   lb_net_get_grads), g a device FP32 [B][H][W][16].
+ * lb_net_mse: loss = mean over pixels and the channels with mask16[c] != 0 of
+ *   (mask (output - target))^2 (target device FP32 [B][H][W][16], mask16 host), its gradient kept
+ *   for lb_net_train_step; *loss on the host (synchronises).
+ * lb_net_adam: one Adam step with the last gradients.  lb_net_train_step: forward, mse,
+ *   backward, Adam (lr, 0.9, 0.999, 1e-8).
+ * lb_conv3x3 / lb_conv3x3_dgrad / lb_conv3x3_wgrad: the single-layer kernels (device pointers,
+ *   BF16 activations and weights w[9][Co][Ci]), exposed to test them alone: forward with optional
+ *   bias and LeakyReLU into BF16 y or FP32 yf; the data gradient gx[B][H][W][Ci] from
+ *   gz[B][H][W][Co]; the weight and bias gradients gw[9][Co][Ci], gb[Co] (FP32) from x and gz.
+ */
+typedef struct lb_net lb_net;
+int lb_net_create(int32_t batch, int32_t height, int32_t width, uint64_t seed, void* stream, lb_net** out);
+int64_t lb_net_num_params(const lb_net* n);
+int lb_net_set_params(lb_net* n, const float* host, int64_t count);
+int lb_net_get_params(lb_net* n, float* host, int64_t count);
+int lb_net_get_grads(lb_net* n, float* host, int64_t count);
+int lb_net_forward(lb_net* n, const void* x, float* y);
+const float* lb_net_output(const lb_net* n);
+int lb_net_backward(lb_net* n, const float* grad_out);
+int lb_net_mse(lb_net* n, const float* target, const float* mask16, double* loss);
+const float* lb_net_loss_grad(const lb_net* n);
+int lb_net_adam(lb_net* n, float lr, float beta1, float beta2, float eps);
+int lb_net_train_step(lb_net* n, const void* x, const float* target, const float* mask16, float lr, double* loss);
+/* Copy one stored BF16 activation of the last forward to the host (a test hook): which = 0 x,
+ * 1 e0a, 2 cat0 [up(d1) | e0b], 3 pool(e0), 4 e1a, 5 cat1 [up(d2) | e1b], 6 pool(e1), 7 e2a,
+ * 8 cat2 [up(bt) | e2b], 9 pool(e2), 10 bta, 11 btb, 12 d2a, 13 d2b, 14 d1a, 15 d1b, 16 d0a,
+ * 17 d0b; bytes must equal the activation's size. */
+int lb_net_activation(lb_net* n, int32_t which, void* host, int64_t bytes);
+const char* lb_net_last_error(const lb_net* n);
+void lb_net_destroy(lb_net* n);
+int lb_conv3x3(const void* x, int64_t ldx, int32_t xoff, const void* w, const float* bias, void* y, float* yf,
+               int64_t ldy, int32_t yoff, int32_t B, int32_t H, int32_t W, int32_t Ci, int32_t Co, int32_t act,
+               void* stream);
+int lb_conv3x3_dgrad(const void* gz, const void* w, void* gx, int32_t B, int32_t H, int32_t W, int32_t Ci, int32_t Co,
+                     void* stream);
+int lb_conv3x3_wgrad(const void* x, const void* gz, float* gw, float* gb, int32_t B, int32_t H, int32_t W, int32_t Ci,
+                     int32_t Co, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

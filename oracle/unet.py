@@ -41,6 +41,15 @@ C_IN, C_OUT = 16, 16
 
 # ---------------------------------------------------------------- elementary operations
 
+def round_bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as FP64: the FP32 value's upper
+    16 bits after adding 0x7FFF + (bit 16) to its bit pattern (finite inputs)."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def conv3x3(x, w, b):
     B, H, W, Ci = x.shape
     Co = w.shape[1]
@@ -119,20 +128,23 @@ def init_params(seed=0):
     return P
 
 
-def forward(P, x):
-    """The network on x[B, H, W, 16] (H, W multiples of 8); returns (y, cache)."""
+def forward(P, x, q=None):
+    """The network on x[B, H, W, 16] (H, W multiples of 8); returns (y, cache).  q: optional
+    rounding applied where a reduced-precision implementation stores a value (every
+    activated convolution output and every pooled value); the head output is not rounded."""
     cache = {}
+    q = q or (lambda v: v)
 
     def conv(name, inp, act):
         z = conv3x3(inp, P[name + ".w"], P[name + ".b"])
-        out = leaky(z) if act else z
+        out = q(leaky(z)) if act else z
         cache[name] = (inp, out)
         return out
 
     e0 = conv("e0b", conv("e0a", x, True), True)
-    e1 = conv("e1b", conv("e1a", pool2(e0), True), True)
-    e2 = conv("e2b", conv("e2a", pool2(e1), True), True)
-    bt = conv("btb", conv("bta", pool2(e2), True), True)
+    e1 = conv("e1b", conv("e1a", q(pool2(e0)), True), True)
+    e2 = conv("e2b", conv("e2a", q(pool2(e1)), True), True)
+    bt = conv("btb", conv("bta", q(pool2(e2)), True), True)
     d2 = conv("d2b", conv("d2a", np.concatenate([up2(bt), e2], axis=3), True), True)
     d1 = conv("d1b", conv("d1a", np.concatenate([up2(d2), e1], axis=3), True), True)
     d0 = conv("d0b", conv("d0a", np.concatenate([up2(d1), e0], axis=3), True), True)
@@ -140,27 +152,31 @@ def forward(P, x):
     return y, cache
 
 
-def backward(P, cache, gy):
-    """Gradients of sum(gy * forward(P, x)) with respect to every parameter and x."""
+def backward(P, cache, gy, q=None):
+    """Gradients of sum(gy * forward(P, x)) with respect to every parameter and x.  q: optional
+    rounding where a reduced-precision implementation stores a back-propagated gradient (the
+    output gradient, every pre-activation gradient, every input gradient of a convolution, of
+    an upsampling and of a pooling join); parameter gradients are not rounded."""
     G = {}
+    q = q or (lambda v: v)
 
     def conv_b(name, g_out, act):
         inp, out = cache[name]
-        gz = leaky_bwd(out, g_out) if act else g_out
+        gz = q(leaky_bwd(out, g_out)) if act else g_out
         gx, gw, gb = conv3x3_bwd(inp, P[name + ".w"], gz)
         G[name + ".w"] = gw
         G[name + ".b"] = gb
-        return gx
+        return q(gx)
 
-    g = conv_b("head", gy, False)
+    g = conv_b("head", q(gy), False)
     g = conv_b("d0a", conv_b("d0b", g, True), True)
     g_up, g_e0 = g[..., :64], g[..., 64:]
-    g = conv_b("d1a", conv_b("d1b", up2_bwd(g_up), True), True)
+    g = conv_b("d1a", conv_b("d1b", q(up2_bwd(g_up)), True), True)
     g_up, g_e1 = g[..., :96], g[..., 96:]
-    g = conv_b("d2a", conv_b("d2b", up2_bwd(g_up), True), True)
+    g = conv_b("d2a", conv_b("d2b", q(up2_bwd(g_up)), True), True)
     g_up, g_e2 = g[..., :128], g[..., 128:]
-    g = conv_b("bta", conv_b("btb", up2_bwd(g_up), True), True)
-    g = conv_b("e2a", conv_b("e2b", pool2_bwd(g) + g_e2, True), True)
-    g = conv_b("e1a", conv_b("e1b", pool2_bwd(g) + g_e1, True), True)
-    gx = conv_b("e0a", conv_b("e0b", pool2_bwd(g) + g_e0, True), True)
+    g = conv_b("bta", conv_b("btb", q(up2_bwd(g_up)), True), True)
+    g = conv_b("e2a", conv_b("e2b", q(pool2_bwd(g) + g_e2), True), True)
+    g = conv_b("e1a", conv_b("e1b", q(pool2_bwd(g) + g_e1), True), True)
+    gx = conv_b("e0a", conv_b("e0b", q(pool2_bwd(g) + g_e0), True), True)
     return G, gx

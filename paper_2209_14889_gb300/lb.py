@@ -56,6 +56,7 @@ class lb_ring(ctypes.Structure):
 _lib = None
 _H = ctypes.c_void_p
 _B = ctypes.c_void_p
+_N = ctypes.c_void_p
 
 
 def library_path() -> str:
@@ -104,6 +105,26 @@ def lib():
             "lb_batch_uses_graph": (i32, [_B]),
             "lb_batch_last_error": (ctypes.c_char_p, [_B]),
             "lb_batch_destroy": (None, [_B]),
+            "lb_net_create": (ctypes.c_int, [i32, i32, i32, ctypes.c_uint64, vp, ctypes.POINTER(_N)]),
+            "lb_net_num_params": (i64, [_N]),
+            "lb_net_set_params": (ctypes.c_int, [_N, vp, i64]),
+            "lb_net_get_params": (ctypes.c_int, [_N, vp, i64]),
+            "lb_net_get_grads": (ctypes.c_int, [_N, vp, i64]),
+            "lb_net_forward": (ctypes.c_int, [_N, vp, vp]),
+            "lb_net_output": (vp, [_N]),
+            "lb_net_backward": (ctypes.c_int, [_N, vp]),
+            "lb_net_mse": (ctypes.c_int, [_N, vp, vp, ctypes.POINTER(ctypes.c_double)]),
+            "lb_net_loss_grad": (vp, [_N]),
+            "lb_net_adam": (ctypes.c_int, [_N, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+            "lb_net_train_step": (ctypes.c_int, [_N, vp, vp, vp, ctypes.c_float,
+                                                 ctypes.POINTER(ctypes.c_double)]),
+            "lb_net_activation": (ctypes.c_int, [_N, i32, vp, i64]),
+            "lb_net_last_error": (ctypes.c_char_p, [_N]),
+            "lb_net_destroy": (None, [_N]),
+            "lb_conv3x3": (ctypes.c_int, [vp, i64, i32, vp, vp, vp, vp, i64, i32, i32, i32, i32, i32, i32,
+                                          i32, vp]),
+            "lb_conv3x3_dgrad": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, i32, vp]),
+            "lb_conv3x3_wgrad": (ctypes.c_int, [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -334,3 +355,137 @@ class Batch:
     @property
     def uses_graph(self) -> bool:
         return bool(lib().lb_batch_uses_graph(self.b))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Net:
+    """The learned stepper's U-Net (lb_net_*): BF16 NHWC input [B, H, W, 16] on the GPU."""
+
+    N_IN = N_OUT = 16
+
+    def __init__(self, batch: int, height: int, width: int, seed: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self.B, self.H, self.W = batch, height, width
+        self.n = _N()
+        rc = lib().lb_net_create(batch, height, width, seed, ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(self.n))
+        if rc != LB_OK:
+            raise LBError(rc, "lb_net_create failed")
+        self.n_params = lib().lb_net_num_params(self.n)
+
+    def _check(self, rc):
+        if rc != LB_OK:
+            raise LBError(rc, lib().lb_net_last_error(self.n).decode())
+
+    def close(self):
+        if self.n:
+            lib().lb_net_destroy(self.n)
+            self.n = _N()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._check(lib().lb_net_get_params(self.n, out.ctypes.data, self.n_params))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        self._check(lib().lb_net_set_params(self.n, p.ctypes.data, self.n_params))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        self._check(lib().lb_net_get_grads(self.n, out.ctypes.data, self.n_params))
+        return out
+
+    def forward(self, x, out=None):
+        """x: torch bfloat16 [B, H, W, 16] on the GPU; returns the FP32 output [B, H, W, 16]."""
+        torch = self._torch
+        assert x.dtype == torch.bfloat16 and x.is_contiguous() and tuple(x.shape) == (self.B, self.H, self.W, 16)
+        if out is None:
+            out = torch.empty((self.B, self.H, self.W, 16), dtype=torch.float32, device="cuda")
+        self._check(lib().lb_net_forward(self.n, _ptr(x), _ptr(out)))
+        return out
+
+    def backward(self, g):
+        torch = self._torch
+        assert g.dtype == torch.float32 and g.is_contiguous()
+        self._check(lib().lb_net_backward(self.n, _ptr(g)))
+
+    ACTIVATIONS = [("x", 0, 16), ("e0a", 0, 32), ("cat0", 0, 96), ("p1", 1, 32), ("e1a", 1, 64),
+                   ("cat1", 1, 160), ("p2", 2, 64), ("e2a", 2, 96), ("cat2", 2, 224), ("p3", 3, 96),
+                   ("bta", 3, 128), ("btb", 3, 128), ("d2a", 2, 96), ("d2b", 2, 96), ("d1a", 1, 64),
+                   ("d1b", 1, 64), ("d0a", 0, 32), ("d0b", 0, 32)]
+
+    def activation(self, name: str) -> np.ndarray:
+        """A stored BF16 activation of the last forward, as FP32 numpy [B, H/2^l, W/2^l, C]."""
+        k = [a[0] for a in self.ACTIVATIONS].index(name)
+        _, lev, c = self.ACTIVATIONS[k]
+        shape = (self.B, self.H >> lev, self.W >> lev, c)
+        raw = np.empty(shape, dtype=np.uint16)
+        self._check(lib().lb_net_activation(self.n, k, raw.ctypes.data, raw.nbytes))
+        return (raw.astype(np.uint32) << 16).view(np.float32)
+
+    def mse(self, target, mask16) -> float:
+        m = np.ascontiguousarray(mask16, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(lib().lb_net_mse(self.n, _ptr(target), m.ctypes.data, ctypes.byref(loss)))
+        return loss.value
+
+    def adam(self, lr: float, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(lib().lb_net_adam(self.n, lr, beta1, beta2, eps))
+
+    def train_step(self, x, target, mask16, lr: float) -> float:
+        m = np.ascontiguousarray(mask16, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(lib().lb_net_train_step(self.n, _ptr(x), _ptr(target), m.ctypes.data, lr,
+                                             ctypes.byref(loss)))
+        return loss.value
+
+
+def conv3x3(x, w, bias=None, act=False, out_f32=True, ldy=None, yoff=0, y=None):
+    """The single-layer forward kernel: x bf16 [B, H, W, Ci], w bf16 [9, Co, Ci]."""
+    import torch
+    B, H, W, Ci = x.shape
+    Co = w.shape[1]
+    if y is None:
+        y = torch.empty((B, H, W, Co), dtype=torch.float32 if out_f32 else torch.bfloat16, device="cuda")
+    ldy = Co if ldy is None else ldy
+    rc = lib().lb_conv3x3(_ptr(x), Ci, 0, _ptr(w), _ptr(bias), None if out_f32 else _ptr(y),
+                          _ptr(y) if out_f32 else None, ldy, yoff, B, H, W, Ci, Co, 1 if act else 0,
+                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(None, rc)
+    return y
+
+
+def conv3x3_dgrad(gz, w):
+    import torch
+    B, H, W, Co = gz.shape
+    Ci = w.shape[2]
+    gx = torch.empty((B, H, W, Ci), dtype=torch.bfloat16, device="cuda")
+    rc = lib().lb_conv3x3_dgrad(_ptr(gz), _ptr(w), _ptr(gx), B, H, W, Ci, Co,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(None, rc)
+    return gx
+
+
+def conv3x3_wgrad(x, gz):
+    import torch
+    B, H, W, Ci = x.shape
+    Co = gz.shape[3]
+    gw = torch.empty((9, Co, Ci), dtype=torch.float32, device="cuda")
+    gb = torch.empty((Co,), dtype=torch.float32, device="cuda")
+    rc = lib().lb_conv3x3_wgrad(_ptr(x), _ptr(gz), _ptr(gw), _ptr(gb), B, H, W, Ci, Co,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(None, rc)
+    return gw, gb

@@ -103,3 +103,26 @@ def test_network_gradient_finite_differences():
     for idx in [(0, 0, 0, 0), (0, 7, 3, 9), (0, 4, 4, 15)]:
         fd = _fd(loss, x, idx)
         assert abs(fd - gx[idx]) <= 1e-5 * max(1.0, abs(fd)), (idx, fd, gx[idx])
+
+
+def test_bf16_rounding_matches_library_and_ties_to_even():
+    torch = pytest.importorskip("torch")
+    r = rng(7)
+    a = np.concatenate([r.normal(size=1000) * 10.0 ** r.integers(-20, 20, size=1000),
+                        [0.0, -0.0, 1.0, -3.5, 65504.0, 1e-38]]).astype(np.float32)
+    ref = torch.tensor(a).to(torch.bfloat16).float().numpy().astype(np.float64)
+    assert np.array_equal(U.round_bf16(a), ref)
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and rounds to the even 1;
+    # 1 + 3 * 2^-8 rounds up to the even 1 + 2^-6
+    assert U.round_bf16(np.float32(1 + 2 ** -8)) == 1.0
+    assert U.round_bf16(np.float32(1 + 3 * 2 ** -8)) == 1 + 2 ** -6
+
+
+def test_rounded_network_reduces_to_exact_one_without_rounding():
+    P = U.init_params(seed=2)
+    x = rng(3).normal(size=(1, 8, 8, U.C_IN))
+    y0, c0 = U.forward(P, x)
+    y1, c1 = U.forward(P, x, q=lambda v: v)
+    assert np.array_equal(y0, y1)
+    yq, _ = U.forward(P, x, q=U.round_bf16)
+    assert 0 < np.linalg.norm(yq - y0) / np.linalg.norm(y0) < 2e-2
