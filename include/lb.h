@@ -287,6 +287,7 @@ int lb_net_mse(lb_net* n, const float* target, const float* mask16, double* loss
 const float* lb_net_loss_grad(const lb_net* n);
 int lb_net_adam(lb_net* n, float lr, float beta1, float beta2, float eps);
 int lb_net_train_step(lb_net* n, const void* x, const float* target, const float* mask16, float lr, double* loss);
+int lb_net_shape(const lb_net* n, int32_t* batch, int32_t* height, int32_t* width);
 /* Copy one stored BF16 activation of the last forward to the host (a test hook): which = 0 x,
  * 1 e0a, 2 cat0 [up(d1) | e0b], 3 pool(e0), 4 e1a, 5 cat1 [up(d2) | e1b], 6 pool(e1), 7 e2a,
  * 8 cat2 [up(bt) | e2b], 9 pool(e2), 10 bta, 11 btb, 12 d2a, 13 d2b, 14 d1a, 15 d1b, 16 d0a,
@@ -301,6 +302,43 @@ int lb_conv3x3_dgrad(const void* gz, const void* w, void* gx, int32_t B, int32_t
                      void* stream);
 int lb_conv3x3_wgrad(const void* x, const void* gz, float* gw, float* gb, int32_t B, int32_t H, int32_t W, int32_t Ci,
                      int32_t Co, void* stream);
+
+/*
+ * The learned stepper (no counterpart in the paper: a surrogate of 16 steps of its method, used
+ * only where a residual check against the method passes).  Network channels: 0 ux, 1 uy,
+ * 2 sigma_xx, 3 sigma_xy, 4 sigma_yy, 5 dP_x, 6 dP_y (dP = P - P_ref), 7 body indicator (sum of
+ * the IB kernel weights phi phi of the ring nodes), 8..15 zero.  norm (host, 23 floats):
+ * shift[8], scale[8] of the inputs x_c = (f_c - shift_c) scale_c, then oscale[7]: the network
+ * outputs the change of channel c over 16 steps times oscale_c.
+ *
+ * lb_learned_pack: the handle's current fields as the network input x (device BF16 [ny][nx][16],
+ *   or NULL) and the raw fields raw (device FP32 [ny][nx][8], or NULL); FP32 state only.
+ * lb_learned_target: the training target (device FP32 [cells][16]) of a pair of raw fields 16
+ *   steps apart.  lb_learned_normalize: the network input (BF16 [cells][16]) of raw fields.
+ * lb_learned_create: a stepper for handle h (FP32 state, readout_every a multiple of 16) with a
+ *   network of batch 1 and the lattice's size.  eps_momentum bounds the momentum-balance
+ *   residual |sum u_net - sum u(t) - 16 F_pull| / (16 |F_pull|); eps_tendency bounds the
+ *   relative mismatch between the network's per-step change and one plain step, in the scaled
+ *   channel norm.
+ * lb_learned_step: `calls` calls of 16 steps each.  Per call: one plain step, then either the
+ *   network's state at t + 16 (both residuals within bounds; populations rebuilt as the
+ *   equilibrium plus the regularised BGK non-equilibrium part, ring nodes advanced 15 steps
+ *   with the mean velocity) or 15 more plain steps (*n_fallbacks counts these).  The restoring
+ *   force series (lb_series) holds the rows of the plain steps at multiples of 16.
+ * lb_learned_stats: out4 = (momentum residual, tendency residual of the last call, calls,
+ *   accepted calls).
+ */
+typedef struct lb_learned lb_learned;
+int lb_learned_pack(lb_handle* h, const float* norm, void* x, float* raw);
+int lb_learned_target(const float* raw0, const float* raw1, const float* norm, float* target, int64_t cells,
+                      void* stream);
+int lb_learned_normalize(const float* raw, const float* norm, void* x, int64_t cells, void* stream);
+int lb_learned_create(lb_handle* h, lb_net* net, const float* norm, double eps_momentum, double eps_tendency,
+                      lb_learned** out);
+int lb_learned_step(lb_learned* L, int64_t calls, int64_t* n_fallbacks);
+int lb_learned_stats(const lb_learned* L, double* out4);
+const char* lb_learned_last_error(const lb_learned* L);
+void lb_learned_destroy(lb_learned* L);
 
 #ifdef __cplusplus
 }

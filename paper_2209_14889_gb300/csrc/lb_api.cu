@@ -103,6 +103,7 @@ FusedArgs fused_args(lb_handle* h)
     a.ctl = h->ctl;
     a.every = h->p.readout_every;
     a.moments_out = h->moments;
+    a.forces_out = nullptr;
     return a;
 }
 

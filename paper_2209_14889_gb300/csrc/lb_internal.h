@@ -76,6 +76,7 @@ struct FusedArgs {
     Ctl* ctl;
     int every;                   // readout period
     float* moments_out;          // MOMENTS mode: drho, ux, uy planes
+    float* forces_out;           // MOMENTS mode, optional: Fx, Fy planes (total lattice force)
 };
 
 // Node kernel geometry: NB owned nodes per CTA, NODE_THREADS >= NB + 4 threads.
@@ -104,7 +105,9 @@ struct NodeArgs {
     Ctl* ctl;
     int every;
     int nx, ny;
-    int advance;                 // 0: forces + box only (initial configuration)
+    int advance;                 // 0: forces + box only (initial configuration); else the steps
+                                 // the positions advance by (1; 15 for a learned jump, the
+                                 // velocities on the boxes then carry that factor)
 };
 
 // Launchers (return cudaError_t of the launch).

@@ -322,7 +322,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
         }
         if (tid == 0) {
             a.ctl->ticket = 0u;
-            if (a.advance) a.ctl->t = t + 1;
+            if (a.advance) a.ctl->t = t + a.advance;      // advance: steps taken (1, or a jump)
             __threadfence();
         }
     }

@@ -328,6 +328,10 @@ __device__ __forceinline__ void moments_out(const FusedArgs& a, const TileMem<TX
         a.moments_out[g] = m.sM[j];
         a.moments_out[NP + g] = m.sM[G::R2 + j];
         a.moments_out[2 * NP + g] = m.sM[2 * G::R2 + j];
+        if (a.forces_out) {
+            a.forces_out[g] = m.sFib[j];
+            a.forces_out[NP + g] = m.sFib[G::R2 + j];
+        }
     }
 }
 
@@ -409,7 +413,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         moments(ph, d, Fx, Fy, drho, ux, uy);
         m.sM[R2 + i] = ux;
         m.sM[2 * R2 + i] = uy;
-        if (MODE == MODE_MOMENTS) m.sM[i] = drho;
+        if (MODE == MODE_MOMENTS) {
+            m.sM[i] = drho;
+            m.sFib[i] = Fx;              // the total force replaces f_IB (read above, this cell only)
+            m.sFib[R2 + i] = Fy;
+        }
         const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && x0 + lx - 2 < nx && y0 + ly - 2 < ny;
         if (MODE == MODE_STEP && own) {
             float D[9];
@@ -616,7 +624,11 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
         moments(ph, d, Fx, Fy, drho, ux, uy);
         st2<true>(m.sM + R2 + i, ux);
         st2<true>(m.sM + 2 * R2 + i, uy);
-        if (MODE == MODE_MOMENTS) st2<true>(m.sM + i, drho);
+        if (MODE == MODE_MOMENTS) {
+            st2<true>(m.sM + i, drho);
+            st2<true>(m.sFib + i, Fx);
+            st2<true>(m.sFib + R2 + i, Fy);
+        }
         const int gx = x0 + lx - 2, gy = y0 + ly - 2;
         const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && gx < nx && gy < ny;
         if (MODE == MODE_STEP && own) {

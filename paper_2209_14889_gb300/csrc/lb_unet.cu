@@ -730,6 +730,15 @@ int lb_net_create(int32_t batch, int32_t height, int32_t width, uint64_t seed, v
 
 int64_t lb_net_num_params(const lb_net* n) { return n ? n->n_params : -1; }
 
+int lb_net_shape(const lb_net* n, int32_t* batch, int32_t* height, int32_t* width)
+{
+    if (!n || !batch || !height || !width) return LB_EINVAL;
+    *batch = n->B;
+    *height = n->H;
+    *width = n->W;
+    return LB_OK;
+}
+
 int lb_net_set_params(lb_net* n, const float* host, int64_t count)
 {
     if (!n || !host) return LB_EINVAL;

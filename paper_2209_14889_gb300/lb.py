@@ -57,6 +57,7 @@ _lib = None
 _H = ctypes.c_void_p
 _B = ctypes.c_void_p
 _N = ctypes.c_void_p
+_L = ctypes.c_void_p
 
 
 def library_path() -> str:
@@ -121,6 +122,17 @@ def lib():
             "lb_net_activation": (ctypes.c_int, [_N, i32, vp, i64]),
             "lb_net_last_error": (ctypes.c_char_p, [_N]),
             "lb_net_destroy": (None, [_N]),
+            "lb_net_shape": (ctypes.c_int, [_N, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                            ctypes.POINTER(i32)]),
+            "lb_learned_pack": (ctypes.c_int, [_H, vp, vp, vp]),
+            "lb_learned_target": (ctypes.c_int, [vp, vp, vp, vp, i64, vp]),
+            "lb_learned_normalize": (ctypes.c_int, [vp, vp, vp, i64, vp]),
+            "lb_learned_create": (ctypes.c_int, [_H, _N, vp, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.POINTER(_L)]),
+            "lb_learned_step": (ctypes.c_int, [_L, i64, ctypes.POINTER(i64)]),
+            "lb_learned_stats": (ctypes.c_int, [_L, vp]),
+            "lb_learned_last_error": (ctypes.c_char_p, [_L]),
+            "lb_learned_destroy": (None, [_L]),
             "lb_conv3x3": (ctypes.c_int, [vp, i64, i32, vp, vp, vp, vp, i64, i32, i32, i32, i32, i32, i32,
                                           i32, vp]),
             "lb_conv3x3_dgrad": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, i32, vp]),
