@@ -305,6 +305,46 @@ def measure_batched(args, lb, W, torch):
     return out
 
 
+def measure_learned(args, lb, torch):
+    """The learned form at 256^2: training pairs from seeded trajectories of the batched recipe's
+    physics (one lattice side), GPU training of the U-Net for a time budget, residual bounds
+    fixed on a validation trajectory, then 64 calls (1024 steps) on a held-out trajectory
+    against the plain FP32 solver on the same GPU."""
+    import numpy as np
+    from paper_2209_14889_gb300 import learned as LR
+    side, calls = 256, 64
+    t0 = time.perf_counter()
+    data = LR.Dataset(LR.learned_workloads(500, 6, side=side), pairs_per_traj=16)
+    t_data = time.perf_counter() - t0
+    net = lb.Net(4, side, side, seed=1)
+    held = list(range(0, data.n, 8))
+    val0 = LR.evaluate(net, data, held)
+    t0 = time.perf_counter()
+    net, losses = LR.train(data, batch=4, seconds=args.learned_seconds, lr=5e-4, seed=1, net=net)
+    t_train = time.perf_counter() - t0
+    val1 = LR.evaluate(net, data, held)
+    inf = LR.inference_net(net, side, side)
+    eps, acc_val, err_val = LR.calibrate(inf, data.norm, LR.learned_workloads(501, 1, side=side)[0], calls=16,
+                                         grid=(0.05, 0.2, 1.0, 5.0, 20.0, 100.0))
+    w = LR.learned_workloads(502, 1, side=side)[0]
+    fr_p, ms_p, _ = LR.run(w, calls=calls)
+    fr_l, ms_l, stt = LR.run(w, inf, data.norm, calls=calls, eps=eps)
+    err = float(np.linalg.norm(fr_l - fr_p) / np.linalg.norm(fr_p))
+    cells = side * side
+    out = {"workload": "256x256 periodic, one ring (batched-recipe physics, seed 502), 64 calls of 16 steps",
+           "value": cells * calls * 16 / (ms_l * 1e-3) / 1e6, "unit": "MLUPS",
+           "plain_fp32_mlups": cells * calls * 16 / (ms_p * 1e-3) / 1e6,
+           "accepted_calls": stt["accepted"], "calls": calls,
+           "frest_err_vs_fp32": {"value": err, "workload": "64 readouts (every 16 steps), relative L2"},
+           "residual_bounds": {"momentum": eps[0], "tendency": eps[1],
+                               "validation_accepted": acc_val, "validation_frest_err": err_val},
+           "training": {"pairs": data.n, "data_s": t_data, "adam_steps": len(losses), "train_s": t_train,
+                        "batch": 4, "loss_subset_before": val0, "loss_subset_after": val1}}
+    inf.close()
+    net.close()
+    return out
+
+
 def cpu_baseline_sample():
     """The oracle as it stands on one host core, on a bounded sample of the workload: one LB
     time step of the 1024 x 1024 lattice."""
@@ -337,6 +377,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "pair", "sweep"],
                     help="lattice kernel (auto: the fastest measured, the one-cell tile kernel)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--learned-seconds", type=float, default=45.0,
+                    help="training budget of the learned form (0: skip it)")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON cache of the batched tile-shape autotuner (default: none)")
     ap.add_argument("--no-extras", action="store_true",
@@ -461,6 +503,8 @@ def main():
     forms = None if world > 1 else measure_forms(args, lb, W, torch)
     if forms is not None and not args.no_batched:
         forms["batched"] = measure_batched(args, lb, W, torch)
+    if forms is not None and args.learned_seconds > 0:
+        forms["learned"] = measure_learned(args, lb, torch)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()

@@ -317,9 +317,10 @@ int lb_conv3x3_wgrad(const void* x, const void* gz, float* gw, float* gb, int32_
  *   steps apart.  lb_learned_normalize: the network input (BF16 [cells][16]) of raw fields.
  * lb_learned_create: a stepper for handle h (FP32 state, readout_every a multiple of 16) with a
  *   network of batch 1 and the lattice's size.  eps_momentum bounds the momentum-balance
- *   residual |sum u_net - sum u(t) - 16 F_pull| / (16 |F_pull|); eps_tendency bounds the
- *   relative mismatch between the network's per-step change and one plain step, in the scaled
- *   channel norm.
+ *   residual |sum u_net - sum u(t) - 16 F_pull| / (16 |F_pull|) (an accepted velocity is then
+ *   shifted uniformly so that the balance holds exactly); eps_tendency bounds the relative
+ *   mismatch between the network's per-step change of sigma and P and one plain step, in the
+ *   scaled channel norm.
  * lb_learned_step: `calls` calls of 16 steps each.  Per call: one plain step, then either the
  *   network's state at t + 16 (both residuals within bounds; populations rebuilt as the
  *   equilibrium plus the regularised BGK non-equilibrium part, ring nodes advanced 15 steps

@@ -13,8 +13,9 @@
 //   3. one plain step (t -> t+1) and its tendency T_1 = f(t+1) - f(t);
 //   4. residual check: (i) momentum balance |sum u_net - sum u(t) - 16 F_pull| / (16 |F_pull|)
 //      (the lattice force sums to the pull: elastic forces cancel, the stress divergences
-//      telescope); (ii) tendency mismatch |(f_net - f(t))/16 - T_1| / |T_1| in the scaled
-//      channel norm.  Both at most their epsilon: accept; else run the remaining 15 plain steps.
+//      telescope); (ii) tendency mismatch |(f_net - f(t))/16 - T_1| / |T_1| of sigma and P in the
+//      scaled channel norm.  Both at most their epsilon: accept (the network's velocity then gets
+//      the uniform correction that makes (i) exact); else run the remaining 15 plain steps.
 //   5. accept: sigma and dP from the net; ring nodes advanced by 15 steps with the mean of
 //      u(t+1) and u_net (one Heun step of the node kernel with 15x velocities on the work boxes);
 //      populations rebuilt as the equilibrium at rho(t+1) and the velocity u_net - F/(2 rho) (the
@@ -92,7 +93,9 @@ __global__ void k_pack(const float* st, const float* mom, long long NP, int nx, 
 }
 
 // residual sums (FP64, per block): 0,1 sum u_net; 2,3 sum u(t); 4 sum_c s_c^2 (T_net - T_1)^2;
-// 5 sum_c s_c^2 T_1^2 with T_net = y_c / oscale_c / 16, T_1 = f(t+1) - f(t), s_c = scale_c
+// 5 sum_c s_c^2 T_1^2 over the slow fields c = 2..6 (sigma, dP) with T_net = y_c / oscale_c / 16,
+// T_1 = f(t+1) - f(t), s_c = scale_c.  The velocity is left out of (ii): its change in one step
+// is dominated by sound waves that a 16-step average does not follow.
 __global__ void k_residual(const float* raw0, const float* y, const float* st1, const float* mom1, long long NP,
                            LearnNorm nm, double* part)
 {
@@ -114,10 +117,12 @@ __global__ void k_residual(const float* raw0, const float* y, const float* st1, 
                 acc[c] += (double)(f0 + d);
                 acc[2 + c] += (double)f0;
             }
-            const double tn = (double)d / 16.0, t1 = (double)f1[c] - (double)f0;
-            const double s2 = (double)nm.scale[c] * nm.scale[c];
-            acc[4] += s2 * (tn - t1) * (tn - t1);
-            acc[5] += s2 * t1 * t1;
+            if (c >= 2) {            // the slow fields: sigma and P
+                const double tn = (double)d / 16.0, t1 = (double)f1[c] - (double)f0;
+                const double s2 = (double)nm.scale[c] * nm.scale[c];
+                acc[4] += s2 * (tn - t1) * (tn - t1);
+                acc[5] += s2 * t1 * t1;
+            }
         }
     }
     for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
@@ -134,12 +139,15 @@ __global__ void k_residual(const float* raw0, const float* y, const float* st1, 
 // accepted call: sigma, dP from the net into the state; u_net into unet [2][NP]; 15-step node
 // velocities 7.5 (u(t+1) + u_net) on every ring's work box
 __global__ void k_unpack(const float* raw0, const float* y, float* st, const float* mom, float* unet, long long NP,
-                         int nx, int ny, LearnNorm nm, const RingDev* rings, int n_rings, float* ubox)
+                         int nx, int ny, LearnNorm nm, const RingDev* rings, int n_rings, float* ubox, float dux,
+                         float duy)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= NP) return;
     float f[7];
     for (int c = 0; c < 7; ++c) f[c] = raw0[g * 8 + c] + y[g * 16 + c] / nm.oscale[c];
+    f[0] += dux;                 // uniform correction: the momentum balance holds exactly
+    f[1] += duy;
     const float u1x = mom[NP + g], u1y = mom[2 * NP + g];
     st[PL_SXX * NP + g] = f[2];
     st[PL_SXY * NP + g] = f[3];
@@ -420,8 +428,10 @@ int lb_learned_step(lb_learned* L, int64_t calls, int64_t* n_fallbacks)
         // sigma, dP and the node jump first; then the force at the new state (the moments
         // pass reads the populations of t+1, unchanged, for drho); then the populations
         float* st = static_cast<float*>(h->state[h->cur]);
+        // uniform velocity correction so that sum u_net = sum u(t) + 16 F_pull exactly
+        const float dux = (float)(-mx / (double)h->plane), duy = (float)(-my / (double)h->plane);
         k_unpack<<<blocks(h->plane), 256, 0, h->stream>>>(L->raw0, y, st, h->moments, L->unet, h->plane, h->p.nx,
-                                                          h->p.ny, L->nm, h->rings, h->n_rings, h->ubox);
+                                                          h->p.ny, L->nm, h->rings, h->n_rings, h->ubox, dux, duy);
         LCK(L, cudaGetLastError());
         LCK(L, launch_nodes(handle_node_args(h, 15), h->stream, false));
         h->t += 15;

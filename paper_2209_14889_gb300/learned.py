@@ -190,7 +190,7 @@ def run(workload, net=None, norm=None, calls: int = 32, eps=(0.25, 0.5), warmup:
 
 
 def calibrate(net, norm, workload, calls: int = 32, target_err: float = 1e-2,
-              grid=(0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0, 5.0)):
+              grid=(0.02, 0.05, 0.1, 0.2, 0.5, 1.0, 2.0, 5.0, 20.0, 100.0)):
     """Residual bounds fixed on a validation trajectory: of the (eps_momentum, eps_tendency)
     pairs on the grid whose run keeps the restoring force within target_err (relative L2 over
     the readouts) of the plain solver, the one that accepts the most calls (ties: the tighter
