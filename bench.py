@@ -305,6 +305,12 @@ def measure_batched(args, lb, W, torch):
     return out
 
 
+# (level, Ci, Co) of the network's 3x3 convolutions (level l at 1/2^l resolution)
+NET_CONVS = [(0, 16, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 96), (2, 96, 96), (3, 96, 128),
+             (3, 128, 128), (2, 224, 96), (2, 96, 96), (1, 160, 64), (1, 64, 64), (0, 96, 32), (0, 32, 32),
+             (0, 32, 16)]
+
+
 def measure_learned(args, lb, torch):
     """The learned form at 256^2: training pairs from seeded trajectories of the batched recipe's
     physics (one lattice side), GPU training of the U-Net for a time budget, residual bounds
@@ -331,7 +337,30 @@ def measure_learned(args, lb, torch):
     fr_l, ms_l, stt = LR.run(w, inf, data.norm, calls=calls, eps=eps)
     err = float(np.linalg.norm(fr_l - fr_p) / np.linalg.norm(fr_p))
     cells = side * side
+    # network forward throughput at 256^2, batch 1, per convolution kernel (CUDA events)
+    flop = 2.0 * 9 * cells * sum(ci * co * 4 ** -lev for lev, ci, co in NET_CONVS)
+    xin = torch.zeros((1, side, side, 16), dtype=torch.bfloat16, device="cuda")
+    fwd = {}
+    for name, k in (("mma_sync", 0), ("tcgen05", 1)):
+        lb.conv_kernel(k)
+        for _ in range(3):
+            inf.forward(xin)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            inf.forward(xin)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        fwd[name] = {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12}
+    lb.conv_kernel(1)
+    lb.conv_status()
+    peaks, _ = measured_peaks()
     out = {"workload": "256x256 periodic, one ring (batched-recipe physics, seed 502), 64 calls of 16 steps",
+           "network_forward": {"gflop": flop / 1e9, "batch": 1, "by_kernel": fwd,
+                               "tensor_roofline": {"bound": "tensor", "achieved": fwd["tcgen05"]["tflops"],
+                                                   "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                                                   "frac": fwd["tcgen05"]["tflops"] / peaks.get("bf16_tflops", 1.0)}},
            "value": cells * calls * 16 / (ms_l * 1e-3) / 1e6, "unit": "MLUPS",
            "plain_fp32_mlups": cells * calls * 16 / (ms_p * 1e-3) / 1e6,
            "accepted_calls": stt["accepted"], "calls": calls,

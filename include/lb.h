@@ -295,6 +295,11 @@ int lb_net_shape(const lb_net* n, int32_t* batch, int32_t* height, int32_t* widt
 int lb_net_activation(lb_net* n, int32_t which, void* host, int64_t bytes);
 const char* lb_net_last_error(const lb_net* n);
 void lb_net_destroy(lb_net* n);
+/* Convolution kernel of the forward passes and data gradients (process-wide): 0 mma.sync
+ * m16n8k16 tiles, 1 tcgen05.mma with tensor-memory accumulators (default).  lb_conv_status returns
+ * LB_ETIMEOUT (once) if a tcgen05 convolution's bounded wait for its MMAs gave up. */
+int lb_conv_kernel(int32_t kernel);
+int lb_conv_status(void);
 int lb_conv3x3(const void* x, int64_t ldx, int32_t xoff, const void* w, const float* bias, void* y, float* yf,
                int64_t ldy, int32_t yoff, int32_t B, int32_t H, int32_t W, int32_t Ci, int32_t Co, int32_t act,
                void* stream);

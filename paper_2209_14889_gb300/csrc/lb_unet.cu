@@ -176,6 +176,163 @@ __global__ void __launch_bounds__(128) k_conv3x3(const ConvArgs a)
     }
 }
 
+// ------------------------------------------------------------------ convolution forward, tcgen05
+//
+// The same convolution on the 5th-generation tensor cores: per 16-channel chunk of the input,
+// the CTA stages the 10 x 18-pixel input tile and the chunk's weights of all 9 taps in shared
+// memory, one thread issues 9 taps x 8 output rows of tcgen05.mma (M = 128 output channels,
+// N = 16 pixels of one output row, K = 16 channels, BF16 -> FP32) into 8 accumulators of 16
+// columns each in tensor memory, and commits them to an mbarrier; after the last chunk the
+// four warps read their 32 lanes (output channels) back with tcgen05.ld for the epilogue.
+// Operands are in the canonical K-major layout without swizzle: core matrices of 8 rows x 16
+// bytes (8 BF16 of K), rows 16 bytes apart.  Input tile: [2 k-halves][180 pixels][8]; a pixel
+// row of the output is 16 consecutive tile pixels, so its two 8-pixel core matrices are 128
+// bytes apart (stride dimension) and the k-halves 180 x 16 bytes apart (leading dimension).
+// Weights: [9 taps][2 k-halves][128 channels][8]; channel groups of 8 are 128 bytes apart,
+// k-halves 2048 bytes.
+
+constexpr int TC_M = 128, TC_N = 16;
+constexpr int TC_NPIX = CT_IH * CT_IW;                              // 180
+constexpr int TC_SX = 2 * TC_NPIX * 8;                              // BF16 elements
+constexpr int TC_SW = 9 * 2 * TC_M * 8;
+// shared memory: weights, input tile, and slack after them so that every descriptor of this
+// kernel, read with its two strides exchanged, still stays inside the allocation
+constexpr int TC_SMEM_BYTES = (TC_SW + TC_SX) * 2 + 40 * 1024 + 64;
+
+__device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N, M
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int* err)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    bf16* sw = reinterpret_cast<bf16*>(tc_smem);
+    bf16* sx = sw + TC_SW;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_SMEM_BYTES - 64);
+    unsigned* tslot = reinterpret_cast<unsigned*>(tc_smem + TC_SMEM_BYTES - 48);
+
+    const int n_cot = (a.Co + TC_M - 1) / TC_M;
+    const int b = blockIdx.z / n_cot, co0 = (blockIdx.z % n_cot) * TC_M;
+    const int tx0 = blockIdx.x * CT_W, ty0 = blockIdx.y * CT_H;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+
+    bool ok = true;
+    int chunk = 0;
+    for (int c0 = 0; c0 < a.Ci; c0 += 16, ++chunk) {
+        for (int q = tid; q < TC_NPIX * 2; q += 128) {
+            const int p = q >> 1, h = q & 1;
+            const int py = p / CT_IW, px = p - py * CT_IW;
+            const int gy = ty0 - 1 + py, gx = tx0 - 1 + px;
+            uint4 v = zero;
+            if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+                v = *reinterpret_cast<const uint4*>(a.x + ((long long)(b * a.H + gy) * a.W + gx) * a.ldx + a.xoff + c0 +
+                                                    h * 8);
+            *reinterpret_cast<uint4*>(sx + (h * TC_NPIX + p) * 8) = v;
+        }
+        for (int q = tid; q < 9 * 2 * TC_M; q += 128) {
+            const int t = q / (2 * TC_M), r = q - t * (2 * TC_M);
+            const int h = r / TC_M, co = r - h * TC_M;
+            uint4 v = zero;
+            if (co0 + co < a.Co)
+                v = *reinterpret_cast<const uint4*>(a.w + ((long long)t * a.Co + co0 + co) * a.Ci + c0 + h * 8);
+            *reinterpret_cast<uint4*>(sw + ((t * 2 + h) * TC_M + co) * 8) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sw0 = smem_u32(sw), sx0 = smem_u32(sx);
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3 - 1, dx = t % 3 - 1;
+                const uint64_t ad = tc_desc(sw0 + (unsigned)(t * 2 * TC_M * 8 * 2), TC_M * 16, 128);
+                for (int r = 0; r < CT_H; ++r) {
+                    const int p0 = (r + 1 + dy) * CT_IW + (1 + dx);
+                    const uint64_t bd = tc_desc(sx0 + (unsigned)(p0 * 16), TC_NPIX * 16, 128);
+                    const unsigned d = tmem + (unsigned)(r * TC_N);
+                    const int acc = (c0 > 0 || t > 0) ? 1 : 0;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(mbar)));
+        }
+        // wait for this chunk's MMAs before the tile is overwritten (bounded)
+        const unsigned parity = (unsigned)(chunk & 1);
+        unsigned done = 0;
+        for (long it = 0; it < (1L << 26) && !done; ++it) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_u32(mbar)), "r"(parity));
+        }
+        if (!done) {
+            ok = false;
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+
+    if (ok) {
+        // epilogue: warp w holds output channels co0 + 32 w + lane, 16 pixels per row
+        const int co = co0 + warp * 32 + lane;
+        const float bv = (a.bias && co < a.Co) ? a.bias[co] : 0.f;
+        for (int r = 0; r < CT_H; ++r) {
+            unsigned v[16];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * TC_N);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int gy = ty0 + r;
+            if (co >= a.Co || gy >= a.H) continue;
+            for (int c = 0; c < TC_N; ++c) {
+                const int gx = tx0 + c;
+                if (gx >= a.W) continue;
+                float val = __uint_as_float(v[c]) + bv;
+                if (a.act) val = val > 0.f ? val : SLOPE * val;
+                const long long o = ((long long)(b * a.H + gy) * a.W + gx) * a.ldy + a.yoff + co;
+                if (a.yf) a.yf[o] = val;
+                else a.y[o] = __float2bfloat16_rn(val);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    }
+}
+
 // ------------------------------------------------------------------ weight gradient
 
 constexpr int WG_CO = 64, WG_CI = 16;           // output block of gw per CTA: [9][64][16]
@@ -520,12 +677,32 @@ int S_parts(int B, int H, int W)
     return tiles < 64 ? tiles : 64;
 }
 
+// convolution kernel: 0 mma.sync, 1 tcgen05 (TMEM accumulators, the default)
+int g_conv_kernel = 1;
+int* g_conv_err = nullptr;      // device flag: a tcgen05 convolution's bounded wait gave up
+
 cudaError_t conv_fwd(cudaStream_t s, const bf16* x, long long ldx, int xoff, const bf16* w, const float* bias, bf16* y,
                      float* yf, long long ldy, int yoff, int B, int H, int W, int Ci, int Co, int act)
 {
     ConvArgs a;
     a.x = x; a.ldx = ldx; a.xoff = xoff; a.w = w; a.bias = bias; a.y = y; a.yf = yf; a.ldy = ldy; a.yoff = yoff;
     a.B = B; a.H = H; a.W = W; a.Ci = Ci; a.Co = Co; a.act = act;
+    if (g_conv_kernel == 1) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        if (!g_conv_err) {
+            cudaError_t e = cudaMalloc(&g_conv_err, sizeof(int));
+            if (e == cudaSuccess) e = cudaMemset(g_conv_err, 0, sizeof(int));
+            if (e != cudaSuccess) return e;
+        }
+        dim3 grid((W + CT_W - 1) / CT_W, (H + CT_H - 1) / CT_H, B * ((Co + TC_M - 1) / TC_M));
+        k_conv3x3_tc<<<grid, 128, TC_SMEM_BYTES, s>>>(a, g_conv_err);
+        return cudaGetLastError();
+    }
     dim3 grid((W + CT_W - 1) / CT_W, (H + CT_H - 1) / CT_H, B * ((Co + CT_CO - 1) / CT_CO));
     k_conv3x3<<<grid, 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -863,6 +1040,26 @@ void lb_net_destroy(lb_net* n)
 }
 
 // ---- single-layer entry points (the building blocks, for tests against the oracle) ----
+
+int lb_conv_kernel(int32_t kernel)
+{
+    if (kernel != 0 && kernel != 1) return LB_EINVAL;
+    g_conv_kernel = kernel;
+    return LB_OK;
+}
+
+int lb_conv_status(void)
+{
+    if (!g_conv_err) return LB_OK;
+    int e = 0;
+    if (cudaMemcpy(&e, g_conv_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LB_ECUDA;
+    if (e) {
+        const int z = 0;
+        cudaMemcpy(g_conv_err, &z, sizeof(int), cudaMemcpyHostToDevice);
+        return LB_ETIMEOUT;
+    }
+    return LB_OK;
+}
 
 int lb_conv3x3(const void* x, int64_t ldx, int32_t xoff, const void* w, const float* bias, void* y, float* yf,
                int64_t ldy, int32_t yoff, int32_t B, int32_t H, int32_t W, int32_t Ci, int32_t Co, int32_t act,

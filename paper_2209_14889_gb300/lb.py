@@ -133,6 +133,8 @@ def lib():
             "lb_learned_stats": (ctypes.c_int, [_L, vp]),
             "lb_learned_last_error": (ctypes.c_char_p, [_L]),
             "lb_learned_destroy": (None, [_L]),
+            "lb_conv_kernel": (ctypes.c_int, [i32]),
+            "lb_conv_status": (ctypes.c_int, []),
             "lb_conv3x3": (ctypes.c_int, [vp, i64, i32, vp, vp, vp, vp, i64, i32, i32, i32, i32, i32, i32,
                                           i32, vp]),
             "lb_conv3x3_dgrad": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, i32, i32, vp]),
@@ -501,3 +503,12 @@ def conv3x3_wgrad(x, gz):
                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     _check(None, rc)
     return gw, gb
+
+
+def conv_kernel(kernel: int):
+    """Convolution kernel of the network: 0 mma.sync, 1 tcgen05 (tensor-memory accumulators)."""
+    _check(None, lib().lb_conv_kernel(int(kernel)))
+
+
+def conv_status():
+    _check(None, lib().lb_conv_status())

@@ -33,9 +33,21 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+KERNELS = [0, 1]      # mma.sync tiles, tcgen05 with tensor-memory accumulators
+
+
+@pytest.fixture(params=KERNELS, ids=["mma_sync", "tcgen05"])
+def conv_kernel(request):
+    torch, lb = _gpu()
+    lb.conv_kernel(request.param)
+    yield request.param
+    lb.conv_status()
+    lb.conv_kernel(1)
+
+
 @pytest.mark.parametrize("B,H,W,Ci,Co,act", [(2, 16, 32, 32, 48, False), (1, 8, 4, 16, 96, True),
-                                             (1, 24, 16, 224, 16, True)])
-def test_conv_forward_vs_oracle(B, H, W, Ci, Co, act):
+                                             (1, 24, 16, 224, 16, True), (1, 16, 16, 32, 160, False)])
+def test_conv_forward_vs_oracle(B, H, W, Ci, Co, act, conv_kernel):
     torch, lb = _gpu()
     r = np.random.Generator(np.random.PCG64(10 + Ci))
     xt, x = bf(torch, r.normal(size=(B, H, W, Ci)))
@@ -56,7 +68,7 @@ def test_conv_forward_vs_oracle(B, H, W, Ci, Co, act):
     assert np.all(np.abs(gotb - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max())
 
 
-def test_conv_into_channel_slice():
+def test_conv_into_channel_slice(conv_kernel):
     # the skip connections write into a channel slice of a wider buffer
     torch, lb = _gpu()
     r = np.random.Generator(np.random.PCG64(3))
@@ -72,7 +84,7 @@ def test_conv_into_channel_slice():
 
 
 @pytest.mark.parametrize("B,H,W,Ci,Co", [(2, 16, 16, 32, 64), (1, 8, 8, 96, 128), (1, 32, 16, 16, 32)])
-def test_conv_gradients_vs_oracle(B, H, W, Ci, Co):
+def test_conv_gradients_vs_oracle(B, H, W, Ci, Co, conv_kernel):
     torch, lb = _gpu()
     r = np.random.Generator(np.random.PCG64(20 + Co))
     xt, x = bf(torch, r.normal(size=(B, H, W, Ci)))
@@ -115,7 +127,7 @@ def _gpu_cache(net, x, y):
             "d0a": (c0, A["d0a"]), "d0b": (A["d0a"], A["d0b"]), "head": (A["d0b"], y)}
 
 
-def test_network_forward_and_gradients_vs_oracle():
+def test_network_forward_and_gradients_vs_oracle(conv_kernel):
     torch, lb = _gpu()
     B, H, W = 2, 32, 32
     P = U.init_params(seed=7)
