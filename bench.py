@@ -311,6 +311,27 @@ NET_CONVS = [(0, 16, 32), (0, 32, 32), (1, 32, 64), (1, 64, 64), (2, 64, 96), (2
              (0, 32, 16)]
 
 
+def run_only_net(args):
+    """Forward passes of the network at 256^2, batch 1, with the default (tcgen05) convolutions."""
+    import torch
+    from paper_2209_14889_gb300 import lb
+    net = lb.Net(1, 256, 256, seed=1)
+    x = torch.zeros((1, 256, 256, 16), dtype=torch.bfloat16, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    lb.conv_status()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flop = 2.0 * 9 * 256 * 256 * sum(ci * co * 4 ** -lev for lev, ci, co in NET_CONVS)
+    print(json.dumps({"network_forward_ms": ms, "tflops": flop / (ms * 1e-3) / 1e12, "steps": args.steps}))
+    net.close()
+
+
 def measure_learned(args, lb, torch):
     """The learned form at 256^2: training pairs from seeded trajectories of the batched recipe's
     physics (one lattice side), GPU training of the U-Net for a time budget, residual bounds
@@ -406,6 +427,8 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=["auto", "tile", "pair", "sweep"],
                     help="lattice kernel (auto: the fastest measured, the one-cell tile kernel)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload")
+    ap.add_argument("--only-net", action="store_true",
+                    help="time the network's forward pass at 256^2 (batch 1) only (for profiling)")
     ap.add_argument("--learned-seconds", type=float, default=45.0,
                     help="training budget of the learned form (0: skip it)")
     ap.add_argument("--tune-cache", default=None,
@@ -416,6 +439,8 @@ def main():
     rank, local, world = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only_net:
+        return run_only_net(args)
 
     import numpy as np
     import torch
