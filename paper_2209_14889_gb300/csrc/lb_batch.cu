@@ -32,10 +32,9 @@ __host__ __device__ constexpr int shape_tx(int s) { return s == 0 ? 32 : (s == 1
 __host__ __device__ constexpr int shape_ty(int s) { return s == 0 ? 16 : (s == 1 ? 8 : (s == 2 ? 8 : 16)); }
 
 constexpr size_t cmaxz(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t BATCH_SMEM =
-    cmaxz(cmaxz(tile::TileGeo<32, 16>::SMEM_BYTES, tile::TileGeo<32, 8>::SMEM_BYTES),
-          cmaxz(cmaxz(tile::TileGeo<64, 8>::SMEM_BYTES, tile::TileGeo<16, 16>::SMEM_BYTES),
-                sizeof(float) * dif::SMEM));
+// dynamic shared memory of the kernel of one tile shape
+template <int TX, int TY>
+constexpr size_t batch_smem() { return cmaxz(tile::TileGeo<TX, TY>::SMEM_BYTES, sizeof(float) * dif::SMEM); }
 
 struct BatchInst {
     FusedArgs fa[2];            // lattice step from buffer p to buffer p^1, p = 0, 1
@@ -112,6 +111,11 @@ __device__ bool grid_sync(const BatchArgs& B)
     return s_ok != 0;
 }
 
+// One kernel per tile shape: the instances of a batch are grouped by their shape and each group
+// runs its own persistent launch (one tile body per kernel keeps within the register budget of
+// two 256-thread CTAs per SM; the instances are independent, so the groups need no common
+// barrier).
+template <int TX, int TY>
 __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
 {
     extern __shared__ __align__(16) float sm[];
@@ -128,12 +132,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
             const int by = local / I.tiles_x, bx = local - by * I.tiles_x;
             // the tile step of lb_step; coherent loads: the state was written by the previous step
             // of this launch
-            switch (I.shape) {
-                case 0: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 16, true>(I.fa[par], bx, by, local, sm); break;
-                case 1: tile::tile_step<MODE_STEP, cell::PREC_FP32, 32, 8, true>(I.fa[par], bx, by, local, sm); break;
-                case 2: tile::tile_step<MODE_STEP, cell::PREC_FP32, 64, 8, true>(I.fa[par], bx, by, local, sm); break;
-                default: tile::tile_step<MODE_STEP, cell::PREC_FP32, 16, 16, true>(I.fa[par], bx, by, local, sm); break;
-            }
+            tile::tile_step<MODE_STEP, cell::PREC_FP32, TX, TY, true>(I.fa[par], bx, by, local, sm);
             __syncthreads();     // shared memory is reused by the next item
         }
         ok = grid_sync(B);
@@ -186,13 +185,19 @@ struct lb_batch {
     cudaStream_t stream = nullptr;          // the batch's own stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<int> shape;                 // per instance
-    BatchInst* d_inst = nullptr;
-    int *d_tile_begin = nullptr, *d_node_begin = nullptr, *d_dif_begin = nullptr;
-    int* d_cur = nullptr;
-    unsigned* d_bar = nullptr;
+    // per tile shape: the group of instances with that shape (device descriptors, prefix sums)
+    BatchInst* d_inst[N_SHAPES] = {};
+    int* d_tile_begin[N_SHAPES] = {};
+    int* d_node_begin[N_SHAPES] = {};
+    int* d_dif_begin[N_SHAPES] = {};
+    int n_group[N_SHAPES] = {};
+    int max_dsub[N_SHAPES] = {};
+    int grid[N_SHAPES] = {};                // CTAs of each shape's persistent launch
+    int* d_cur = nullptr;                   // buffer parity, one word per group
+    unsigned* d_bar = nullptr;              // barrier words, two per group
     int* d_err = nullptr;
     std::vector<double*> partials;          // per instance: readout partial sums sized for any shape
-    int max_dsub = 0, grid = 0, chunk = 10;
+    int chunk = 10;
     unsigned extra_arrivals = 0;
     unsigned long long wait_ns = 2000000000ull;
     cudaGraphExec_t graph = nullptr;
@@ -224,78 +229,112 @@ void drop_graph(lb_batch* b)
     b->graph_tried = false;
 }
 
-// (re)build the per-instance descriptors for the current tile shapes
+// (re)build the per-instance descriptors of every shape group for the current tile shapes
 int build_plan(lb_batch* b)
 {
     const int n = (int)b->h.size();
-    std::vector<BatchInst> inst(n);
-    std::vector<int> tb(n + 1, 0), nb(n + 1, 0), db(n + 1, 0);
-    b->max_dsub = 0;
-    for (int i = 0; i < n; ++i) {
-        lb_handle* h = b->h[i];
-        BatchInst& I = inst[i];
-        const int save = h->cur;
-        for (int p = 0; p < 2; ++p) {
-            h->cur = p;
-            I.fa[p] = handle_fused_args(h);
-            I.fa[p].partials = b->partials[i];
+    for (int sh = 0; sh < N_SHAPES; ++sh) {
+        std::vector<BatchInst> inst;
+        std::vector<int> tb(1, 0), nb(1, 0), db(1, 0);
+        b->max_dsub[sh] = 0;
+        for (int i = 0; i < n; ++i) {
+            if (b->shape[i] != sh) continue;
+            lb_handle* h = b->h[i];
+            BatchInst I;
+            const int save = h->cur;
+            for (int p = 0; p < 2; ++p) {
+                h->cur = p;
+                I.fa[p] = handle_fused_args(h);
+                I.fa[p].partials = b->partials[i];
+            }
+            h->cur = save;
+            I.na = handle_node_args(h, 1);
+            I.na.partials = b->partials[i];
+            I.shape = sh;
+            I.tiles_x = (h->p.nx + shape_tx(sh) - 1) / shape_tx(sh);
+            I.tiles_y = (h->p.ny + shape_ty(sh) - 1) / shape_ty(sh);
+            I.na.n_partials = I.tiles_x * I.tiles_y;
+            for (int p = 0; p < 2; ++p) I.sig[p] = static_cast<float*>(h->state[p]) + (size_t)PL_SXX * h->plane;
+            I.dsub = h->p.diffusion_substeps;
+            I.dsub_D = I.dsub > 0 ? (float)(h->p.Dp / I.dsub) : 0.f;
+            I.dif_tx = diffuse_tiles_x(h->p.nx);
+            I.dif_ty = diffuse_tiles_y(h->p.ny);
+            b->max_dsub[sh] = std::max(b->max_dsub[sh], I.dsub);
+            tb.push_back(tb.back() + I.tiles_x * I.tiles_y);
+            nb.push_back(nb.back() + h->n_node_ctas);
+            db.push_back(db.back() + (I.dsub > 0 ? I.dif_tx * I.dif_ty : 0));
+            inst.push_back(I);
         }
-        h->cur = save;
-        I.na = handle_node_args(h, 1);
-        I.na.partials = b->partials[i];
-        I.shape = b->shape[i];
-        I.tiles_x = (h->p.nx + shape_tx(I.shape) - 1) / shape_tx(I.shape);
-        I.tiles_y = (h->p.ny + shape_ty(I.shape) - 1) / shape_ty(I.shape);
-        I.na.n_partials = I.tiles_x * I.tiles_y;
-        for (int p = 0; p < 2; ++p) I.sig[p] = static_cast<float*>(h->state[p]) + (size_t)PL_SXX * h->plane;
-        I.dsub = h->p.diffusion_substeps;
-        I.dsub_D = I.dsub > 0 ? (float)(h->p.Dp / I.dsub) : 0.f;
-        I.dif_tx = diffuse_tiles_x(h->p.nx);
-        I.dif_ty = diffuse_tiles_y(h->p.ny);
-        b->max_dsub = std::max(b->max_dsub, I.dsub);
-        tb[i + 1] = tb[i] + I.tiles_x * I.tiles_y;
-        nb[i + 1] = nb[i] + h->n_node_ctas;
-        db[i + 1] = db[i] + (I.dsub > 0 ? I.dif_tx * I.dif_ty : 0);
+        b->n_group[sh] = (int)inst.size();
+        if (inst.empty()) continue;
+        const int g = (int)inst.size();
+        BCK(b, cudaMemcpy(b->d_inst[sh], inst.data(), sizeof(BatchInst) * g, cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_tile_begin[sh], tb.data(), sizeof(int) * (g + 1), cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_node_begin[sh], nb.data(), sizeof(int) * (g + 1), cudaMemcpyHostToDevice));
+        BCK(b, cudaMemcpy(b->d_dif_begin[sh], db.data(), sizeof(int) * (g + 1), cudaMemcpyHostToDevice));
     }
-    BCK(b, cudaMemcpy(b->d_inst, inst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_node_begin, nb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_dif_begin, db.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     drop_graph(b);
     return LB_OK;
 }
 
-BatchArgs batch_args(const lb_batch* b)
+BatchArgs batch_args(const lb_batch* b, int sh)
 {
     BatchArgs a;
-    a.inst = b->d_inst;
-    a.n_inst = (int)b->h.size();
-    a.tile_begin = b->d_tile_begin;
-    a.node_begin = b->d_node_begin;
-    a.dif_begin = b->d_dif_begin;
-    a.max_dsub = b->max_dsub;
-    a.cur = b->d_cur;
-    a.bar = b->d_bar;
+    a.inst = b->d_inst[sh];
+    a.n_inst = b->n_group[sh];
+    a.tile_begin = b->d_tile_begin[sh];
+    a.node_begin = b->d_node_begin[sh];
+    a.dif_begin = b->d_dif_begin[sh];
+    a.max_dsub = b->max_dsub[sh];
+    a.cur = b->d_cur + sh;
+    a.bar = b->d_bar + 2 * sh;
     a.err = b->d_err;
     a.extra_arrivals = b->extra_arrivals;
     a.wait_ns = b->wait_ns;
     return a;
 }
 
-cudaError_t launch_batch(const lb_batch* b, int nsteps)
+template <int TX, int TY>
+cudaError_t launch_shape(const lb_batch* b, int sh, int nsteps)
 {
-    BatchArgs a = batch_args(b);
+    BatchArgs a = batch_args(b, sh);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b->grid);
+    cfg.gridDim = dim3(b->grid[sh]);
     cfg.blockDim = dim3(BT);
-    cfg.dynamicSmemBytes = BATCH_SMEM;
+    cfg.dynamicSmemBytes = batch_smem<TX, TY>();
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch, a, nsteps);
+    return cudaLaunchKernelEx(&cfg, k_batch<TX, TY>, a, nsteps);
+}
+
+// one persistent launch per non-empty shape group, one after another on the batch stream
+cudaError_t launch_batch(const lb_batch* b, int nsteps)
+{
+    cudaError_t e = cudaSuccess;
+    if (b->n_group[0] && e == cudaSuccess) e = launch_shape<32, 16>(b, 0, nsteps);
+    if (b->n_group[1] && e == cudaSuccess) e = launch_shape<32, 8>(b, 1, nsteps);
+    if (b->n_group[2] && e == cudaSuccess) e = launch_shape<64, 8>(b, 2, nsteps);
+    if (b->n_group[3] && e == cudaSuccess) e = launch_shape<16, 16>(b, 3, nsteps);
+    return e;
+}
+
+// shared-memory opt-in and the co-resident grid of one shape's kernel
+template <int TX, int TY>
+cudaError_t setup_shape(lb_batch* b, int sh, int n_sm)
+{
+    const size_t smem = batch_smem<TX, TY>();
+    cudaError_t e = cudaFuncSetAttribute(k_batch<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TX, TY>, BT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    b->grid[sh] = n_sm * per_sm;
+    return cudaSuccess;
 }
 
 // Capture one persistent launch of `chunk` steps as a graph (once per plan).  If capture or
@@ -369,12 +408,14 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(LB_ECUDA);
-    if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
-        cudaMalloc(&b->d_tile_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_node_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_dif_begin, sizeof(int) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_cur, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+    for (int sh = 0; sh < N_SHAPES; ++sh)
+        if (cudaMalloc(&b->d_inst[sh], sizeof(BatchInst) * n) != cudaSuccess ||
+            cudaMalloc(&b->d_tile_begin[sh], sizeof(int) * (n + 1)) != cudaSuccess ||
+            cudaMalloc(&b->d_node_begin[sh], sizeof(int) * (n + 1)) != cudaSuccess ||
+            cudaMalloc(&b->d_dif_begin[sh], sizeof(int) * (n + 1)) != cudaSuccess)
+            return cleanup(LB_ENOMEM);
+    if (cudaMalloc(&b->d_cur, sizeof(int) * N_SHAPES) != cudaSuccess ||
+        cudaMalloc(&b->d_bar, 2 * sizeof(unsigned) * N_SHAPES) != cudaSuccess ||
         cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess)
         return cleanup(LB_ENOMEM);
     for (int i = 0; i < n; ++i) {
@@ -387,18 +428,17 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
     // the handles' queued work must be done before the batch's control words are set
     if (cudaStreamSynchronize(b->user) != cudaSuccess) return cleanup(LB_ECUDA);
     const int c0 = handles[0]->cur;
-    if (cudaMemcpy(b->d_cur, &c0, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
+    const int c4[N_SHAPES] = {c0, c0, c0, c0};
+    if (cudaMemcpy(b->d_cur, c4, sizeof(c4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned) * N_SHAPES) != cudaSuccess ||
         cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess)
         return cleanup(LB_ECUDA);
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM) != cudaSuccess)
-        return cleanup(LB_ECUDA);
-    int dev = 0, n_sm = 0, per_sm = 0;
+    int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, BATCH_SMEM) != cudaSuccess || per_sm < 1)
+    if (setup_shape<32, 16>(b, 0, n_sm) != cudaSuccess || setup_shape<32, 8>(b, 1, n_sm) != cudaSuccess ||
+        setup_shape<64, 8>(b, 2, n_sm) != cudaSuccess || setup_shape<16, 16>(b, 3, n_sm) != cudaSuccess)
         return cleanup(LB_ECUDA);
-    b->grid = n_sm * per_sm;
     const int rc = build_plan(b);
     if (rc != LB_OK) return cleanup(rc);
     *out = b;
@@ -437,7 +477,7 @@ int lb_batch_sync(lb_batch* b)
     BCK(b, cudaMemcpy(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         const int z = 0;
-        unsigned zb[2] = {0u, 0u};
+        unsigned zb[2 * N_SHAPES] = {};
         BCK(b, cudaMemcpy(b->d_err, &z, sizeof(int), cudaMemcpyHostToDevice));
         BCK(b, cudaMemcpy(b->d_bar, zb, sizeof zb, cudaMemcpyHostToDevice));
         return bfail(b, LB_ETIMEOUT, "a grid barrier of the batched kernel timed out; the states are undefined");
@@ -449,7 +489,7 @@ int lb_batch_sync(lb_batch* b)
     return LB_OK;
 }
 
-int32_t lb_batch_grid(const lb_batch* b) { return b ? b->grid : 0; }
+int32_t lb_batch_grid(const lb_batch* b) { return b ? b->grid[0] : 0; }
 
 int32_t lb_batch_uses_graph(const lb_batch* b) { return b && b->graph ? 1 : 0; }
 
@@ -537,8 +577,8 @@ int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps)
             }
         }
     }
-    int dcur = 0;
-    BCK(b, cudaMemcpy(&dcur, b->d_cur, sizeof(int), cudaMemcpyDeviceToHost));
+    int dcur[N_SHAPES] = {};
+    BCK(b, cudaMemcpy(dcur, b->d_cur, sizeof dcur, cudaMemcpyDeviceToHost));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -579,7 +619,7 @@ int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps)
     for (size_t k = 0; k < saved.size(); ++k)
         cudaMemcpy(saved[k].first, saved[k].second, saved_bytes[k], cudaMemcpyDeviceToDevice);
     release();
-    cudaMemcpy(b->d_cur, &dcur, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_cur, dcur, sizeof dcur, cudaMemcpyHostToDevice);
     int berr = 0;
     cudaMemcpy(&berr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (rc != LB_OK) return rc;
@@ -611,10 +651,12 @@ void lb_batch_destroy(lb_batch* b)
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
-    cudaFree(b->d_inst);
-    cudaFree(b->d_tile_begin);
-    cudaFree(b->d_node_begin);
-    cudaFree(b->d_dif_begin);
+    for (int sh = 0; sh < N_SHAPES; ++sh) {
+        cudaFree(b->d_inst[sh]);
+        cudaFree(b->d_tile_begin[sh]);
+        cudaFree(b->d_node_begin[sh]);
+        cudaFree(b->d_dif_begin[sh]);
+    }
     cudaFree(b->d_cur);
     cudaFree(b->d_bar);
     cudaFree(b->d_err);

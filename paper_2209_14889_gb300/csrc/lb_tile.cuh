@@ -357,7 +357,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const int nx = a.nx, ny = a.ny;
     const long long NP = a.plane;
     const int x0 = bx * TX, y0 = by * TY;
-    const Phys ph = a.ph;
+    const Phys& ph = a.ph;
     const void* src = a.src;
 
     stage<PREC, COH>(a, m, x0, y0);
@@ -565,7 +565,7 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
     // plane size and pair start (x0 + lx, lx even) even
     const bool nx_even = (nx & 1) == 0;
     const int x0 = bx * TX, y0 = by * TY;
-    const Phys ph = a.ph;
+    const Phys& ph = a.ph;
     const void* src = a.src;
 
     stage<PREC, COH>(a, m, x0, y0);
