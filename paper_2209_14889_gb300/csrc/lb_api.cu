@@ -56,6 +56,7 @@ void free_rings(lb_handle* h)
 {
     dfree(h->rings);
     dfree(h->X);
+    dfree(h->X_alt);
     dfree(h->node_cell);
     dfree(h->node_frac);
     dfree(h->node_force);
@@ -113,6 +114,7 @@ NodeArgs node_args(lb_handle* h, int advance)
     a.n_rings = h->n_rings;
     a.rings = h->rings;
     a.X = h->X;
+    a.X_out = advance ? h->X_alt : h->X;     // no advance: the same values written in place
     a.node_cell = h->node_cell;
     a.node_frac = h->node_frac;
     a.node_force = h->node_force;
@@ -462,6 +464,7 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
     if (n_rings > 0) {
         CK(h, cudaMalloc(&h->rings, sizeof(RingDev) * n_rings));
         CK(h, cudaMalloc(&h->X, sizeof(double2) * off));
+        CK(h, cudaMalloc(&h->X_alt, sizeof(double2) * off));
         CK(h, cudaMalloc(&h->node_cell, sizeof(int2) * off));
         CK(h, cudaMalloc(&h->node_frac, sizeof(float2) * off));
         CK(h, cudaMalloc(&h->node_force, sizeof(float2) * off));
@@ -524,6 +527,7 @@ int lb_step(lb_handle* h, int64_t n)
             if (e0) cudaEventRecord(e0, h->stream);
         }
         CK(h, launch_nodes(node_args(h, 1), h->stream, pdl && !sweep));
+        std::swap(h->X, h->X_alt);
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
         h->cur ^= 1;
         h->t += 1;

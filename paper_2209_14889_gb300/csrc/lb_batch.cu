@@ -40,6 +40,7 @@ struct BatchInst {
     FusedArgs fa[2];            // lattice step from buffer p to buffer p^1, p = 0, 1
     NodeArgs na;
     float* sig[2];              // sigma planes of buffer 0 and 1
+    double2* xb[2];             // node positions read in a step whose lattice source is buffer p
     int shape, tiles_x, tiles_y;
     int dsub;                   // diffusion sub-steps (0: none)
     float dsub_D;               // D_p / dsub
@@ -166,7 +167,10 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
         if (!ok) break;
         for (int item = blockIdx.x; item < n_nodes; item += gridDim.x) {
             const int i = find_inst(B.node_begin, B.n_inst, item);
-            node::node_block(B.inst[i].na, item - __ldg(B.node_begin + i));
+            NodeArgs na = B.inst[i].na;
+            na.X = B.inst[i].xb[par];
+            na.X_out = B.inst[i].xb[par ^ 1];
+            node::node_block(na, item - __ldg(B.node_begin + i));
             __syncthreads();
         }
         ok = grid_sync(B);
@@ -250,6 +254,8 @@ int build_plan(lb_batch* b)
             h->cur = save;
             I.na = handle_node_args(h, 1);
             I.na.partials = b->partials[i];
+            I.xb[h->cur] = h->X;
+            I.xb[h->cur ^ 1] = h->X_alt;
             I.shape = sh;
             I.tiles_x = (h->p.nx + shape_tx(sh) - 1) / shape_tx(sh);
             I.tiles_y = (h->p.ny + shape_ty(sh) - 1) / shape_ty(sh);
@@ -378,6 +384,7 @@ int run_steps(lb_batch* b, long long n)
     for (lb_handle* h : b->h) {
         h->t += n;
         h->cur ^= (int)(n & 1);
+        if (n & 1) std::swap(h->X, h->X_alt);
     }
     return LB_OK;
 }

@@ -35,7 +35,9 @@ struct lb_handle {
     // rings
     int n_rings = 0, n_total = 0;
     RingDev* rings = nullptr;
-    double2* X = nullptr;
+    double2* X = nullptr;                   // node positions of the current step
+    double2* X_alt = nullptr;               // the other position buffer: an advancing node launch
+                                            // reads X and writes X_alt, then the two swap
     int2* node_cell = nullptr;
     float2* node_frac = nullptr;
     float2* node_force = nullptr;

@@ -92,7 +92,9 @@ struct NodeArgs {
     const int* ring_ctas;
     unsigned* ring_tickets;      // per ring: arrival counter
     double* node_partials;       // per CTA: F_rest (2), COM (2), box min/max (4)
-    double2* X;                  // FP64 master node positions, wrapped into [0, n)
+    const double2* X;            // FP64 master node positions, wrapped into [0, n) (read)
+    double2* X_out;              // the advanced positions (written; a different buffer than X when
+                                 // advancing: other CTAs read their halo nodes from X meanwhile)
     int2* node_cell;
     float2* node_frac;
     float2* node_force;

@@ -434,6 +434,7 @@ int lb_learned_step(lb_learned* L, int64_t calls, int64_t* n_fallbacks)
                                                           h->p.ny, L->nm, h->rings, h->n_rings, h->ubox, dux, duy);
         LCK(L, cudaGetLastError());
         LCK(L, launch_nodes(handle_node_args(h, 15), h->stream, false));
+        std::swap(h->X, h->X_alt);
         h->t += 15;
         rc = moments(h, L->frc);
         if (rc != LB_OK) return lfail(L, rc, "moments");

@@ -229,7 +229,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
             const float fx = tex[j] - tex[j - 1] - eps * (dpx[j + 1] + dqx[j - 1] - dpx[j] - dqx[j]) + (float)R.pull_x;
             const float fy = tey[j] - tey[j - 1] - eps * (dpy[j + 1] + dqy[j - 1] - dpy[j] - dqy[j]) + (float)R.pull_y;
             a.node_force[off + k] = make_float2(fx, fy);
-            a.X[off + k] = Xn;
+            a.X_out[off + k] = Xn;
             int cx = (int)Xn.x, cy = (int)Xn.y;
             float frx = (float)(Xn.x - cx), fry = (float)(Xn.y - cy);
             if (frx >= 1.f) { frx = 0.f; cx += 1; }
