@@ -187,7 +187,22 @@ int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, doub
 #define LB_KERNEL_PAIR 3
 int lb_set_kernel(lb_handle* h, int32_t kernel);
 
-/* Number of kernels launched per lb_step(1) call (2: fused lattice + node kernel). */
+/*
+ * Where lb_step runs the node step (App. A: interpolation of u onto the nodes, their advection
+ * and forces, the ring readouts) relative to the lattice step of the same time step.
+ * enable = 1 (default): in the tail of the tile kernels (LB_KERNEL_TILE, _PAIR, _AUTO), one launch
+ * per step: once the last tile whose region meets a ring's work box is done, that ring's node
+ * blocks run in tiles that finish later while the other tiles still run.  enable = 0: a separate
+ * node kernel after each lattice kernel.  Both compute the same values bit for bit;
+ * LB_KERNEL_SWEEP always takes the separate kernel.  LB_EINVAL for other values.
+ */
+int lb_set_node_tail(lb_handle* h, int32_t enable);
+
+/*
+ * Number of kernels launched per lb_step(1) call: 1 (tile kernel with the node tail) or 2
+ * (lattice + node kernel), plus, with s > 0 diffusion sub-steps, s sub-step launches and one
+ * copy when s is odd.
+ */
 int32_t lb_launches_per_step(const lb_handle* h);
 
 /* Bytes of lattice state per cell moved by one step (read + write, the algorithmic minimum). */

@@ -66,9 +66,12 @@ void free_rings(lb_handle* h)
     dfree(h->ring_cta0);
     dfree(h->ring_ctas);
     dfree(h->ring_tickets);
+    dfree(h->box_tickets);
+    dfree(h->ring_claim);
     dfree(h->node_partials);
     h->n_node_ctas = 1;
     h->n_rings = h->n_total = 0;
+    h->tile_rot = 0;
     h->row_len = 6;
 }
 
@@ -84,7 +87,7 @@ cudaEvent_t ev_get(std::vector<cudaEvent_t>& pool, size_t& used)
 
 FusedArgs fused_args(lb_handle* h)
 {
-    FusedArgs a;
+    FusedArgs a = {};
     a.src = h->state[h->cur];
     a.dst = h->state[h->cur ^ 1];
     a.prec = h->p.precision == LB_FP32 ? 0 : 1;
@@ -377,6 +380,13 @@ int lb_init_fields(lb_handle* h, const double* noise)
     if (rc != LB_OK) return rc;
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     h->t = 0;
+    h->after_tail = false;
+    if (h->n_rings > 0) {
+        // restart at t = 0: the work box of the current positions into the slot of even steps
+        CK(h, cudaMemsetAsync(h->box_tickets, 0, sizeof(unsigned) * h->n_rings, h->stream));
+        CK(h, cudaMemsetAsync(h->ring_claim, 0, sizeof(unsigned long long) * h->n_rings, h->stream));
+        CK(h, launch_nodes(node_args(h, 0), h->stream));
+    }
     h->fields_ready = true;
     CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
@@ -416,6 +426,9 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
         // supports of its nodes) must span less than half the lattice
         const int lim = std::min(nx, ny) - 8;
         int cw = (int)std::ceil(mxx - mnx) + 8, chh = (int)std::ceil(mxy - mny) + 8;
+        // the tail launches start at the tile row over the first ring's top (minus the box
+        // margin and the staged halo), so its node blocks run while most tiles are still to come
+        if (r == 0) h->tile_rot = fused_tile_rot(nx, ny, P[1] + mny - 4.0);
         if (2 * cw > nx || 2 * chh > ny) return fail(h, LB_EINVAL, "ring %d does not fit the lattice", r);
         cw = std::min(cw + 2 * std::max(16, cw / 2), lim);
         chh = std::min(chh + 2 * std::max(16, chh / 2), lim);
@@ -429,9 +442,8 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
         d.pull_y = g.pull_force * std::sin(g.pull_angle) / g.n_nodes;
         // until the first node-kernel pass the box is empty; its origin is node 0's cell, the
         // reference from which the node kernel measures the ring's extent
-        d.box_x0 = (int)std::floor(X[off].x);
-        d.box_y0 = (int)std::floor(X[off].y);
-        d.box_w = d.box_h = 0;
+        d.box[0] = make_int4((int)std::floor(X[off].x), (int)std::floor(X[off].y), 0, 0);
+        d.box[1] = d.box[0];
         d.cap_w = cw;
         d.cap_h = chh;
         d.box_off = box_off;
@@ -461,6 +473,10 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
     CK(h, cudaMemcpy(h->ring_cta0, cta0.data(), sizeof(int) * cta0.size(), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->ring_ctas, nctas.data(), sizeof(int) * nctas.size(), cudaMemcpyHostToDevice));
     CK(h, cudaMemset(h->ring_tickets, 0, sizeof(unsigned) * nctas.size()));
+    CK(h, cudaMalloc(&h->box_tickets, sizeof(unsigned) * nctas.size()));
+    CK(h, cudaMemset(h->box_tickets, 0, sizeof(unsigned) * nctas.size()));
+    CK(h, cudaMalloc(&h->ring_claim, sizeof(unsigned long long) * nctas.size()));
+    CK(h, cudaMemset(h->ring_claim, 0, sizeof(unsigned long long) * nctas.size()));
     if (n_rings > 0) {
         CK(h, cudaMalloc(&h->rings, sizeof(RingDev) * n_rings));
         CK(h, cudaMalloc(&h->X, sizeof(double2) * off));
@@ -504,15 +520,30 @@ int lb_step(lb_handle* h, int64_t n)
         // CTAs per SM, and 121 us for the sweep)
         const bool sweep = h->kernel == LB_KERNEL_SWEEP;
         const bool pair = h->kernel == LB_KERNEL_PAIR;
-        // consecutive lattice and node kernels overlap by programmatic dependent launch, except
-        // when per-kernel timing brackets each launch with events
+        // consecutive kernels overlap by programmatic dependent launch, except when per-kernel
+        // timing brackets each launch with events
         const bool pdl = !h->timing;
+        // the tile kernels run the node step in their tail: one launch per step
+        const bool tail = h->node_tail && !sweep;
         if (sweep) {
             CK(h, launch_sweep(fa, h->sweep_chunk, h->stream));
             h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
         } else {
-            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl, pair));
+            if (tail) {
+                h->n_partials = fused_ctas(h->p.nx, h->p.ny);
+                fa.node_tail = 1;
+                fa.t = h->t;
+                fa.tile_rot = h->tile_rot;
+                fa.box_tickets = h->box_tickets;
+                fa.ring_claim = h->ring_claim;
+                fa.na = node_args(h, 1);
+            }
+            // without the tail, a lattice kernel stages the state before its dependency wait,
+            // which is safe behind a node kernel only: after a launch with the tail it waits for
+            // that launch to complete
+            CK(h, launch_fused(fa, MODE_STEP, h->stream, &h->n_partials, pdl && (tail || !h->after_tail), pair));
         }
+        h->after_tail = tail;
         if (h->p.diffusion_substeps > 0) {
             // sigma of the new state; the old state's sigma planes serve as the other buffer
             float* sig_new = static_cast<float*>(h->state[h->cur ^ 1]) + (size_t)PL_SXX * h->plane;
@@ -521,14 +552,16 @@ int lb_step(lb_handle* h, int64_t n)
                                    (float)(h->p.Dp / h->p.diffusion_substeps), h->p.diffusion_substeps, h->stream));
         }
         if (h->timing && e1) cudaEventRecord(e1, h->stream);
-        if (h->timing) {
-            e0 = ev_get(h->ev_nodes, h->ev_nodes_used);
-            e1 = ev_get(h->ev_nodes, h->ev_nodes_used);
-            if (e0) cudaEventRecord(e0, h->stream);
+        if (!tail) {
+            if (h->timing) {
+                e0 = ev_get(h->ev_nodes, h->ev_nodes_used);
+                e1 = ev_get(h->ev_nodes, h->ev_nodes_used);
+                if (e0) cudaEventRecord(e0, h->stream);
+            }
+            CK(h, launch_nodes(node_args(h, 1), h->stream, pdl && !sweep));
+            if (h->timing && e1) cudaEventRecord(e1, h->stream);
         }
-        CK(h, launch_nodes(node_args(h, 1), h->stream, pdl && !sweep));
         std::swap(h->X, h->X_alt);
-        if (h->timing && e1) cudaEventRecord(e1, h->stream);
         h->cur ^= 1;
         h->t += 1;
     }
@@ -679,7 +712,21 @@ int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, doub
     return LB_OK;
 }
 
-int32_t lb_launches_per_step(const lb_handle* h) { return h ? 2 : 0; }
+int32_t lb_launches_per_step(const lb_handle* h)
+{
+    if (!h) return 0;
+    const int s = h->p.diffusion_substeps;
+    const bool tail = h->node_tail && h->kernel != LB_KERNEL_SWEEP;
+    return (tail ? 1 : 2) + (s > 0 ? s + (s & 1) : 0);
+}
+
+int lb_set_node_tail(lb_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (enable != 0 && enable != 1) return fail(h, LB_EINVAL, "enable must be 0 or 1");
+    h->node_tail = enable != 0;
+    return LB_OK;
+}
 
 int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries)
 {

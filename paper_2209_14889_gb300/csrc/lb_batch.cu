@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
             NodeArgs na = B.inst[i].na;
             na.X = B.inst[i].xb[par];
             na.X_out = B.inst[i].xb[par ^ 1];
-            node::node_block(na, item - __ldg(B.node_begin + i));
+            // the tiles' shared memory is free in this phase
+            node::node_block(na, item - __ldg(B.node_begin + i), *reinterpret_cast<node::NodeSmem*>(sm));
             __syncthreads();
         }
         ok = grid_sync(B);

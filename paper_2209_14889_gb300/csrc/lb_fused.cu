@@ -1,8 +1,11 @@
 // lb_fused.cu -- the tile kernels: one CTA per 32 x 16 tile of the fused step (lb_tile.cuh), one
 // cell per thread (tile_step) or two neighbouring cells per thread on paired FP32 instructions
-// (tile_step2).
+// (tile_step2); optionally with the node step of the same time step in their tail.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
+#include "lb_node.cuh"
 #include "lb_tile.cuh"
 
 namespace vlb {
@@ -11,23 +14,184 @@ namespace {
 
 using namespace tile;
 
+// Tiles c = 0 .. n_tiles - 1 of one lattice axis whose staged region [c T - 2, c T - 2 + RW)
+// meets the box span [b, b + bw) (the test of ib_gather); one warp, result in every lane.
+__device__ __forceinline__ int tiles_meeting(int n_tiles, int T, int RW, int b, int bw, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int c0 = 0; c0 < n_tiles; c0 += 32) {
+        const int c = c0 + lane;
+        cnt += __popc(__ballot_sync(0xffffffffu, c < n_tiles && meets(c * T - 2, RW, b, bw, n)));
+    }
+    return cnt;
+}
+
+// One open node block of a ring at step tag (t + 1): increments the claim count of
+// ring_claim (tag << 16 | count) while it is below nc and returns the claimed block, or -1.
+// Each failed exchange means another CTA claimed a block, so at most nc + 1 rounds run; the
+// bound only guards that argument.
+__device__ __forceinline__ int claim_block(unsigned long long* p, unsigned long long tag, int nc, int* err)
+{
+    unsigned long long w = __ldcg(p);
+    for (int it = 0; it < 4096; ++it) {
+        if ((w >> 16) != tag || (int)(w & 0xffffu) >= nc) return -1;
+        const unsigned long long old = atomicCAS(p, w, w + 1);
+        if (old == w) return (int)(w & 0xffffu);
+        w = old;
+    }
+    atomicExch(err, 1);
+    return -1;
+}
+
+// The node step in the tail of the lattice kernel (FusedArgs::node_tail), after this tile's
+// step (App. A).  A ring's nodes are read (spreading) only by the tiles whose region meets its
+// box of step t, and the node update writes only the box of step t + 1 (RingDev::box), the
+// nodes and the other position buffer: so once the last of those tiles has written u(t) and
+// f^p(t) onto the box, the ring can advance while the remaining tiles run.  That tile opens the
+// ring's node blocks; it and the helper tiles that finish later (every eighth in launch order,
+// and any tile that met a ring) run them, one claimed block at a time.  Other tiles only test
+// their region against the boxes (cached loads): the tail costs them almost nothing.  On readout
+// steps the last tile overall sums the lattice readout.  sm: the tile's shared memory, free
+// again here.
+template <int TX, int TY>
+__device__ __noinline__ void node_tail(const FusedArgs& a, int bx, int by, bool helper, float* sm)
+{
+    using G = TileGeo<TX, TY>;
+    node::NodeSmem& S = *reinterpret_cast<node::NodeSmem*>(sm);
+    int& s_go = S.flag[0];
+    int* s_cnt = S.flag + 1;
+    unsigned& s_open = S.mask;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int nx = a.nx, ny = a.ny, nr = a.n_rings;
+    const long long t = a.t;
+    const unsigned long long tag = (unsigned long long)(t + 1);
+    const bool readout = (t % a.every) == 0;
+    bool fenced = false;
+    // this CTA's global writes of the step (state, boxes, partials) before any of its arrivals
+    if (readout) {
+        __threadfence();
+        fenced = true;
+    }
+    __syncthreads();     // the tile's last reads of shared memory are done
+    for (int r = 0; r < nr; ++r) {
+        const int4 B = ring_box(a.rings[r], t);
+        if (!meets(bx * TX - 2, G::R2W, B.x, B.z, nx) || !meets(by * TY - 2, G::R2H, B.y, B.w, ny)) continue;
+        helper = true;
+        if (!fenced) {
+            __threadfence();
+            fenced = true;
+        }
+        if (wid == 0) {
+            const int c = tiles_meeting(gridDim.x, TX, G::R2W, B.x, B.z, nx);
+            if (lane == 0) s_cnt[0] = c;
+        } else if (wid == 1) {
+            const int c = tiles_meeting(gridDim.y, TY, G::R2H, B.y, B.w, ny);
+            if (lane == 0) s_cnt[1] = c;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.box_tickets[r], 1u);
+            if (prev == (unsigned)(s_cnt[0] * s_cnt[1] - 1)) {
+                // every tile meeting the box is done with it: open the ring's node blocks
+                a.box_tickets[r] = 0u;
+                __threadfence();
+                atomicExch(&a.ring_claim[r], tag << 16);
+            }
+        }
+        __syncthreads();
+    }
+    // open node blocks of any ring, claimed one at a time
+    for (int r0 = 0; r0 < (helper ? nr : 0); r0 += 32) {
+        if (wid == 0) {
+            const int r = r0 + lane;
+            bool open = false;
+            if (r < nr) {
+                const unsigned long long w = __ldcg(a.ring_claim + r);
+                open = (w >> 16) == tag && (int)(w & 0xffffu) < a.na.ring_ctas[r];
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, open);
+            if (lane == 0) s_open = m;
+        }
+        __syncthreads();
+        unsigned m = s_open;
+        while (m) {
+            const int r = r0 + __ffs(m) - 1;
+            m &= m - 1;
+            const int c0 = a.na.ring_cta0[r], nc = a.na.ring_ctas[r];
+            for (;;) {
+                __syncthreads();
+                if (tid == 0) s_go = claim_block(a.ring_claim + r, tag, nc, &a.ctl->err_timeout);
+                __syncthreads();
+                const int c = s_go;
+                if (c < 0) break;
+                __threadfence();
+                node::node_block(a.na, c0 + c, S, false, t);
+            }
+        }
+        __syncthreads();
+    }
+    if (readout) {
+        // the last tile: lattice readout sums
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.ctl->tile_ticket, 1u);
+            s_go = prev == gridDim.x * gridDim.y - 1u;
+        }
+        __syncthreads();
+        if (s_go) {
+            __threadfence();
+            if (tid == 0) a.ctl->tile_ticket = 0u;
+            node::lattice_readout(a.na, t, S.dred);
+        }
+    }
+    // nothing in this launch reads the device step counter
+    if (bx == 0 && by == 0 && tid == 0) a.ctl->t = t + 1;
+}
+
 template <int MODE, int PREC>
 __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 {
     extern __shared__ __align__(16) float sm[];
-    tile_step<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
+    const bool tail = MODE == MODE_STEP && a.node_tail;
+    int by = blockIdx.y;
+    if (tail) {
+        // consecutive lattice launches: the state staged first was written by the previous one
+        pdl_wait();
+        by += a.tile_rot;
+        if (by >= (int)gridDim.y) by -= gridDim.y;
+    }
+    tile_step<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
+    if (tail) node_tail<TILE_X, TILE_Y>(a, blockIdx.x, by, ((blockIdx.y * gridDim.x + blockIdx.x) & 7) == 0, sm);
 }
 
 template <int MODE, int PREC>
 __global__ void __launch_bounds__(NT, 2) k_fused_pair(const FusedArgs a)
 {
     extern __shared__ __align__(16) float sm[];
-    tile_step2<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, sm);
+    const bool tail = MODE == MODE_STEP && a.node_tail;
+    int by = blockIdx.y;
+    if (tail) {
+        pdl_wait();
+        by += a.tile_rot;
+        if (by >= (int)gridDim.y) by -= gridDim.y;
+    }
+    tile_step2<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
+    if (tail) node_tail<TILE_X, TILE_Y>(a, blockIdx.x, by, ((blockIdx.y * gridDim.x + blockIdx.x) & 7) == 0, sm);
 }
 
 }  // namespace
 
 int fused_ctas(int nx, int ny) { return ((nx + TILE_X - 1) / TILE_X) * ((ny + TILE_Y - 1) / TILE_Y); }
+
+int fused_tile_rot(int nx, int ny, double y_top)
+{
+    (void)nx;
+    const int ty = (ny + TILE_Y - 1) / TILE_Y;
+    int row = (int)std::floor(y_top / TILE_Y) % ty;
+    if (row < 0) row += ty;
+    return row;
+}
 
 template <int MODE, int PREC, bool PAIR>
 static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s, bool pdl)

@@ -48,6 +48,11 @@ struct lb_handle {
     int* ring_cta0 = nullptr;
     int* ring_ctas = nullptr;
     unsigned* ring_tickets = nullptr;
+    unsigned* box_tickets = nullptr;        // per ring: tile arrivals of the node tail
+    unsigned long long* ring_claim = nullptr;   // per ring: open node blocks of the node tail
+    bool node_tail = true;                  // node step in the lattice kernel's tail (tile kernels)
+    bool after_tail = false;                // the last lattice launch ran the node tail
+    int tile_rot = 0;                       // first tile row of the tail launches
     double* node_partials = nullptr;
     long long box_floats = 0;
     bool fields_ready = false;

@@ -24,10 +24,15 @@ constexpr int LUT_N = 4096;
 struct RingDev {
     int n_nodes, node_off;        // nodes [node_off, node_off + n_nodes)
     double k_spring, eps_angle, l_eq, pull_x, pull_y;   // pull per node = pull / n_nodes
-    int box_x0, box_y0, box_w, box_h;  // work box of the current step (wrapped origin)
+    int4 box[2];                  // work box (x0, y0, w, h; wrapped origin) of the steps with even
+                                  // and odd t: step t reads box[t & 1], its node update writes the
+                                  // other one, so a lattice kernel that advances the nodes while
+                                  // its later tiles still run keeps them on the box of step t
     int cap_w, cap_h;             // capacity of the box buffers
     long long box_off;            // offset (floats) of this ring's boxes in the box buffers
 };
+
+__host__ __device__ inline int4 ring_box(const RingDev& R, long long t) { return R.box[t & 1]; }
 
 // Physical constants of the lattice kernel, FP32.
 struct Phys {
@@ -55,28 +60,7 @@ struct Ctl {
     int err_body;
     int err_cfl;
     int err_timeout;             // a bounded wait of a lattice kernel gave up
-};
-
-struct FusedArgs {
-    const void* src;             // state at t (N_PLANES planes: FP32, or FP16/BF16 in the precision form)
-    void* dst;                   // state at t + 1
-    int prec;                    // 0: FP32 state, 1: FP16 populations + BF16 sigma, dP
-    long long plane;             // nx * ny
-    int nx, ny;
-    Phys ph;
-    const float2* lut;           // LUT_N + 1 entries (a2, a4)
-    int n_rings;
-    const RingDev* rings;
-    const int2* node_cell;       // grid view of the nodes: cell, fraction, force (FP32)
-    const float2* node_frac;
-    const float2* node_force;
-    float* ubox;                 // u(t) on each ring's box (written)
-    float* fpbox;                // f^p(t) on each ring's box (written on readout steps)
-    double* partials;            // per-CTA readout sums (5 per CTA)
-    Ctl* ctl;
-    int every;                   // readout period
-    float* moments_out;          // MOMENTS mode: drho, ux, uy planes
-    float* forces_out;           // MOMENTS mode, optional: Fx, Fy planes (total lattice force)
+    unsigned int tile_ticket;    // tile arrivals of a lattice kernel with the node tail (readout steps)
 };
 
 // Node kernel geometry: NB owned nodes per CTA, NODE_THREADS >= NB + 4 threads.
@@ -112,6 +96,43 @@ struct NodeArgs {
                                  // velocities on the boxes then carry that factor)
 };
 
+struct FusedArgs {
+    const void* src;             // state at t (N_PLANES planes: FP32, or FP16/BF16 in the precision form)
+    void* dst;                   // state at t + 1
+    int prec;                    // 0: FP32 state, 1: FP16 populations + BF16 sigma, dP
+    long long plane;             // nx * ny
+    int nx, ny;
+    Phys ph;
+    const float2* lut;           // LUT_N + 1 entries (a2, a4)
+    int n_rings;
+    const RingDev* rings;
+    const int2* node_cell;       // grid view of the nodes: cell, fraction, force (FP32)
+    const float2* node_frac;
+    const float2* node_force;
+    float* ubox;                 // u(t) on each ring's box (written)
+    float* fpbox;                // f^p(t) on each ring's box (written on readout steps)
+    double* partials;            // per-CTA readout sums (5 per CTA)
+    Ctl* ctl;
+    int every;                   // readout period
+    float* moments_out;          // MOMENTS mode: drho, ux, uy planes
+    float* forces_out;           // MOMENTS mode, optional: Fx, Fy planes (total lattice force)
+    // STEP mode with node_tail = 1: the node step of the same time step runs in the kernel's
+    // tail.  Every tile whose staged region meets a ring's work box counts itself in
+    // box_tickets[ring] once its u (and f^p) box writes are out; the last of them opens the
+    // ring's node blocks (na, as the node kernel would run them) in ring_claim, and every tile
+    // that finishes later claims and runs open blocks one at a time.  Only the tiles that meet
+    // the box of step t read a ring's nodes, and the node update writes the box of step t + 1,
+    // so the update needs no second launch.  The step index comes from the host (t), and
+    // ctl->t is advanced during the launch.
+    int node_tail;
+    int tile_rot;                // node_tail: the launch order starts at this tile row, so that
+                                 // the tiles over the first ring run early
+    long long t;                 // node_tail: the step index
+    unsigned* box_tickets;       // node_tail, per ring: arrivals of the tiles meeting its box
+    unsigned long long* ring_claim;   // node_tail, per ring: (t + 1) << 16 | blocks claimed
+    NodeArgs na;                 // node step of this time step (node_tail)
+};
+
 // Launchers (return cudaError_t of the launch).
 // pair: the tile kernel with two cells per thread (paired FP32 instructions)
 cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl = false,
@@ -123,6 +144,9 @@ int sweep_ctas(int nx, int ny, int chunk);
 cudaError_t launch_sweep(const FusedArgs& a, int chunk, cudaStream_t s);
 cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s, bool pdl = false);
 int fused_ctas(int nx, int ny);
+// the tile row holding the cell row y_top (any real value; wrapped): where the launch order of
+// the tile kernel with the node tail starts
+int fused_tile_rot(int nx, int ny, double y_top);
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 

@@ -58,7 +58,7 @@ __device__ __forceinline__ float phi(float r)
 // raw fields f(t) [P][8] (channel 7: body indicator) from the state, the moment planes and the
 // ring nodes; x = BF16 normalised input [P][16] (batch slot offset applied by the caller)
 __global__ void k_pack(const float* st, const float* mom, long long NP, int nx, int ny, const RingDev* rings,
-                       int n_rings, const double2* X, LearnNorm nm, float* raw, bf16* x)
+                       int n_rings, const double2* X, LearnNorm nm, float* raw, bf16* x, long long t)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= NP) return;
@@ -74,8 +74,9 @@ __global__ void k_pack(const float* st, const float* mom, long long NP, int nx, 
     float ind = 0.f;
     for (int r = 0; r < n_rings; ++r) {
         const RingDev R = rings[r];
-        const int bx = wrap(cx - R.box_x0, nx), by = wrap(cy - R.box_y0, ny);
-        if (bx >= R.box_w || by >= R.box_h) continue;
+        const int4 B = ring_box(R, t);
+        const int bx = wrap(cx - B.x, nx), by = wrap(cy - B.y, ny);
+        if (bx >= B.z || by >= B.w) continue;
         for (int k = 0; k < R.n_nodes; ++k) {
             const double2 p = X[R.node_off + k];
             const float dx = (float)mimg((double)cx - p.x, nx), dy = (float)mimg((double)cy - p.y, ny);
@@ -140,7 +141,7 @@ __global__ void k_residual(const float* raw0, const float* y, const float* st1, 
 // velocities 7.5 (u(t+1) + u_net) on every ring's work box
 __global__ void k_unpack(const float* raw0, const float* y, float* st, const float* mom, float* unet, long long NP,
                          int nx, int ny, LearnNorm nm, const RingDev* rings, int n_rings, float* ubox, float dux,
-                         float duy)
+                         float duy, long long t)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= NP) return;
@@ -159,8 +160,9 @@ __global__ void k_unpack(const float* raw0, const float* y, float* st, const flo
     const int cx = (int)(g % nx), cy = (int)(g / nx);
     for (int r = 0; r < n_rings; ++r) {
         const RingDev R = rings[r];
-        const int bx = wrap(cx - R.box_x0, nx), by = wrap(cy - R.box_y0, ny);
-        if (bx < R.box_w && by < R.box_h) {
+        const int4 B = ring_box(R, t);
+        const int bx = wrap(cx - B.x, nx), by = wrap(cy - B.y, ny);
+        if (bx < B.z && by < B.w) {
             const long long o = R.box_off + (long long)by * R.cap_w + bx;
             const long long cap = (long long)R.cap_w * R.cap_h;
             ubox[o] = 7.5f * (u1x + f[0]);
@@ -281,7 +283,7 @@ int pack(lb_handle* h, const LearnNorm& nm, float* raw, bf16* x)
     int rc = moments(h);
     if (rc != LB_OK) return rc;
     k_pack<<<blocks(h->plane), 256, 0, h->stream>>>(static_cast<const float*>(h->state[h->cur]), h->moments, h->plane,
-                                                    h->p.nx, h->p.ny, h->rings, h->n_rings, h->X, nm, raw, x);
+                                                    h->p.nx, h->p.ny, h->rings, h->n_rings, h->X, nm, raw, x, h->t);
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ECUDA;
 }
 
@@ -431,7 +433,8 @@ int lb_learned_step(lb_learned* L, int64_t calls, int64_t* n_fallbacks)
         // uniform velocity correction so that sum u_net = sum u(t) + 16 F_pull exactly
         const float dux = (float)(-mx / (double)h->plane), duy = (float)(-my / (double)h->plane);
         k_unpack<<<blocks(h->plane), 256, 0, h->stream>>>(L->raw0, y, st, h->moments, L->unet, h->plane, h->p.nx,
-                                                          h->p.ny, L->nm, h->rings, h->n_rings, h->ubox, dux, duy);
+                                                          h->p.ny, L->nm, h->rings, h->n_rings, h->ubox, dux, duy,
+                                                          h->t);
         LCK(L, cudaGetLastError());
         LCK(L, launch_nodes(handle_node_args(h, 15), h->stream, false));
         std::swap(h->X, h->X_alt);

@@ -125,24 +125,71 @@ __device__ void cta_reduce(T (&v)[K], T* red, bool is_min)
     __syncthreads();
 }
 
+// Shared memory of one node block.  It is passed in rather than declared static: a kernel that
+// runs node blocks after other work hands over space it no longer needs, so the node code takes
+// nothing from the L1 share of that kernel's main work.
+struct NodeSmem {
+    double sx[NODE_THREADS], sy[NODE_THREADS];     // new positions relative to node j = 0
+    double dred[4 * 32];
+    float tex[NODE_THREADS], tey[NODE_THREADS];    // spring tension vector of edge (j, j+1)
+    float dpx[NODE_THREADS], dpy[NODE_THREADS];    // d cos(gamma_j) / d p, / d q
+    float dqx[NODE_THREADS], dqy[NODE_THREADS];
+    int ired[4 * 32];
+    int s_last;
+    int flag[3];                                   // free for the caller
+    unsigned mask;                                 // free for the caller
+};
+
+// Lattice readout of step t, run by the last CTA to arrive (all its threads): the sums of the
+// per-tile partials in a fixed order into columns 0-5 of the readout row.  dred: 4 * 32 doubles
+// of shared scratch.
+__device__ __forceinline__ void lattice_readout(const NodeArgs& a, long long t, double* dred)
+{
+    const int tid = threadIdx.x;
+    double* row = a.series + (long long)((t / a.every) % a.series_cap) * a.row_len;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double v4 = 0.0;
+    for (int k = tid; k < a.n_partials; k += blockDim.x) {
+        const volatile double* p = a.partials + (long long)k * 5;
+        v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3]; v4 += p[4];
+    }
+    double w1[1] = {v4};
+    cta_reduce<4, double>(v, dred, false);
+    cta_reduce<1, double>(w1, dred, false);
+    if (tid == 0) {
+        row[0] = (double)t;
+        for (int c = 0; c < 4; ++c) row[1 + c] = v[c];
+        row[5] = w1[0];
+        for (int c = 0; c < 5; ++c)
+            if (!isfinite(row[1 + c])) atomicExch(&a.ctl->err_nonfinite, 1);
+    }
+}
+
 // One CTA per block of NB nodes of one ring, with a halo of HALO nodes on each side whose
 // advance is recomputed (identically) so that the forces of the owned nodes need no other CTA.
 // One node block (cta: index into a.work) of the node step; called by k_nodes (one block per
-// CTA) and by the batched persistent kernel.
-__device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
+// CTA), by the batched persistent kernel, and (whole_step = false: without the end of the step,
+// which the caller then runs itself; t_in: the step index, else read from ctl->t) by the tail of
+// the lattice kernel.
+__device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem& S, bool whole_step = true,
+                                           long long t_in = -1)
 {
-    __shared__ double sx[NODE_THREADS], sy[NODE_THREADS];     // new positions relative to node j = 0
-    __shared__ float tex[NODE_THREADS], tey[NODE_THREADS];    // spring tension vector of edge (j, j+1)
-    __shared__ float dpx[NODE_THREADS], dpy[NODE_THREADS];    // d cos(gamma_j) / d p, / d q
-    __shared__ float dqx[NODE_THREADS], dqy[NODE_THREADS];
-    __shared__ double dred[4 * 32];
-    __shared__ int ired[4 * 32];
-    __shared__ int s_last;
+    double* sx = S.sx;
+    double* sy = S.sy;
+    float* tex = S.tex;
+    float* tey = S.tey;
+    float* dpx = S.dpx;
+    float* dpy = S.dpy;
+    float* dqx = S.dqx;
+    float* dqy = S.dqy;
+    double* dred = S.dred;
+    int* ired = S.ired;
+    int& s_last = S.s_last;
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const double Lx = nx, Ly = ny;
-    const long long t = a.ctl->t;
+    const long long t = t_in >= 0 ? t_in : a.ctl->t;
     const bool readout = a.advance && (t % a.every) == 0;
     double* row = a.series + (long long)((t / a.every) % a.series_cap) * a.row_len;
     const int2 wk = a.work[cta];                           // (ring, first owned node)
@@ -151,7 +198,8 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
         const RingDev R = a.rings[wk.x];
         const int n = R.n_nodes, off = R.node_off;
         const int k0 = wk.y, n_own = min(NB, n - k0);
-        const int bx0 = R.box_x0, by0 = R.box_y0, bw = R.box_w, bh = R.box_h;
+        const int4 B0 = ring_box(R, t);
+        const int bx0 = B0.x, by0 = B0.y, bw = B0.z, bh = B0.w;
         const int j = tid;                                   // local slot: node k0 - HALO + j
         const bool active = j < NODE_THREADS && j < n_own + 2 * HALO;   // larger CTAs: extra threads idle
         const bool own = j >= HALO && j < HALO + n_own;
@@ -271,11 +319,9 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
                 w = min(w, R.cap_w);
                 h = min(h, R.cap_h);
             }
-            RingDev& Rg = a.rings[wk.x];
-            Rg.box_x0 = wrapi1(wrapi1(bx0 + m[0] - 2, nx), nx);
-            Rg.box_y0 = wrapi1(wrapi1(by0 + m[2] - 2, ny), ny);
-            Rg.box_w = w;
-            Rg.box_h = h;
+            // the box of the step the nodes advance to
+            a.rings[wk.x].box[(t + a.advance) & 1] =
+                make_int4(wrapi1(wrapi1(bx0 + m[0] - 2, nx), nx), wrapi1(wrapi1(by0 + m[2] - 2, ny), ny), w, h);
             if (readout) {
                 double* rr = row + 6 + 4 * wk.x;
                 rr[0] = sum[0];
@@ -289,6 +335,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
         }
     }
 
+    if (!whole_step) return;
     // the last CTA overall: lattice readout sums (fixed order) and the step counter
     if (wk.x < 0) {
         cell::pdl_wait();
@@ -302,24 +349,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta)
     __syncthreads();
     if (s_last) {
         __threadfence();
-        if (readout) {
-            double v[4] = {0.0, 0.0, 0.0, 0.0};
-            double v4 = 0.0;
-            for (int k = tid; k < a.n_partials; k += blockDim.x) {
-                const volatile double* p = a.partials + (long long)k * 5;
-                v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3]; v4 += p[4];
-            }
-            double w1[1] = {v4};
-            cta_reduce<4, double>(v, dred, false);
-            cta_reduce<1, double>(w1, dred, false);
-            if (tid == 0) {
-                row[0] = (double)t;
-                for (int c = 0; c < 4; ++c) row[1 + c] = v[c];
-                row[5] = w1[0];
-                for (int c = 0; c < 5; ++c)
-                    if (!isfinite(row[1 + c])) atomicExch(&a.ctl->err_nonfinite, 1);
-            }
-        }
+        if (readout) lattice_readout(a, t, dred);
         if (tid == 0) {
             a.ctl->ticket = 0u;
             if (a.advance) a.ctl->t = t + a.advance;      // advance: steps taken (1, or a jump)

@@ -9,7 +9,11 @@ namespace {
 
 using namespace node;
 
-__global__ void __launch_bounds__(NODE_THREADS) k_nodes(const NodeArgs a) { node_block(a, blockIdx.x); }
+__global__ void __launch_bounds__(NODE_THREADS) k_nodes(const NodeArgs a)
+{
+    __shared__ NodeSmem S;
+    node_block(a, blockIdx.x, S);
+}
 
 }  // namespace
 

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
     const int n_sh_rings = min(a.n_rings, MAX_SH_RINGS);
     for (int i = tid; i < n_sh_rings; i += NT) {
         const RingDev& R = a.rings[i];
-        sBox[i] = make_int4(R.box_x0, R.box_y0, R.box_w, R.box_h);
+        sBox[i] = ring_box(R, t);
         sBoxB[i] = make_int4(R.cap_w, R.cap_h, (int)(R.box_off & 0xffffffffLL), (int)(R.box_off >> 32));
     }
     if (tid == 0) {
@@ -270,9 +270,7 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
             // immersed-boundary spreading from the nodes whose support meets these two rows
             const int gyc0 = wrapn(e0 + 2 * k + 2, ny);
             for (int ri = 0; ri < a.n_rings; ++ri) {
-                const int4 bx = ri < MAX_SH_RINGS ? sBox[ri]
-                                                  : make_int4(a.rings[ri].box_x0, a.rings[ri].box_y0,
-                                                              a.rings[ri].box_w, a.rings[ri].box_h);
+                const int4 bx = ri < MAX_SH_RINGS ? sBox[ri] : ring_box(a.rings[ri], t);
                 if (!meets(gyc0, RB, bx.y, bx.w, ny) || !meets(xs + 2, SW - 4, bx.x, bx.z, nx))
                     continue;
                 const RingDev& R = a.rings[ri];
@@ -453,7 +451,7 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
                         C2 = sBoxB[ri];
                     } else {
                         const RingDev& R = a.rings[ri];
-                        B = make_int4(R.box_x0, R.box_y0, R.box_w, R.box_h);
+                        B = ring_box(R, t);
                         C2 = make_int4(R.cap_w, R.cap_h, (int)(R.box_off & 0xffffffffLL), (int)(R.box_off >> 32));
                     }
                     int bx = gx - B.x; if (bx < 0) bx += nx;

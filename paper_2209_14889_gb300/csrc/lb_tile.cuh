@@ -191,6 +191,10 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
 // A node at cell c with fraction f sits at (c - o) + f relative to the region origin o; the
 // integer part is kept apart from the fraction so that kernel arguments stay exact in FP32.
 // Each cell sums the nodes in ring and index order, so the result does not depend on the tile.
+// the step index of a lattice launch: from the host with the node tail (which advances ctl->t
+// while tiles still run), else from the device step counter
+__device__ __forceinline__ long long step_index(const FusedArgs& a) { return a.node_tail ? a.t : a.ctl->t; }
+
 template <int TX, int TY>
 __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
 {
@@ -199,9 +203,11 @@ __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const bool small = (nx < R2W + 8) || (ny < R2H + 8);   // region may wrap onto itself
+    const long long t = step_index(a);
     for (int r = 0; r < a.n_rings; ++r) {
         const RingDev& R = a.rings[r];
-        if (!meets(x0 - 2, R2W, R.box_x0, R.box_w, nx) || !meets(y0 - 2, R2H, R.box_y0, R.box_h, ny))
+        const int4 bx = ring_box(R, t);
+        if (!meets(x0 - 2, R2W, bx.x, bx.z, nx) || !meets(y0 - 2, R2H, bx.y, bx.w, ny))
             continue;
         for (int base = 0; base < R.n_nodes; base += NT) {
             const int k = base + tid;
@@ -272,15 +278,16 @@ __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, 
 // u(t) (and f^p(t) = div sigma^p on readout steps) of the owned cell (gx, gy) on the work box of
 // every ring containing it; j3: the cell's index in the halo-3 sigma planes (width R3W).
 template <int R3, int R3W>
-__device__ __forceinline__ void box_write(const FusedArgs& a, int gx, int gy, float ux, float uy, bool readout,
-                                          const float* sS, int j3)
+__device__ __forceinline__ void box_write(const FusedArgs& a, long long t, int gx, int gy, float ux, float uy,
+                                          bool readout, const float* sS, int j3)
 {
     const int nx = a.nx, ny = a.ny;
     for (int rr = 0; rr < a.n_rings; ++rr) {
         const RingDev& R = a.rings[rr];
-        int bx = gx - R.box_x0; if (bx < 0) bx += nx;
-        int by = gy - R.box_y0; if (by < 0) by += ny;
-        if (bx < R.box_w && by < R.box_h) {
+        const int4 B = ring_box(R, t);
+        int bx = gx - B.x; if (bx < 0) bx += nx;
+        int by = gy - B.y; if (by < 0) by += ny;
+        if (bx < B.z && by < B.w) {
             const long long o = R.box_off + (long long)by * R.cap_w + bx;
             const long long cap = (long long)R.cap_w * R.cap_h;
             a.ubox[o] = ux;
@@ -386,7 +393,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     // ---- C: total force and moments on the halo-2 region; collision of the owned cells ------
     // Owned cells collide here, with their populations still in registers, and push to
     // x + c_n (Eq. LB, Eq. BGK, Guo source; exactly conservative FP32 increments).
-    const long long t = a.ctl->t;
+    const long long t = step_index(a);
     const bool readout = (t % a.every) == 0;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     void* dst = a.dst;
@@ -512,7 +519,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
             st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
         }
-        box_write<R3, R3W>(a, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
+        box_write<R3, R3W>(a, t, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
     }
     if (readout) readout_reduce(a, acc, m.sRed, tile_index);
 }
@@ -593,7 +600,7 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
     // ---- C (pairs): total force and moments on the halo-2 region; collision of the owned
     // pairs (the owned columns 2 .. TX+1 of the halo-2 frame start at an even column, so a pair
     // is owned or not as a whole) -------------------------------------------------------------
-    const long long t = a.ctl->t;
+    const long long t = step_index(a);
     const bool readout = (t % a.every) == 0;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     void* dst = a.dst;
@@ -794,8 +801,8 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
             }
         }
         const int j3 = (ly + 3) * R3W + lx + 3;
-        box_write<R3, R3W>(a, gx, gy, ux.x, uy.x, readout, m.sS, j3);
-        if (has1) box_write<R3, R3W>(a, gx + 1, gy, ux.y, uy.y, readout, m.sS, j3 + 1);
+        box_write<R3, R3W>(a, t, gx, gy, ux.x, uy.x, readout, m.sS, j3);
+        if (has1) box_write<R3, R3W>(a, t, gx + 1, gy, ux.y, uy.y, readout, m.sS, j3 + 1);
     }
     if (readout) readout_reduce(a, acc, m.sRed, tile_index);
 }

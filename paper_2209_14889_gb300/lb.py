@@ -91,6 +91,7 @@ def lib():
                                               ctypes.POINTER(i64)]),
             "lb_launches_per_step": (i32, [_H]),
             "lb_set_kernel": (ctypes.c_int, [_H, i32]),
+            "lb_set_node_tail": (ctypes.c_int, [_H, i32]),
             "lb_stiffness_table": (i32, [ctypes.c_double, vp, i32]),
             "lb_bytes_per_cell": (ctypes.c_double, [_H]),
             "lb_last_error": (ctypes.c_char_p, [_H]),
@@ -289,6 +290,11 @@ class Solver:
     def set_kernel(self, kernel: int):
         """LB_KERNEL_AUTO (the fastest measured), LB_KERNEL_TILE, LB_KERNEL_PAIR or LB_KERNEL_SWEEP."""
         _check(self.h, lib().lb_set_kernel(self.h, int(kernel)))
+
+    def set_node_tail(self, enable: bool):
+        """Node step in the tail of the tile kernels (True, default: one launch per step) or in a
+        separate node kernel (False); the two compute the same values bit for bit."""
+        _check(self.h, lib().lb_set_node_tail(self.h, 1 if enable else 0))
 
     def timing(self, enable: bool):
         _check(self.h, lib().lb_timing(self.h, 1 if enable else 0))

@@ -326,3 +326,87 @@ def test_pair_and_single_cell_tile_kernels_vs_oracle(nx, ny, centre):
         check_fields(got, ref)
         check_nodes(got, ref, w)
         check_series(got, ref, 1)
+
+
+# ------------------------------------------------------------------------------------------
+# Node step in the tail of the tile kernels against the separate node kernel
+# ------------------------------------------------------------------------------------------
+
+def _tail_cases():
+    return {
+        "ragged_seam": W.small(98, 34, n_nodes=20, radius=4.0, centre=(96.4, 1.5), steps=0),
+        "wraps_in_tile": W.small(40, 26, n_nodes=12, radius=2.4, steps=0),
+        "four_rings": W.cfg3(seed=5, side=256, n_rings=4),
+        "no_ring": W.small(40, 26, n_nodes=0),
+        "substeps": W.small(96, 80, n_nodes=40, radius=8.0, Dp=0.6, diffusion_substeps=3),
+    }
+
+
+@pytest.mark.parametrize("case", ["ragged_seam", "wraps_in_tile", "four_rings", "no_ring", "substeps"])
+@pytest.mark.parametrize("kernel", ["tile", "pair"])
+def test_node_tail_matches_separate_node_kernel_bitwise(case, kernel):
+    """The node step run in the tile kernel's tail (one launch per step) computes exactly what
+    the separate node kernel computes: fields, positions and the readout series bit for bit,
+    over steps that cross readouts and both step parities of the ring boxes."""
+    lb = _gpu()
+    w = _tail_cases()[case]
+    k = lb.LB_KERNEL_TILE if kernel == "tile" else lb.LB_KERNEL_PAIR
+    out = []
+    for tail in (True, False):
+        s = lb.Solver.from_workload(w)
+        s.set_kernel(k)
+        s.set_node_tail(tail)
+        dsub = w.get("diffusion_substeps", 0)
+        assert s.launches_per_step == (1 if tail else 2) + (dsub + (dsub & 1) if dsub else 0)
+        s.step(23)
+        s.sync()
+        assert s.t == 23
+        out.append(dict(fields=s.fields(), series=s.series(), X=s.nodes()))
+        s.close()
+    a, b = out
+    for f in a["fields"]:
+        assert np.array_equal(a["fields"][f], b["fields"][f]), f
+    assert np.array_equal(a["X"], b["X"])
+    assert np.array_equal(a["series"], b["series"])
+
+
+def test_node_tail_precision_form_switching_and_restart():
+    # the FP16/BF16 state with the tail, a run that changes mode between steps, and a restart
+    # from lb_init_fields at an odd step, against the separate kernel throughout
+    lb = _gpu()
+    w = W.cfg3(seed=7, side=256, n_rings=3)
+    runs = []
+    for plan in ([(True, 12), (False, 5), (True, 8)], [(False, 25)]):
+        s = lb.Solver.from_workload(w, precision=lb.LB_FP16_BF16)
+        for tail, n in plan:
+            s.set_node_tail(tail)
+            s.step(n)
+        s.sync()
+        runs.append((s.readout("pop5", device=False), s.readout("Py", device=False), s.series(), s.nodes()))
+        s.close()
+    for x, y in zip(*runs):
+        assert np.array_equal(x, y)
+    restarted = []
+    for tail in (True, False):
+        s = lb.Solver.from_workload(w)
+        s.set_node_tail(tail)
+        s.step(7)
+        s.init_fields(w["noise"])                   # restart with the rings where they are
+        s.step(14)
+        s.sync()
+        assert s.t == 14
+        restarted.append((s.fields(), s.nodes()))
+        s.close()
+    for f in restarted[0][0]:
+        assert np.array_equal(restarted[0][0][f], restarted[1][0][f]), f
+    assert np.array_equal(restarted[0][1], restarted[1][1])
+
+
+def test_node_tail_rejects_bad_values():
+    lb = _gpu()
+    s = lb.Solver.from_workload(W.small(32, 32, n_nodes=0))
+    assert lb.lib().lb_set_node_tail(s.h, 2) == lb.LB_EINVAL
+    assert lb.lib().lb_set_node_tail(s.h, -1) == lb.LB_EINVAL
+    s.set_node_tail(False)
+    assert s.launches_per_step == 2
+    s.close()
