@@ -49,7 +49,7 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-KERNEL_SOURCES = ["lb_fused.cu", "lb_tile.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h"]
+KERNEL_SOURCES = ["lb_fused.cu", "lb_tile.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h", "lb_node.cuh"]
 
 
 def kernel_source_sha1():
