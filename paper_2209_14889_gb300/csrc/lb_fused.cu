@@ -44,55 +44,93 @@ __device__ __forceinline__ int claim_block(unsigned long long* p, unsigned long 
     return -1;
 }
 
+// Node blocks of the rings in `open` (bits; ring r0 + bit), claimed one at a time, then (last)
+// the lattice readout sums: the rare parts of the node tail, kept out of line so that the tiles
+// that have none of it pay nothing for them.  The node blocks take the tile's shared memory,
+// whose staged fields are dead once every thread has passed the barrier at the start.
+__device__ __noinline__ void tail_work(const FusedArgs& a, unsigned open, int r0, bool last, float* sm)
+{
+    node::NodeSmem& S = *reinterpret_cast<node::NodeSmem*>(sm);
+    const int tid = threadIdx.x;
+    const long long t = a.t;
+    const unsigned long long tag = (unsigned long long)(t + 1);
+    __syncthreads();
+    while (open) {
+        const int r = r0 + __ffs(open) - 1;
+        open &= open - 1;
+        const int c0 = a.na.ring_cta0[r], nc = a.na.ring_ctas[r];
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) S.flag[0] = claim_block(a.ring_claim + r, tag, nc, &a.ctl->err_timeout);
+            __syncthreads();
+            const int c = S.flag[0];
+            if (c < 0) break;
+            __threadfence();
+            node::node_block(a.na, c0 + c, S, false, t);
+        }
+    }
+    if (last) {
+        __syncthreads();
+        __threadfence();
+        if (tid == 0) a.ctl->tile_ticket = 0u;
+        node::lattice_readout(a.na, t, S.dred);
+    }
+}
+
+// tiles that look for open node blocks in their tail: one in 32 in launch order, and all of the
+// last thirty-second (rings whose tiles run late still find helpers)
+__device__ __forceinline__ bool helper_tile()
+{
+    const int order = blockIdx.y * gridDim.x + blockIdx.x, total = gridDim.x * gridDim.y;
+    return (order & 31) == 0 || order >= total - total / 32;
+}
+
 // The node step in the tail of the lattice kernel (FusedArgs::node_tail), after this tile's
 // step (App. A).  A ring's nodes are read (spreading) only by the tiles whose region meets its
 // box of step t, and the node update writes only the box of step t + 1 (RingDev::box), the
 // nodes and the other position buffer: so once the last of those tiles has written u(t) and
 // f^p(t) onto the box, the ring can advance while the remaining tiles run.  That tile opens the
-// ring's node blocks; it and the helper tiles that finish later (every eighth in launch order,
-// and any tile that met a ring) run them, one claimed block at a time.  Other tiles only test
-// their region against the boxes (cached loads): the tail costs them almost nothing.  On readout
-// steps the last tile overall sums the lattice readout.  sm: the tile's shared memory, free
-// again here.
+// ring's node blocks; it and the helper tiles that finish later (helper_tile, and any tile that
+// met a ring) run them, one claimed block at a time.  On readout steps every tile counts itself
+// and the last one sums the lattice readout.  Flags live in the scan scratch of ib_gather (free
+// by now; the ring masks after it stay intact).  Out of line: node_tail below calls it only for
+// the tiles that have something to do.
 template <int TX, int TY>
-__device__ __noinline__ void node_tail(const FusedArgs& a, int bx, int by, bool helper, float* sm)
+__device__ __noinline__ void node_tail_work(const FusedArgs& a, float* sm)
 {
     using G = TileGeo<TX, TY>;
-    node::NodeSmem& S = *reinterpret_cast<node::NodeSmem*>(sm);
-    int& s_go = S.flag[0];
-    int* s_cnt = S.flag + 1;
-    unsigned& s_open = S.mask;
+    static_assert(sizeof(node::NodeSmem) <= sizeof(float) * G::OFF_SC, "node blocks overlay the staged fields only");
+    int* sT = reinterpret_cast<int*>(sm + G::OFF_SC);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int nx = a.nx, ny = a.ny, nr = a.n_rings;
+    const int nr = a.n_rings;
     const long long t = a.t;
-    const unsigned long long tag = (unsigned long long)(t + 1);
+    const int bx = blockIdx.x;
+    int by = blockIdx.y + a.tile_rot;
+    if (by >= (int)gridDim.y) by -= gridDim.y;
+    bool helper = helper_tile();
     const bool readout = (t % a.every) == 0;
-    bool fenced = false;
-    // this CTA's global writes of the step (state, boxes, partials) before any of its arrivals
-    if (readout) {
-        __threadfence();
-        fenced = true;
-    }
-    __syncthreads();     // the tile's last reads of shared memory are done
-    for (int r = 0; r < nr; ++r) {
+    const unsigned meet = nr > 32 ? 0xffffffffu : (unsigned)sT[NT / 32 + 2];
+    const unsigned long long tag = (unsigned long long)(t + 1);
+    // the CTA's global writes of the step (state, boxes, partials) before any of its arrivals
+    __threadfence();
+    for (int r = 0; r < nr && meet != 0u; ++r) {
+        if (nr <= 32 && !((meet >> r) & 1u)) continue;
         const int4 B = ring_box(a.rings[r], t);
-        if (!meets(bx * TX - 2, G::R2W, B.x, B.z, nx) || !meets(by * TY - 2, G::R2H, B.y, B.w, ny)) continue;
+        if (nr > 32 &&
+            (!meets(bx * TX - 2, G::R2W, B.x, B.z, a.nx) || !meets(by * TY - 2, G::R2H, B.y, B.w, a.ny)))
+            continue;
         helper = true;
-        if (!fenced) {
-            __threadfence();
-            fenced = true;
-        }
         if (wid == 0) {
-            const int c = tiles_meeting(gridDim.x, TX, G::R2W, B.x, B.z, nx);
-            if (lane == 0) s_cnt[0] = c;
+            const int c = tiles_meeting(gridDim.x, TX, G::R2W, B.x, B.z, a.nx);
+            if (lane == 0) sT[0] = c;
         } else if (wid == 1) {
-            const int c = tiles_meeting(gridDim.y, TY, G::R2H, B.y, B.w, ny);
-            if (lane == 0) s_cnt[1] = c;
+            const int c = tiles_meeting(gridDim.y, TY, G::R2H, B.y, B.w, a.ny);
+            if (lane == 0) sT[1] = c;
         }
         __syncthreads();
         if (tid == 0) {
             const unsigned prev = atomicAdd(&a.box_tickets[r], 1u);
-            if (prev == (unsigned)(s_cnt[0] * s_cnt[1] - 1)) {
+            if (prev == (unsigned)(sT[0] * sT[1] - 1)) {
                 // every tile meeting the box is done with it: open the ring's node blocks
                 a.box_tickets[r] = 0u;
                 __threadfence();
@@ -101,7 +139,7 @@ __device__ __noinline__ void node_tail(const FusedArgs& a, int bx, int by, bool 
         }
         __syncthreads();
     }
-    // open node blocks of any ring, claimed one at a time
+    // open node blocks of any ring (helpers), 32 rings at a time
     for (int r0 = 0; r0 < (helper ? nr : 0); r0 += 32) {
         if (wid == 0) {
             const int r = r0 + lane;
@@ -111,42 +149,33 @@ __device__ __noinline__ void node_tail(const FusedArgs& a, int bx, int by, bool 
                 open = (w >> 16) == tag && (int)(w & 0xffffu) < a.na.ring_ctas[r];
             }
             const unsigned m = __ballot_sync(0xffffffffu, open);
-            if (lane == 0) s_open = m;
+            if (lane == 0) sT[2] = (int)m;
         }
         __syncthreads();
-        unsigned m = s_open;
-        while (m) {
-            const int r = r0 + __ffs(m) - 1;
-            m &= m - 1;
-            const int c0 = a.na.ring_cta0[r], nc = a.na.ring_ctas[r];
-            for (;;) {
-                __syncthreads();
-                if (tid == 0) s_go = claim_block(a.ring_claim + r, tag, nc, &a.ctl->err_timeout);
-                __syncthreads();
-                const int c = s_go;
-                if (c < 0) break;
-                __threadfence();
-                node::node_block(a.na, c0 + c, S, false, t);
-            }
-        }
+        const unsigned m = (unsigned)sT[2];
+        if (m) tail_work(a, m, r0, false, sm);
         __syncthreads();
     }
     if (readout) {
-        // the last tile: lattice readout sums
+        // every tile counts itself; the last one sums the lattice readout
         __syncthreads();
-        if (tid == 0) {
-            const unsigned prev = atomicAdd(&a.ctl->tile_ticket, 1u);
-            s_go = prev == gridDim.x * gridDim.y - 1u;
-        }
+        if (tid == 0) sT[3] = atomicAdd(&a.ctl->tile_ticket, 1u) == gridDim.x * gridDim.y - 1u;
         __syncthreads();
-        if (s_go) {
-            __threadfence();
-            if (tid == 0) a.ctl->tile_ticket = 0u;
-            node::lattice_readout(a.na, t, S.dred);
-        }
+        if (sT[3]) tail_work(a, 0u, 0, true, sm);
     }
-    // nothing in this launch reads the device step counter
-    if (bx == 0 && by == 0 && tid == 0) a.ctl->t = t + 1;
+}
+
+// The node tail of one tile: the step counter (one tile), then node_tail_work where this tile
+// meets a ring's box, is a helper, or the step is a readout step; nothing else for most tiles.
+template <int TX, int TY>
+__device__ __forceinline__ void node_tail(const FusedArgs& a, float* sm)
+{
+    using G = TileGeo<TX, TY>;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) a.ctl->t = a.t + 1;   // nothing here reads it
+    const int* sT = reinterpret_cast<const int*>(sm + G::OFF_SC);
+    // the rings whose box meets this tile's staged region (tested in ib_gather for up to 32 rings)
+    if (a.n_rings > 32 || sT[NT / 32 + 2] != 0 || helper_tile() || (a.t % a.every) == 0)
+        node_tail_work<TX, TY>(a, sm);
 }
 
 template <int MODE, int PREC>
@@ -162,7 +191,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         if (by >= (int)gridDim.y) by -= gridDim.y;
     }
     tile_step<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
-    if (tail) node_tail<TILE_X, TILE_Y>(a, blockIdx.x, by, ((blockIdx.y * gridDim.x + blockIdx.x) & 7) == 0, sm);
+    if (tail) node_tail<TILE_X, TILE_Y>(a, sm);
 }
 
 template <int MODE, int PREC>
@@ -177,7 +206,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused_pair(const FusedArgs a)
         if (by >= (int)gridDim.y) by -= gridDim.y;
     }
     tile_step2<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
-    if (tail) node_tail<TILE_X, TILE_Y>(a, blockIdx.x, by, ((blockIdx.y * gridDim.x + blockIdx.x) & 7) == 0, sm);
+    if (tail) node_tail<TILE_X, TILE_Y>(a, sm);
 }
 
 }  // namespace

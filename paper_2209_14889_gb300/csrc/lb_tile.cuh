@@ -55,8 +55,9 @@ struct TileGeo {
     static constexpr int OFF_NF = OFF_N + 4 * NT;                 // node forces [NT] float2
     static constexpr int OFF_XI = OFF_NF + 2 * NT;                // wrapped x index [R4W] (int)
     static constexpr int OFF_YI = OFF_XI + R4W;                   // wrapped y index [R4H] (int)
-    static constexpr int OFF_SC = OFF_YI + R4H;                   // scan scratch [NT/32 + 1] (int)
-    static constexpr int OFF_RED = al4(OFF_SC + NT / 32 + 1);     // readout [5][NT/32] (double)
+    static constexpr int OFF_SC = OFF_YI + R4H;                   // scan scratch [NT/32 + 1] (int),
+                                                                  // then the tile's ring masks [2]
+    static constexpr int OFF_RED = al4(OFF_SC + NT / 32 + 3);     // readout [5][NT/32] (double)
     static constexpr int SMEM_FLOATS = OFF_RED + 2 * 5 * (NT / 32);
     static constexpr size_t SMEM_BYTES = sizeof(float) * SMEM_FLOATS;
     static_assert(OFF_N % 4 == 0 && OFF_NF % 2 == 0 && OFF_RED % 2 == 0, "shared-memory alignment");
@@ -204,11 +205,28 @@ __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, 
     const int nx = a.nx, ny = a.ny;
     const bool small = (nx < R2W + 8) || (ny < R2H + 8);   // region may wrap onto itself
     const long long t = step_index(a);
-    for (int r = 0; r < a.n_rings; ++r) {
+    const int nr = a.n_rings;
+    // with up to 32 rings every warp tests one ring per lane: the rings whose box meets the
+    // staged halo-2 region (meet) and the owned cells (own); beyond 32 rings each is tested below
+    unsigned meet = 0xffffffffu, own = 0xffffffffu;
+    if (nr <= 32) {
+        const int lane = tid & 31;
+        bool m2 = false, mo = false;
+        if (lane < nr) {
+            const int4 bx = ring_box(a.rings[lane], t);
+            m2 = meets(x0 - 2, R2W, bx.x, bx.z, nx) && meets(y0 - 2, R2H, bx.y, bx.w, ny);
+            mo = m2 && meets(x0, TX, bx.x, bx.z, nx) && meets(y0, TY, bx.y, bx.w, ny);
+        }
+        meet = __ballot_sync(0xffffffffu, m2);
+        own = __ballot_sync(0xffffffffu, mo);
+    }
+    for (int r = 0; r < nr; ++r) {
+        if (nr <= 32 && !((meet >> r) & 1u)) continue;
         const RingDev& R = a.rings[r];
-        const int4 bx = ring_box(R, t);
-        if (!meets(x0 - 2, R2W, bx.x, bx.z, nx) || !meets(y0 - 2, R2H, bx.y, bx.w, ny))
-            continue;
+        if (nr > 32) {
+            const int4 bx = ring_box(R, t);
+            if (!meets(x0 - 2, R2W, bx.x, bx.z, nx) || !meets(y0 - 2, R2H, bx.y, bx.w, ny)) continue;
+        }
         for (int base = 0; base < R.n_nodes; base += NT) {
             const int k = base + tid;
             bool keep = false;
@@ -272,17 +290,21 @@ __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, 
             __syncthreads();
         }
     }
+    if (tid == 0) {
+        m.sScan[NT / 32 + 1] = (int)own;    // for the box writes of phase E
+        m.sScan[NT / 32 + 2] = (int)meet;   // for the node tail
+    }
     __syncthreads();
 }
 
 // u(t) (and f^p(t) = div sigma^p on readout steps) of the owned cell (gx, gy) on the work box of
-// every ring containing it; j3: the cell's index in the halo-3 sigma planes (width R3W).
+// ring rr if it contains the cell; j3: the cell's index in the halo-3 sigma planes (width R3W).
 template <int R3, int R3W>
-__device__ __forceinline__ void box_write(const FusedArgs& a, long long t, int gx, int gy, float ux, float uy,
-                                          bool readout, const float* sS, int j3)
+__device__ __forceinline__ void box_write_ring(const FusedArgs& a, int rr, long long t, int gx, int gy, float ux,
+                                               float uy, bool readout, const float* sS, int j3)
 {
     const int nx = a.nx, ny = a.ny;
-    for (int rr = 0; rr < a.n_rings; ++rr) {
+    {
         const RingDev& R = a.rings[rr];
         const int4 B = ring_box(R, t);
         int bx = gx - B.x; if (bx < 0) bx += nx;
@@ -299,6 +321,21 @@ __device__ __forceinline__ void box_write(const FusedArgs& a, long long t, int g
             }
         }
     }
+}
+
+// u(t) (and f^p(t) on readout steps) of the owned cell (gx, gy) on the box of every ring that
+// contains it; mask: the rings whose box meets the tile's owned cells (with up to 32 rings; all
+// rings are tested when there are more).
+template <int R3, int R3W>
+__device__ __forceinline__ void box_write(const FusedArgs& a, unsigned mask, long long t, int gx, int gy, float ux,
+                                          float uy, bool readout, const float* sS, int j3)
+{
+    if (a.n_rings > 32) {
+        for (int rr = 0; rr < a.n_rings; ++rr) box_write_ring<R3, R3W>(a, rr, t, gx, gy, ux, uy, readout, sS, j3);
+        return;
+    }
+    for (; mask; mask &= mask - 1)
+        box_write_ring<R3, R3W>(a, __ffs(mask) - 1, t, gx, gy, ux, uy, readout, sS, j3);
 }
 
 // fixed-order block reduction of the FP64 readout sums of the tile into its partial slot
@@ -491,6 +528,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     __syncthreads();
 
     // ---- E: corrector, field stores, box writes, readout sums -------------------------------
+    const unsigned bmask = (unsigned)m.sScan[NT / 32 + 1];
     for (int i = tid; i < R0; i += NT) {
         const int ly = i / TX, lx = i - ly * TX;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -519,7 +557,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
             st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
         }
-        box_write<R3, R3W>(a, t, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
+        box_write<R3, R3W>(a, bmask, t, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
     }
     if (readout) readout_reduce(a, acc, m.sRed, tile_index);
 }
@@ -744,6 +782,7 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
     __syncthreads();
 
     // ---- E (pairs): corrector, field stores, box writes, readout sums ---------------------
+    const unsigned bmask = (unsigned)m.sScan[NT / 32 + 1];
     for (int q = tid; q < R0 / 2; q += NT) {
         const int ly = q / (TX / 2), lx = 2 * (q - ly * (TX / 2));
         const int gx = x0 + lx, gy = y0 + ly;
@@ -801,8 +840,8 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
             }
         }
         const int j3 = (ly + 3) * R3W + lx + 3;
-        box_write<R3, R3W>(a, t, gx, gy, ux.x, uy.x, readout, m.sS, j3);
-        if (has1) box_write<R3, R3W>(a, t, gx + 1, gy, ux.y, uy.y, readout, m.sS, j3 + 1);
+        box_write<R3, R3W>(a, bmask, t, gx, gy, ux.x, uy.x, readout, m.sS, j3);
+        if (has1) box_write<R3, R3W>(a, bmask, t, gx + 1, gy, ux.y, uy.y, readout, m.sS, j3 + 1);
     }
     if (readout) readout_reduce(a, acc, m.sRed, tile_index);
 }

@@ -339,10 +339,12 @@ def _tail_cases():
         "four_rings": W.cfg3(seed=5, side=256, n_rings=4),
         "no_ring": W.small(40, 26, n_nodes=0),
         "substeps": W.small(96, 80, n_nodes=40, radius=8.0, Dp=0.6, diffusion_substeps=3),
+        "forty_rings": W.cfg3(seed=9, side=512, n_rings=40),
     }
 
 
-@pytest.mark.parametrize("case", ["ragged_seam", "wraps_in_tile", "four_rings", "no_ring", "substeps"])
+@pytest.mark.parametrize("case", ["ragged_seam", "wraps_in_tile", "four_rings", "no_ring", "substeps",
+                                  "forty_rings"])
 @pytest.mark.parametrize("kernel", ["tile", "pair"])
 def test_node_tail_matches_separate_node_kernel_bitwise(case, kernel):
     """The node step run in the tile kernel's tail (one launch per step) computes exactly what
@@ -410,3 +412,12 @@ def test_node_tail_rejects_bad_values():
     s.set_node_tail(False)
     assert s.launches_per_step == 2
     s.close()
+
+
+def test_more_rings_than_a_tile_mask_holds_vs_oracle():
+    # 36 rings: the tiles test every ring one by one instead of through their 32-bit ring masks
+    w = W.cfg3(seed=11, side=256, n_rings=36)
+    got, ref = run_both(w, 30)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 36)
