@@ -379,6 +379,34 @@ __device__ __forceinline__ void moments_out(const FusedArgs& a, const TileMem<TX
     }
 }
 
+// Cell k of a region made of the TX x TY owned cells and a frame BD cells wide around them, in
+// the order in which the tile step visits it: first the owned cells row by row (a warp covers
+// one row of 32, so its stencil reads fall in distinct banks, and the owned cells, which carry
+// most of the work, spread evenly over the threads), then the frame: BD rows on top, BD rows at
+// the bottom, then the BD + BD side cells of each owned row.  (lx, ly): coordinates in the
+// region, whose width is TX + 2 BD.
+template <int TX, int TY, int BD>
+__device__ __forceinline__ void region_cell(int k, int& lx, int& ly)
+{
+    constexpr int W = TX + 2 * BD, H = TY + 2 * BD;
+    if (k < TX * TY) {
+        ly = BD + k / TX;
+        lx = BD + k % TX;
+        return;
+    }
+    int h = k - TX * TY;
+    if (h < 2 * BD * W) {
+        const int r = h / W;
+        lx = h - r * W;
+        ly = r < BD ? r : H - 2 * BD + r;
+        return;
+    }
+    h -= 2 * BD * W;
+    const int r = h / (2 * BD), c = h - r * (2 * BD);
+    ly = BD + r;
+    lx = c < BD ? c : TX + c;
+}
+
 // D2Q9 (Sec. II A): c_n, n = 0..8
 __device__ constexpr int C_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int C_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -407,8 +435,10 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     stage<PREC, COH>(a, m, x0, y0);
 
     // ---- B: molecular field and Ericksen stress on the halo-3 region ------------------------
-    for (int i = tid; i < R3; i += NT) {
-        const int ly = i / R3W, lx = i - ly * R3W;
+    for (int k = tid; k < R3; k += NT) {
+        int lx, ly;
+        region_cell<TX, TY, 3>(k, lx, ly);
+        const int i = ly * R3W + lx;
         const St px = st_at(m.sP, R4W, lx + 1, ly + 1);         // dP stencils
         const St py = st_at(m.sP + R4, R4W, lx + 1, ly + 1);
         float hx, hy, E[4];
@@ -434,8 +464,10 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const bool readout = (t % a.every) == 0;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     void* dst = a.dst;
-    for (int i = tid; i < R2; i += NT) {
-        const int ly = i / R2W, lx = i - ly * R2W;
+    for (int k = tid; k < R2; k += NT) {
+        int lx, ly;
+        region_cell<TX, TY, 2>(k, lx, ly);
+        const int i = ly * R2W + lx;
         float Fx, Fy;
         div_sigma(st_at(m.sS, R3W, lx + 1, ly + 1), st_at(m.sS + R3, R3W, lx + 1, ly + 1),
                   st_at(m.sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
@@ -462,7 +494,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             m.sFib[i] = Fx;              // the total force replaces f_IB (read above, this cell only)
             m.sFib[R2 + i] = Fy;
         }
-        const bool own = lx >= 2 && lx < TX + 2 && ly >= 2 && ly < TY + 2 && x0 + lx - 2 < nx && y0 + ly - 2 < ny;
+        const bool own = k < R0 && x0 + lx - 2 < nx && y0 + ly - 2 < ny;
         if (MODE == MODE_STEP && own) {
             float D[9];
             collide(ph, d, drho, ux, uy, Fx, Fy, D);
@@ -499,8 +531,10 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     }
 
     // ---- D: predictor on the halo-1 region --------------------------------------------------
-    for (int i = tid; i < R1; i += NT) {
-        const int ly = i / R1W, lx = i - ly * R1W;
+    for (int k = tid; k < R1; k += NT) {
+        int lx, ly;
+        region_cell<TX, TY, 1>(k, lx, ly);
+        const int i = ly * R1W + lx;
         const int j2 = (ly + 1) * R2W + lx + 1;
         float pxx, pyy, pxy, om;
         vgrad(m.sM + R2, m.sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
@@ -519,10 +553,9 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         m.sY[2 * R1 + i] = s2.c + r[2];
         m.sY[3 * R1 + i] = p0.c + r[3];
         m.sY[4 * R1 + i] = p1.c + r[4];
-        if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) {
-            const int j0 = (ly - 1) * TX + (lx - 1);
+        if (k < R0) {       // an owned cell: k = (ly - 1) TX + (lx - 1)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) m.sR[c * R0 + j0] = r[c];
+            for (int c = 0; c < 5; ++c) m.sR[c * R0 + k] = r[c];
         }
     }
     __syncthreads();
