@@ -10,7 +10,9 @@
 //                                                                           K = pixels)
 // with off_t = (t / 3 - 1, t % 3 - 1).  Tiles are staged in shared memory (rows padded to 48 or
 // 144 bytes, so the 8 rows of each ldmatrix fall in distinct banks) and multiplied with
-// mma.sync m16n8k16 BF16 -> FP32.  Weight gradients are reduced over pixel tiles in a fixed
+// mma.sync m16n8k16 BF16 -> FP32; by default the forward and the data gradient run instead on
+// tcgen05 (k_conv3x3_tc: pixels as M, output channels as N, accumulators in tensor memory).
+// Weight gradients are reduced over pixel tiles in a fixed
 // order (per-CTA partials, then a sum over CTAs), so training is bitwise reproducible.
 // Joins: 2x2 average pooling, nearest 2x upsampling written into a channel slice of the
 // concatenation buffer (the skip is written there by its producing convolution), LeakyReLU
@@ -176,60 +178,85 @@ __global__ void __launch_bounds__(128) k_conv3x3(const ConvArgs a)
     }
 }
 
-// ------------------------------------------------------------------ convolution forward, tcgen05
-//
-// The same convolution on the 5th-generation tensor cores: per 16-channel chunk of the input,
-// the CTA stages the 10 x 18-pixel input tile and the chunk's weights of all 9 taps in shared
-// memory, one thread issues 9 taps x 8 output rows of tcgen05.mma (M = 128 output channels,
-// N = 16 pixels of one output row, K = 16 channels, BF16 -> FP32) into 8 accumulators of 16
-// columns each in tensor memory, and commits them to an mbarrier; after the last chunk the
-// four warps read their 32 lanes (output channels) back with tcgen05.ld for the epilogue.
-// Operands are in the canonical K-major layout without swizzle: core matrices of 8 rows x 16
-// bytes (8 BF16 of K), rows 16 bytes apart.  Input tile: [2 k-halves][180 pixels][8]; a pixel
-// row of the output is 16 consecutive tile pixels, so its two 8-pixel core matrices are 128
-// bytes apart (stride dimension) and the k-halves 180 x 16 bytes apart (leading dimension).
-// Weights: [9 taps][2 k-halves][128 channels][8]; channel groups of 8 are 128 bytes apart,
-// k-halves 2048 bytes.
+// ------------------------------------------------------------------ tcgen05 descriptors
 
-constexpr int TC_M = 128, TC_N = 16;
-constexpr int TC_NPIX = CT_IH * CT_IW;                              // 180
-constexpr int TC_SX = 2 * TC_NPIX * 8;                              // BF16 elements
-constexpr int TC_SW = 9 * 2 * TC_M * 8;
-// shared memory: weights, input tile, and slack after them so that every descriptor of this
-// kernel, read with its two strides exchanged, still stays inside the allocation
-constexpr int TC_SMEM_BYTES = (TC_SW + TC_SX) * 2 + 40 * 1024 + 64;
-
+// shared-memory matrix descriptor: start address, leading (K-direction core-matrix) and stride
+// (8-row group) byte offsets, descriptor version 1, no swizzle
 __device__ __forceinline__ uint64_t tc_desc(unsigned saddr, unsigned lbo, unsigned sbo)
 {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);   // version 1, no swizzle
 }
 
-// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N, M
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                              ((uint32_t)(TC_M >> 4) << 24);
+// ------------------------------------------------------------------ convolution forward, tcgen05
+//
+// The convolution on the 5th-generation tensor cores, with the output pixels as the MMA's M
+// dimension and the output channels as N, so that layers with 32 or 64 output channels fill the
+// tensor core.  A CTA computes 4 output rows x 30 pixels.  Its input tile is staged as 6 rows of 32
+// pixels (x0 - 1 .. x0 + 30), so a tap (dy, dx) reads the 128 consecutive staged pixels that
+// start at (1 + dy) 32 + (1 + dx): position m = 32 r + c of that window is output pixel (r, c)
+// for c < 30 (c = 30, 31 fall beyond the tile and are not stored).  One chunk of 16 input
+// channels is then 9 MMAs, M = 128, N = Co (up to 128, a multiple of 16), K = 16, into one
+// accumulator of N columns in tensor memory; the next chunk's input and weights are copied
+// asynchronously (cp.async) into the other of two buffers while the MMAs of this one run.
+// Operands in the canonical K-major layout without swizzle: input [2 k-halves][200 pixels][8],
+// weights [9 taps][2 k-halves][N channels][8]; 8-row groups 128 bytes apart.
 
-__global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int* err)
+constexpr int T2_GW = 32, T2_OW = T2_GW - 2, T2_OH = 4, T2_IH = T2_OH + 2;
+constexpr int T2_NPIX = T2_IH * T2_GW + 8;                          // + zero slack for the last tap
+constexpr int T2_SX = 2 * T2_NPIX * 8;                              // BF16 per input buffer
+constexpr int T2_COMAX = 128;
+
+__host__ __device__ constexpr int t2_smem_bytes(int cop)
 {
-    extern __shared__ __align__(128) unsigned char tc_smem[];
-    bf16* sw = reinterpret_cast<bf16*>(tc_smem);
-    bf16* sx = sw + TC_SW;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc_smem + TC_SMEM_BYTES - 64);
-    unsigned* tslot = reinterpret_cast<unsigned*>(tc_smem + TC_SMEM_BYTES - 48);
+    return (2 * T2_SX + 2 * 9 * 2 * cop * 8) * 2 + 64 + 1024;
+}
 
-    const int n_cot = (a.Co + TC_M - 1) / TC_M;
-    const int b = blockIdx.z / n_cot, co0 = (blockIdx.z % n_cot) * TC_M;
-    const int tx0 = blockIdx.x * CT_W, ty0 = blockIdx.y * CT_H;
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// bounded wait for the phase of parity `parity` of an mbarrier; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity)
+{
+    unsigned done = 0;
+    for (long it = 0; it < (1L << 26) && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(mb)), "r"(parity));
+    }
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int cop, int* err)
+{
+    extern __shared__ __align__(128) unsigned char t2_smem[];
+    const int swn = 9 * 2 * cop * 8;
+    bf16* const sx0 = reinterpret_cast<bf16*>(t2_smem);
+    bf16* const sw0 = sx0 + 2 * T2_SX;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(t2_smem + (size_t)(2 * T2_SX + 2 * swn) * 2);
+    unsigned* tslot = reinterpret_cast<unsigned*>(mbar + 2);
+
+    const int n_cot = (a.Co + cop - 1) / cop;
+    const int b = blockIdx.z / n_cot, co0 = (blockIdx.z % n_cot) * cop;
+    const int tx0 = blockIdx.x * T2_OW, ty0 = blockIdx.y * T2_OH;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    const unsigned ncol = cop <= 32 ? 32u : (cop <= 64 ? 64u : 128u);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(128));
+                     "r"(ncol));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + 1)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -237,74 +264,81 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int* err)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
 
-    bool ok = true;
-    int chunk = 0;
-    for (int c0 = 0; c0 < a.Ci; c0 += 16, ++chunk) {
-        for (int q = tid; q < TC_NPIX * 2; q += 128) {
+    // asynchronous copies of chunk k (16 input channels) into buffer k & 1; out-of-range pixels
+    // and channels are zero-filled
+    auto stage = [&](int k) {
+        const int c0 = k * 16;
+        bf16* sx = sx0 + (k & 1) * T2_SX;
+        bf16* sw = sw0 + (k & 1) * swn;
+        for (int q = tid; q < T2_NPIX * 2; q += 128) {
             const int p = q >> 1, h = q & 1;
-            const int py = p / CT_IW, px = p - py * CT_IW;
+            const int py = p / T2_GW, px = p - py * T2_GW;
             const int gy = ty0 - 1 + py, gx = tx0 - 1 + px;
-            uint4 v = zero;
-            if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-                v = *reinterpret_cast<const uint4*>(a.x + ((long long)(b * a.H + gy) * a.W + gx) * a.ldx + a.xoff + c0 +
-                                                    h * 8);
-            *reinterpret_cast<uint4*>(sx + (h * TC_NPIX + p) * 8) = v;
+            const bool in = p < T2_IH * T2_GW && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+            const bf16* src = in ? a.x + ((long long)(b * a.H + gy) * a.W + gx) * a.ldx + a.xoff + c0 + h * 8 : a.x;
+            cp_async16(sx + (h * T2_NPIX + p) * 8, src, in ? 16 : 0);
         }
-        for (int q = tid; q < 9 * 2 * TC_M; q += 128) {
-            const int t = q / (2 * TC_M), r = q - t * (2 * TC_M);
-            const int h = r / TC_M, co = r - h * TC_M;
-            uint4 v = zero;
-            if (co0 + co < a.Co)
-                v = *reinterpret_cast<const uint4*>(a.w + ((long long)t * a.Co + co0 + co) * a.Ci + c0 + h * 8);
-            *reinterpret_cast<uint4*>(sw + ((t * 2 + h) * TC_M + co) * 8) = v;
+        for (int q = tid; q < 9 * 2 * cop; q += 128) {
+            const int t = q / (2 * cop), r = q - t * (2 * cop);
+            const int h = r / cop, co = r - h * cop;
+            const bool in = co0 + co < a.Co;
+            const bf16* src = in ? a.w + ((long long)t * a.Co + co0 + co) * a.Ci + c0 + h * 8 : a.w;
+            cp_async16(sw + ((t * 2 + h) * cop + co) * 8, src, in ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(cop >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const int nchunk = a.Ci / 16;
+    bool ok = true;
+    stage(0);
+    for (int k = 0; k < nchunk; ++k) {
+        if (k + 1 < nchunk) {
+            // the other buffer was last read by the MMAs of chunk k - 1 (one decision for all threads)
+            if (k >= 1 && !__syncthreads_and(mbar_wait(mbar + ((k - 1) & 1), (unsigned)(((k - 1) >> 1) & 1)))) {
+                ok = false;
+                break;
+            }
+            stage(k + 1);
+            cp_async_wait<1>();     // chunk k has landed; chunk k + 1 may still be in flight
+        } else {
+            cp_async_wait<0>();
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned sw0 = smem_u32(sw), sx0 = smem_u32(sx);
+            const unsigned sxa = smem_u32(sx0 + (k & 1) * T2_SX), swa = smem_u32(sw0 + (k & 1) * swn);
             for (int t = 0; t < 9; ++t) {
                 const int dy = t / 3 - 1, dx = t % 3 - 1;
-                const uint64_t ad = tc_desc(sw0 + (unsigned)(t * 2 * TC_M * 8 * 2), TC_M * 16, 128);
-                for (int r = 0; r < CT_H; ++r) {
-                    const int p0 = (r + 1 + dy) * CT_IW + (1 + dx);
-                    const uint64_t bd = tc_desc(sx0 + (unsigned)(p0 * 16), TC_NPIX * 16, 128);
-                    const unsigned d = tmem + (unsigned)(r * TC_N);
-                    const int acc = (c0 > 0 || t > 0) ? 1 : 0;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                        "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc));
-                }
+                const int p0 = (1 + dy) * T2_GW + (1 + dx);
+                const uint64_t ad = tc_desc(sxa + (unsigned)(p0 * 16), T2_NPIX * 16, 128);
+                const uint64_t bd = tc_desc(swa + (unsigned)(t * 2 * cop * 16), (unsigned)(cop * 16), 128);
+                const int acc = (k > 0 || t > 0) ? 1 : 0;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(mbar)));
+                smem_u32(mbar + (k & 1))));
         }
-        // wait for this chunk's MMAs before the tile is overwritten (bounded)
-        const unsigned parity = (unsigned)(chunk & 1);
-        unsigned done = 0;
-        for (long it = 0; it < (1L << 26) && !done; ++it) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_u32(mbar)), "r"(parity));
-        }
-        if (!done) {
-            ok = false;
-            if (tid == 0) atomicExch(err, 1);
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
     }
+    cp_async_wait<0>();     // no copy in flight past this point, whatever happened above
+    if (ok) ok = mbar_wait(mbar + ((nchunk - 1) & 1), (unsigned)(((nchunk - 1) >> 1) & 1));
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (ok) {
-        // epilogue: warp w holds output channels co0 + 32 w + lane, 16 pixels per row
-        const int co = co0 + warp * 32 + lane;
-        const float bv = (a.bias && co < a.Co) ? a.bias[co] : 0.f;
-        for (int r = 0; r < CT_H; ++r) {
+        // epilogue: warp w holds output row w, lane c its column; columns of the accumulator are
+        // the output channels co0 ..
+        const int gy = ty0 + warp, gx = tx0 + lane;
+        const bool valid = lane < T2_OW && gy < a.H && gx < a.W;
+        const long long o0 = ((long long)(b * a.H + gy) * a.W + gx) * a.ldy + a.yoff + co0;
+        for (int j = 0; j < cop; j += 16) {
             unsigned v[16];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * TC_N);
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)j;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                 "%13, %14, %15}, [%16];"
@@ -312,16 +346,34 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int* err)
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int gy = ty0 + r;
-            if (co >= a.Co || gy >= a.H) continue;
-            for (int c = 0; c < TC_N; ++c) {
-                const int gx = tx0 + c;
-                if (gx >= a.W) continue;
-                float val = __uint_as_float(v[c]) + bv;
+            if (!valid) continue;
+            float f[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int co = co0 + j + e;
+                float val = __uint_as_float(v[e]) + ((a.bias && co < a.Co) ? a.bias[co] : 0.f);
                 if (a.act) val = val > 0.f ? val : SLOPE * val;
-                const long long o = ((long long)(b * a.H + gy) * a.W + gx) * a.ldy + a.yoff + co;
-                if (a.yf) a.yf[o] = val;
-                else a.y[o] = __float2bfloat16_rn(val);
+                f[e] = val;
+            }
+            if (a.yf) {
+                for (int e = 0; e < 16; ++e)
+                    if (co0 + j + e < a.Co) a.yf[o0 + j + e] = f[e];
+            } else if (co0 + j + 16 <= a.Co && ((o0 + j) & 7) == 0) {
+                uint4 w0, w1;
+                unsigned* u0 = &w0.x;
+                unsigned* u1 = &w1.x;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat162 p = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+                    const __nv_bfloat162 q = __floats2bfloat162_rn(f[8 + 2 * e], f[8 + 2 * e + 1]);
+                    u0[e] = *reinterpret_cast<const unsigned*>(&p);
+                    u1[e] = *reinterpret_cast<const unsigned*>(&q);
+                }
+                *reinterpret_cast<uint4*>(a.y + o0 + j) = w0;
+                *reinterpret_cast<uint4*>(a.y + o0 + j + 8) = w1;
+            } else {
+                for (int e = 0; e < 16; ++e)
+                    if (co0 + j + e < a.Co) a.y[o0 + j + e] = __float2bfloat16_rn(f[e]);
             }
         }
     }
@@ -329,7 +381,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const ConvArgs a, int* err)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol));
     }
 }
 
@@ -690,7 +742,8 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16* x, long long ldx, int xoff, con
     if (g_conv_kernel == 1) {
         static bool attr = false;
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, t2_smem_bytes(T2_COMAX));
             if (e != cudaSuccess) return e;
             attr = true;
         }
@@ -699,8 +752,11 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16* x, long long ldx, int xoff, con
             if (e == cudaSuccess) e = cudaMemset(g_conv_err, 0, sizeof(int));
             if (e != cudaSuccess) return e;
         }
-        dim3 grid((W + CT_W - 1) / CT_W, (H + CT_H - 1) / CT_H, B * ((Co + TC_M - 1) / TC_M));
-        k_conv3x3_tc<<<grid, 128, TC_SMEM_BYTES, s>>>(a, g_conv_err);
+        if (Ci % 16 != 0) return cudaErrorInvalidValue;
+        int cop = (Co + 15) / 16 * 16;
+        if (cop > T2_COMAX) cop = T2_COMAX;
+        dim3 grid((W + T2_OW - 1) / T2_OW, (H + T2_OH - 1) / T2_OH, B * ((Co + cop - 1) / cop));
+        k_conv3x3_tc<<<grid, 128, t2_smem_bytes(cop), s>>>(a, cop, g_conv_err);
         return cudaGetLastError();
     }
     dim3 grid((W + CT_W - 1) / CT_W, (H + CT_H - 1) / CT_H, B * ((Co + CT_CO - 1) / CT_CO));
