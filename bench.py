@@ -184,8 +184,9 @@ def run_reference(args, rank, world):
 
 def measure_forms(args, lb, W, torch):
     """The 4096^2 workload with 16 rings (128 nodes, radius 12, seeded positions and pull angles)
-    in the FP32 and the FP16/BF16 storage forms (state 0.94-1.9 GB, larger than L2, so no flush),
-    and the precision form's restoring-force error against the FP32 step (256^2, 2000 steps)."""
+    in the FP32 and the FP16/BF16 storage forms and with the scalar model (one modulus, no P
+    field) in FP32 (state 0.94-1.9 GB, larger than L2, so no flush), and the precision form's
+    restoring-force error against the FP32 step (256^2, 2000 steps)."""
     import numpy as np
     peaks, _ = measured_peaks()
     out = {"workload": "4096x4096 periodic, 16 rings of 128 nodes (radius 12, seeded), pull 5e-4 "
@@ -193,8 +194,10 @@ def measure_forms(args, lb, W, torch):
     w = W.cfg3()
     cells = w["nx"] * w["ny"]
     steps = max(3, min(args.steps, 10))
-    for name, prec in [("fp32", lb.LB_FP32), ("fp16_bf16", lb.LB_FP16_BF16)]:
-        s = lb.Solver.from_workload(w, precision=prec)
+    ws = dict(w, **W.scalar_physics())
+    for name, prec, wk in [("fp32", lb.LB_FP32, w), ("fp16_bf16", lb.LB_FP16_BF16, w),
+                           ("scalar_fp32", lb.LB_FP32, ws)]:
+        s = lb.Solver.from_workload(wk, precision=prec)
         stream = torch.cuda.current_stream()
         for _ in range(2):
             s.step(LB_STEPS_PER_STEP)

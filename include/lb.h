@@ -73,9 +73,23 @@ typedef struct lb_params {
     int32_t readout_every;          /* record readouts when t % readout_every == 0 (10)       */
     int32_t max_samples;            /* capacity of the readout ring buffer (rows)             */
     int32_t diffusion_substeps;     /* 0: D_p inside the Heun step (needs 8 D_p <= 2); s > 0:  */
-    int32_t pad_;                   /*   the Heun step without diffusion, then s Heun sub-steps */
+                                    /*   the Heun step without diffusion, then s Heun sub-steps */
                                     /*   of D_p / s on sigma (needs 8 D_p / s <= 2; FP32 only)  */
+    int32_t model;                  /* LB_MODEL_TENSORIAL (0) or LB_MODEL_SCALAR (1), below    */
 } lb_params;
+
+/*
+ * Viscoelastic model.  LB_MODEL_TENSORIAL: Eq. StiffCons with C~(P) (App. B) and the
+ * Beris-Edwards P field (Eq. BE).  LB_MODEL_SCALAR: the scalar diffusive Johnson-Segalman model
+ * of Eq. MaxDiff (Sec. II B), D sigma / Dt = C Psi - (C / eta_p) sigma + D_p lap sigma with one
+ * modulus C, and no orientation field: the state moves 12 planes (96 B per cell and step in
+ * FP32).  It needs K2222 = K1111, K1122 = 0, K1212 = K1111 / 2 (C = K1111: the isotropic K^x, for
+ * which the tensorial C~ is C times the identity at every P, so both models then compute the same
+ * fluid and stress), ericksen = 0, the FP32 state and the one-cell tile kernel (lb_set_kernel
+ * AUTO or TILE); P stays at its initial field and is not writable.  Else LB_EINVAL.
+ */
+#define LB_MODEL_TENSORIAL 0
+#define LB_MODEL_SCALAR 1
 
 typedef struct lb_ring {
     int32_t n_nodes;                /* 3 <= n_nodes <= 1024                                    */
@@ -229,7 +243,7 @@ void lb_destroy(lb_handle* h);
  * equal; the readout sums of the lattice may differ in the last bits with the tile shape).
  *
  * lb_batch_create: handles[0..n-1] (n >= 1) must be distinct, have their fields and bodies set
- *   (lb_init_fields, lb_set_body), use the FP32 state, share one stream and be at the same
+ *   (lb_init_fields, lb_set_body), use the FP32 state and the tensorial model, share one stream and be at the same
  *   buffer parity (an equal step count mod 2).  The batch keeps the pointers: the handles must
  *   outlive it and must not be stepped with lb_step while it exists.  Readouts (lb_readout,
  *   lb_series, ...) on the handles stay valid and are ordered after the batch's steps.
@@ -335,7 +349,7 @@ int lb_conv3x3_wgrad(const void* x, const void* gz, float* gw, float* gb, int32_
  *   or NULL) and the raw fields raw (device FP32 [ny][nx][8], or NULL); FP32 state only.
  * lb_learned_target: the training target (device FP32 [cells][16]) of a pair of raw fields 16
  *   steps apart.  lb_learned_normalize: the network input (BF16 [cells][16]) of raw fields.
- * lb_learned_create: a stepper for handle h (FP32 state, readout_every a multiple of 16) with a
+ * lb_learned_create: a stepper for handle h (FP32 state, tensorial model, readout_every a multiple of 16) with a
  *   network of batch 1 and the lattice's size.  eps_momentum bounds the momentum-balance
  *   residual |sum u_net - sum u(t) - 16 F_pull| / (16 |F_pull|) (an accepted velocity is then
  *   shifted uniformly so that the balance holds exactly); eps_tendency bounds the relative

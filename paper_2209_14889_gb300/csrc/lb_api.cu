@@ -91,6 +91,7 @@ FusedArgs fused_args(lb_handle* h)
     a.src = h->state[h->cur];
     a.dst = h->state[h->cur ^ 1];
     a.prec = h->p.precision == LB_FP32 ? 0 : 1;
+    a.scalar = h->p.model == LB_MODEL_SCALAR ? 1 : 0;
     a.plane = h->plane;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
@@ -250,6 +251,15 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     if (!(eta > 0.0)) eta = p.lambda_steps * S8;
     if (!(eta > 0.0) || !std::isfinite(eta)) return fail(nullptr, LB_EINVAL, "need eta_p > 0 or lambda_steps > 0");
     // explicit stability bounds of the Heun steps (|z| <= 2 on the negative real axis)
+    if (p.model != LB_MODEL_TENSORIAL && p.model != LB_MODEL_SCALAR)
+        return fail(nullptr, LB_EINVAL, "unknown model %d", p.model);
+    if (p.model == LB_MODEL_SCALAR) {
+        if (p.precision != LB_FP32) return fail(nullptr, LB_EINVAL, "the scalar model needs the FP32 state");
+        if (p.ericksen) return fail(nullptr, LB_EINVAL, "the scalar model has no Ericksen force (ericksen = 0)");
+        const double C = p.K1111, tol = 1e-12 * std::fabs(C);
+        if (!(C > 0.0) || std::fabs(p.K2222 - C) > tol || std::fabs(p.K1122) > tol || std::fabs(p.K1212 - 0.5 * C) > tol)
+            return fail(nullptr, LB_EINVAL, "the scalar model needs K2222 = K1111, K1122 = 0, K1212 = K1111 / 2");
+    }
     if (p.diffusion_substeps < 0) return fail(nullptr, LB_EINVAL, "diffusion_substeps < 0");
     if (p.diffusion_substeps > 0 && p.precision != LB_FP32)
         return fail(nullptr, LB_EINVAL, "diffusion sub-steps need the FP32 state");
@@ -378,6 +388,13 @@ int lb_init_fields(lb_handle* h, const double* noise)
     }
     cudaFree(tmp);
     if (rc != LB_OK) return rc;
+    if (h->p.model == LB_MODEL_SCALAR) {
+        // the scalar model never writes P: both buffers keep the initial field
+        const size_t pb = (size_t)h->esz * N;
+        CK(h, cudaMemcpyAsync(static_cast<char*>(h->state[h->cur ^ 1]) + PL_PX * pb,
+                              static_cast<const char*>(h->state[h->cur]) + PL_PX * pb, 2 * pb,
+                              cudaMemcpyDeviceToDevice, h->stream));
+    }
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->stream));
     h->t = 0;
     h->after_tail = false;
@@ -628,6 +645,8 @@ int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, i
     if (field >= LB_FIELD_SXX && field <= LB_FIELD_PY) plane = PL_SXX + field - LB_FIELD_SXX;
     else if (field >= LB_FIELD_POP0 && field < LB_FIELD_POP0 + 9) plane = field - LB_FIELD_POP0;
     else return fail(h, LB_EINVAL, "field %d is not writable", field);
+    if (h->p.model == LB_MODEL_SCALAR && (field == LB_FIELD_PX || field == LB_FIELD_PY))
+        return fail(h, LB_EINVAL, "the scalar model has no P field to write");
     const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (!h->moments) CK(h, cudaMalloc(&h->moments, sizeof(float) * 3 * N));
     CK(h, cudaMemcpyAsync(h->moments, src, bytes, kind, h->stream));
@@ -745,13 +764,20 @@ int lb_set_kernel(lb_handle* h, int32_t kernel)
     if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_PAIR) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
     if (kernel == LB_KERNEL_SWEEP && h->p.precision != LB_FP32)
         return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
+    if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.model == LB_MODEL_SCALAR)
+        return fail(h, LB_EINVAL, "the scalar model runs on the one-cell tile kernel only");
     if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))
         return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");
     h->kernel = kernel;
     return LB_OK;
 }
 
-double lb_bytes_per_cell(const lb_handle* h) { return h ? 2.0 * N_PLANES * h->esz : 0.0; }
+double lb_bytes_per_cell(const lb_handle* h)
+{
+    if (!h) return 0.0;
+    const int planes = h->p.model == LB_MODEL_SCALAR ? N_PLANES - 2 : N_PLANES;   // no P planes
+    return 2.0 * planes * h->esz;
+}
 
 }  // extern "C"
 

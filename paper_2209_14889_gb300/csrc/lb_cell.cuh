@@ -142,11 +142,37 @@ __device__ __forceinline__ void molecular(const Phys& ph, const StT<T>& dx, cons
 
 // Right-hand sides of Eq. StiffCons (with the Jaumann derivative) and Eq. BE at one cell, for
 // the frozen u, Psi = (pxx, pyy, pxy), omega = Omega_xy; s = sigma (xx, yy, xy), p = dP (x, y).
-template <class T>
+// SCALAR: the scalar model of Eq. MaxDiff (Sec. II B): a constant modulus C = ph.kS8 in place of
+// C~(P), and no P field (p0, p1, hx, hy unused; r[3], r[4] not written).  It rounds exactly as
+// the tensorial form does for the isotropic K^x (K2222 = K1111, K1122 = 0, K1212 = K1111 / 2),
+// whose C~ is C times the identity for every P.
+template <class T, bool SCALAR = false>
 __device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, T ux, T uy, T pxx, T pyy, T pxy,
                                          T om, const StT<T>& s0, const StT<T>& s1, const StT<T>& s2,
                                          const StT<T>& p0, const StT<T>& p1, T hx, T hy, T* r)
 {
+    // C psi - C s / eta_p = C (psi - s / eta_p)
+    const T v0 = vfma(-ph.inv_eta, s0.c, pxx);
+    const T v1 = vfma(-ph.inv_eta, s1.c, pyy);
+    const T v2 = vfma(-ph.inv_eta, s2.c, pxy);
+    T Cv0, Cv1, Cv2;
+    // Jaumann rotation (Omega s - s Omega) = (2 w sxy, -2 w sxy, w (syy - sxx))
+    const T J0 = 2.f * (om * s2.c);
+    const T J2 = om * (s1.c - s0.c);
+    // advection -(u.grad) y with central differences (uh = u / 2 times the plain differences)
+    const T uxh = 0.5f * ux, uyh = 0.5f * uy;
+    const float D = ph.Dp;
+    auto nadv = [&](const StT<T>& f) { return vfma(uxh, f.w - f.e, uyh * (f.s - f.n)); };
+    auto lap = [&](const StT<T>& f) { return vfma(-4.f, f.c, (f.e + f.w) + (f.n + f.s)); };
+    if (SCALAR) {
+        Cv0 = ph.kS8 * v0;
+        Cv1 = ph.kS8 * v1;
+        Cv2 = ph.kS8 * v2;
+        r[0] = vfma(D, lap(s0), (Cv0 - J0) + nadv(s0));
+        r[1] = vfma(D, lap(s1), (Cv1 + J0) + nadv(s1));
+        r[2] = vfma(D, lap(s2), (Cv2 - J2) + nadv(s2));
+        return;
+    }
     // stiffness C~(P) (App. B) from the table of a2, a4 and polynomials in P = P_ref + dP
     const T Px = p0.c + ph.prx, Py = p1.c + ph.pry;
     const T PxPx = Px * Px, PyPy = Py * Py;
@@ -164,24 +190,9 @@ __device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, T ux,
     const T C22 = vfma(-ph.dK, r2c2, C11);
     const T C23 = hds - xs;
     const T C33 = vfma(-2.f, xc, bc<T>(ph.kC33));
-
-    // C psi - C s / eta_p = C (psi - s / eta_p)
-    const T v0 = vfma(-ph.inv_eta, s0.c, pxx);
-    const T v1 = vfma(-ph.inv_eta, s1.c, pyy);
-    const T v2 = vfma(-ph.inv_eta, s2.c, pxy);
-    const T Cv0 = vfma(C11, v0, vfma(C12, v1, C13 * v2));
-    const T Cv1 = vfma(C12, v0, vfma(C22, v1, C23 * v2));
-    const T Cv2 = vfma(0.5f * C13, v0, vfma(0.5f * C23, v1, C33 * v2));
-
-    // Jaumann rotation (Omega s - s Omega) = (2 w sxy, -2 w sxy, w (syy - sxx))
-    const T J0 = 2.f * (om * s2.c);
-    const T J2 = om * (s1.c - s0.c);
-
-    // advection -(u.grad) y with central differences (uh = u / 2 times the plain differences)
-    const T uxh = 0.5f * ux, uyh = 0.5f * uy;
-    const float D = ph.Dp;
-    auto nadv = [&](const StT<T>& f) { return vfma(uxh, f.w - f.e, uyh * (f.s - f.n)); };
-    auto lap = [&](const StT<T>& f) { return vfma(-4.f, f.c, (f.e + f.w) + (f.n + f.s)); };
+    Cv0 = vfma(C11, v0, vfma(C12, v1, C13 * v2));
+    Cv1 = vfma(C12, v0, vfma(C22, v1, C23 * v2));
+    Cv2 = vfma(0.5f * C13, v0, vfma(0.5f * C23, v1, C33 * v2));
     r[0] = vfma(D, lap(s0), (Cv0 - J0) + nadv(s0));
     r[1] = vfma(D, lap(s1), (Cv1 + J0) + nadv(s1));
     r[2] = vfma(D, lap(s2), (Cv2 - J2) + nadv(s2));

@@ -178,7 +178,7 @@ __device__ __forceinline__ void node_tail(const FusedArgs& a, float* sm)
         node_tail_work<TX, TY>(a, sm);
 }
 
-template <int MODE, int PREC>
+template <int MODE, int PREC, bool SCALAR = false>
 __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
 {
     extern __shared__ __align__(16) float sm[];
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(const FusedArgs a)
         by += a.tile_rot;
         if (by >= (int)gridDim.y) by -= gridDim.y;
     }
-    tile_step<MODE, PREC, TILE_X, TILE_Y>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
+    tile_step<MODE, PREC, TILE_X, TILE_Y, false, SCALAR>(a, blockIdx.x, by, by * gridDim.x + blockIdx.x, sm);
     if (tail) node_tail<TILE_X, TILE_Y>(a, sm);
 }
 
@@ -222,11 +222,11 @@ int fused_tile_rot(int nx, int ny, double y_top)
     return row;
 }
 
-template <int MODE, int PREC, bool PAIR>
+template <int MODE, int PREC, bool PAIR, bool SCALAR = false>
 static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s, bool pdl)
 {
     static bool attr_done = false;
-    auto kern = PAIR ? k_fused_pair<MODE, PREC> : k_fused<MODE, PREC>;
+    auto kern = PAIR ? k_fused_pair<MODE, PREC> : k_fused<MODE, PREC, SCALAR>;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)TileGeo<TILE_X, TILE_Y>::SMEM_BYTES);
@@ -249,6 +249,10 @@ static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s, boo
 template <bool PAIR>
 static cudaError_t launch_form(const FusedArgs& a, int mode, dim3 grid, cudaStream_t s, bool pdl)
 {
+    // the scalar model's step (FP32 state, one-cell tiles); its moments pass is the tensorial one,
+    // which reads the unchanged P planes and, with the Ericksen force off, does not use them
+    if (!PAIR && a.scalar && a.prec == PREC_FP32 && mode == MODE_STEP)
+        return launch_one<MODE_STEP, PREC_FP32, false, true>(a, grid, s, pdl);
     if (a.prec == PREC_FP32)
         return mode == MODE_STEP ? launch_one<MODE_STEP, PREC_FP32, PAIR>(a, grid, s, pdl)
                                  : launch_one<MODE_MOMENTS, PREC_FP32, PAIR>(a, grid, s, false);

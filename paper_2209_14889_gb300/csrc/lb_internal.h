@@ -100,6 +100,7 @@ struct FusedArgs {
     const void* src;             // state at t (N_PLANES planes: FP32, or FP16/BF16 in the precision form)
     void* dst;                   // state at t + 1
     int prec;                    // 0: FP32 state, 1: FP16 populations + BF16 sigma, dP
+    int scalar;                  // 1: the scalar model (constant modulus, no P field; FP32 only)
     long long plane;             // nx * ny
     int nx, ny;
     Phys ph;

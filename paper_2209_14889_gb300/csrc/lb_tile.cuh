@@ -109,7 +109,7 @@ __device__ __forceinline__ float2 ld_fld2(const void* src, long long NP, int pla
 // With nx even every staged row starts at an even column (x0 - 4, wrapped), so the rows are read
 // as aligned pairs that never straddle the periodic seam; each thread issues all its loads
 // before its shared-memory stores.  Odd nx takes single-value loads.
-template <int PREC, bool COH, int TX, int TY>
+template <int PREC, bool COH, int TX, int TY, bool SCALAR = false>
 __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
 {
     using G = TileGeo<TX, TY>;
@@ -132,7 +132,7 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             const int q = tid + k * NT;
-            if (q < NPP) {
+            if (!SCALAR && q < NPP) {
                 const int ly = q / HP, lx = 2 * (q - ly * HP);
                 const long long g = (long long)m.sYi[ly] * nx + m.sXi[lx];
                 vp[k][0] = ld_fld2<PREC, COH>(src, NP, PL_PX, g);
@@ -152,7 +152,7 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             const int q = tid + k * NT;
-            if (q < NPP) {
+            if (!SCALAR && q < NPP) {
                 st2<true>(m.sP + 2 * q, vp[k][0]);
                 st2<true>(m.sP + R4 + 2 * q, vp[k][1]);
             }
@@ -171,7 +171,7 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
             }
         }
     } else {
-        for (int i = tid; i < R4; i += NT) {
+        for (int i = tid; i < (SCALAR ? 0 : R4); i += NT) {
             const int ly = i / R4W, lx = i - ly * R4W;
             const long long g = (long long)m.sYi[ly] * nx + m.sXi[lx];
             m.sP[i] = ld_fld<PREC, COH>(src, NP, PL_PX, g);
@@ -414,7 +414,7 @@ __device__ constexpr int C_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 // One TX x TY tile (tile coordinates bx, by) of the step, one cell per thread and iteration;
 // sm: TileGeo<TX, TY>::SMEM_BYTES of shared memory.  Used by the sweep comparison and kept as the
 // reference form of the paired step below.
-template <int MODE, int PREC, int TX, int TY, bool COH = false>
+template <int MODE, int PREC, int TX, int TY, bool COH = false, bool SCALAR = false>
 __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, int tile_index, float* sm)
 {
     using G = TileGeo<TX, TY>;
@@ -432,10 +432,10 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const Phys& ph = a.ph;
     const void* src = a.src;
 
-    stage<PREC, COH>(a, m, x0, y0);
+    stage<PREC, COH, TX, TY, SCALAR>(a, m, x0, y0);
 
-    // ---- B: molecular field and Ericksen stress on the halo-3 region ------------------------
-    for (int k = tid; k < R3; k += NT) {
+    // ---- B: molecular field and Ericksen stress on the halo-3 region (not in the scalar model)
+    for (int k = tid; k < (SCALAR ? 0 : R3); k += NT) {
         int lx, ly;
         region_cell<TX, TY, 3>(k, lx, ly);
         const int i = ly * R3W + lx;
@@ -541,21 +541,23 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         const St s0 = st_at(m.sS, R3W, lx + 2, ly + 2);
         const St s1 = st_at(m.sS + R3, R3W, lx + 2, ly + 2);
         const St s2 = st_at(m.sS + 2 * R3, R3W, lx + 2, ly + 2);
-        const St p0 = st_at(m.sP, R4W, lx + 3, ly + 3);
-        const St p1 = st_at(m.sP + R4, R4W, lx + 3, ly + 3);
+        const St p0 = SCALAR ? St{} : st_at(m.sP, R4W, lx + 3, ly + 3);
+        const St p1 = SCALAR ? St{} : st_at(m.sP + R4, R4W, lx + 3, ly + 3);
         const int j3 = (ly + 2) * R3W + lx + 2;
         float r[5];
-        rhs_cell(ph, sL, m.sM[R2 + j2], m.sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
-                 m.sH[j3], m.sH[R3 + j3], r);
+        rhs_cell<float, SCALAR>(ph, sL, m.sM[R2 + j2], m.sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
+                                SCALAR ? 0.f : m.sH[j3], SCALAR ? 0.f : m.sH[R3 + j3], r);
         // y* (the sigma^E buffer is dead: C has finished)
         m.sY[i] = s0.c + r[0];
         m.sY[R1 + i] = s1.c + r[1];
         m.sY[2 * R1 + i] = s2.c + r[2];
-        m.sY[3 * R1 + i] = p0.c + r[3];
-        m.sY[4 * R1 + i] = p1.c + r[4];
+        if (!SCALAR) {
+            m.sY[3 * R1 + i] = p0.c + r[3];
+            m.sY[4 * R1 + i] = p1.c + r[4];
+        }
         if (k < R0) {       // an owned cell: k = (ly - 1) TX + (lx - 1)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) m.sR[c * R0 + k] = r[c];
+            for (int c = 0; c < (SCALAR ? 3 : 5); ++c) m.sR[c * R0 + k] = r[c];
         }
     }
     __syncthreads();
@@ -576,19 +578,27 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             const St s0 = st_at(m.sY, R1W, lx + 1, ly + 1);
             const St s1 = st_at(m.sY + R1, R1W, lx + 1, ly + 1);
             const St s2 = st_at(m.sY + 2 * R1, R1W, lx + 1, ly + 1);
-            const St p0 = st_at(m.sY + 3 * R1, R1W, lx + 1, ly + 1);
-            const St p1 = st_at(m.sY + 4 * R1, R1W, lx + 1, ly + 1);
-            float hx, hy;
-            molecular(ph, p0, p1, hx, hy);
+            const St p0 = SCALAR ? St{} : st_at(m.sY + 3 * R1, R1W, lx + 1, ly + 1);
+            const St p1 = SCALAR ? St{} : st_at(m.sY + 4 * R1, R1W, lx + 1, ly + 1);
+            float hx = 0.f, hy = 0.f;
+            if (!SCALAR) molecular(ph, p0, p1, hx, hy);
             float r[5];
-            rhs_cell(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
+            rhs_cell<float, SCALAR>(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
             const int j3 = (ly + 3) * R3W + lx + 3;
             const int j4 = (ly + 4) * R4W + lx + 4;
-            const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], m.sP[j4], m.sP[R4 + j4]};
-            float ynew[5];
+            if (SCALAR) {
+                // sigma only: the scalar model has no P field (its planes keep their values)
+                float* d = reinterpret_cast<float*>(dst);
+                d[PL_SXX * NP + g] = vfma(0.5f, m.sR[i] + r[0], m.sS[j3]);
+                d[PL_SYY * NP + g] = vfma(0.5f, m.sR[R0 + i] + r[1], m.sS[R3 + j3]);
+                d[PL_SXY * NP + g] = vfma(0.5f, m.sR[2 * R0 + i] + r[2], m.sS[2 * R3 + j3]);
+            } else {
+                const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], m.sP[j4], m.sP[R4 + j4]};
+                float ynew[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
-            st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
+                for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
+                st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
+            }
         }
         box_write<R3, R3W>(a, bmask, t, gx, gy, ux, uy, readout, m.sS, (ly + 3) * R3W + lx + 3);
     }

@@ -21,6 +21,7 @@ LB_FP32 = 0
 LB_FP16_BF16 = 1
 LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP, LB_KERNEL_PAIR = 0, 1, 2, 3
 FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
+LB_MODEL_TENSORIAL, LB_MODEL_SCALAR = 0, 1
 LB_FIELD_POP0 = 8
 LB_FIELD_NODES = 17
 
@@ -43,7 +44,7 @@ class lb_params(ctypes.Structure):
                 ("P_cap", ctypes.c_double), ("director_angle", ctypes.c_double),
                 ("ericksen", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32),
-                ("diffusion_substeps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("diffusion_substeps", ctypes.c_int32), ("model", ctypes.c_int32)]
 
 
 class lb_ring(ctypes.Structure):
@@ -163,7 +164,7 @@ def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4
                      P_cap=w.get("P_cap", 0.99), director_angle=w["director_angle"],
                      ericksen=w.get("ericksen", 1), precision=precision,
                      readout_every=w.get("every", 10), max_samples=max_samples,
-                     diffusion_substeps=w.get("diffusion_substeps", 0))
+                     diffusion_substeps=w.get("diffusion_substeps", 0), model=w.get("model", LB_MODEL_TENSORIAL))
 
 
 def stiffness_table(P_cap: float = 0.99) -> np.ndarray:

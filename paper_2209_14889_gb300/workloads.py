@@ -29,6 +29,14 @@ DEFAULT_PHYSICS = dict(tau=0.8, rho0=1.0, K=(2e-3, 1e-3, 1e-3, 1e-3), lambda_ste
                        P_cap=0.99, ericksen=1, director_angle=0.0)
 
 
+def scalar_physics(C: float = 1.875e-3) -> dict:
+    """Overrides for the scalar model (Eq. MaxDiff, Sec. II B): one modulus C written as the
+    isotropic K^x (K1111 = K2222 = C, K1122 = 0, K1212 = C / 2; C defaults to C~11(k = 0) of the
+    default K^x), no Ericksen force.  The oracle runs the same physics through the tensorial
+    equations, whose C~ is then C times the identity."""
+    return dict(K=(C, 0.0, C, C / 2), ericksen=0, model=1)
+
+
 def ring(n_nodes: int, radius: float, centre, k_spring=0.1, eps_angle=0.01, pull_force=1e-3,
          pull_angle=0.0, phase=0.0) -> dict:
     """A closed ring of n_nodes points on a circle (node a at angle phase + 2 pi a / N)."""

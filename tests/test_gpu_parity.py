@@ -421,3 +421,76 @@ def test_more_rings_than_a_tile_mask_holds_vs_oracle():
     check_fields(got, ref)
     check_nodes(got, ref, w)
     check_series(got, ref, 36)
+
+
+# ------------------------------------------------------------------------------------------
+# Scalar model (Eq. MaxDiff): one modulus, no P field, 96 B per cell and step
+# ------------------------------------------------------------------------------------------
+
+SCALAR_FIELDS = ("drho", "ux", "uy", "sxx", "syy", "sxy")
+
+
+def _scalar_workload(**kw):
+    return W.small(64, 48, n_nodes=24, radius=5.0, steps=0, **W.scalar_physics(), **kw)
+
+
+def test_scalar_model_vs_oracle():
+    # the oracle runs the same physics through the tensorial equations (C~ = C I for the
+    # isotropic K^x, Ericksen force off); its P field evolves but feeds back into nothing
+    lb = _gpu()
+    w = _scalar_workload()
+    sim = O.Sim.from_workload(w)
+    sim.step(120, every=10)
+    ref = dict(fields={k: v for k, v in sim.fields().items() if k in SCALAR_FIELDS},
+               series=np.array(sim.series), X=sim.X.copy())
+    s = lb.Solver.from_workload(w)
+    assert s.bytes_per_cell == 96.0
+    P0 = s.readout("Px", device=False)
+    s.step(120)
+    s.sync()
+    got = dict(fields={k: s.readout(k, device=False).astype(np.float64) for k in SCALAR_FIELDS},
+               series=s.series(), X=s.nodes())
+    assert np.array_equal(s.readout("Px", device=False), P0)      # P keeps its initial field
+    s.close()
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+@pytest.mark.parametrize("dsub", [0, 2])
+def test_scalar_model_equals_tensorial_with_isotropic_stiffness_bitwise(dsub):
+    # with C~ = C I the tensorial step computes the same fluid, stress, nodes and readouts, bit
+    # for bit: the scalar step skips the P field and rounds the stress terms in the same order
+    lb = _gpu()
+    w = _scalar_workload(Dp=0.3 if dsub else 0.05, diffusion_substeps=dsub)
+    out = []
+    for model in (lb.LB_MODEL_SCALAR, lb.LB_MODEL_TENSORIAL):
+        s = lb.Solver.from_workload(dict(w, model=model))
+        s.step(37)
+        s.sync()
+        out.append(({k: s.readout(k, device=False) for k in SCALAR_FIELDS}, s.nodes(), s.series()))
+        s.close()
+    for k in SCALAR_FIELDS:
+        assert np.array_equal(out[0][0][k], out[1][0][k]), k
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_scalar_model_rejections():
+    lb = _gpu()
+    w = _scalar_workload()
+    for bad in (dict(precision=lb.LB_FP16_BF16),):
+        with pytest.raises(lb.LBError):
+            lb.Solver(lb.params_from_workload(w, **bad))
+    for over in (dict(ericksen=1), dict(K=(1.875e-3, 0.0, 1.875e-3, 1.0e-3))):
+        with pytest.raises(lb.LBError):
+            lb.Solver(lb.params_from_workload(dict(w, **over)))
+    s = lb.Solver.from_workload(w)
+    for k in (lb.LB_KERNEL_PAIR, lb.LB_KERNEL_SWEEP):
+        with pytest.raises(lb.LBError):
+            s.set_kernel(k)
+    with pytest.raises(lb.LBError):
+        s.write_field("Px", np.zeros((w["ny"], w["nx"]), dtype=np.float32))
+    with pytest.raises(lb.LBError):
+        lb.Batch([s])
+    s.close()

@@ -193,6 +193,21 @@ def test_scalar_limit():
     assert np.abs(ds - ref).max() < 1e-14
 
 
+def test_isotropic_stiffness_is_scalar_at_every_P():
+    # the reading behind the scalar model: with K2222 = K1111, K1122 = 0, K1212 = K1111 / 2
+    # (Delta K = X = 0 in App. B) the orientation average is C times the identity for every
+    # |P| and angle, not only at k = 0, so the scalar Eq. MaxDiff is that tensor's exact case
+    C0 = 1.875e-3
+    p = _p(K1111=C0, K1122=0.0, K2222=C0, K1212=C0 / 2, eta_p=1.0)
+    for mag in (0.0, 0.3, 0.7, 0.95, 0.99, 1.2):
+        for th in (0.0, 0.4, 1.3, 2.9):
+            C = O.stiffness(p, mag * np.cos(th), mag * np.sin(th))
+            assert np.abs(C - C0 * np.eye(3)).max() <= 1e-15, (mag, th)
+    # and an anisotropic K is not: the same test fails for K1212 off by 10 %
+    q = _p(K1111=C0, K1122=0.0, K2222=C0, K1212=0.55 * C0, eta_p=1.0)
+    assert np.abs(O.stiffness(q, 0.6, 0.3) - O.stiffness(q, 0.0, 0.0)).max() > 1e-6
+
+
 # ----------------------------------------------------------------------------------------
 # Immersed boundary (App. A)
 # ----------------------------------------------------------------------------------------
