@@ -151,7 +151,7 @@ def params_from_workload(w: dict) -> Params:
                   K2222=K[2], K1212=K[3], eta_p=eta_p, Dp=w["Dp"], alpha=w["alpha"],
                   beta=w["beta"], xi=w["xi"], Gamma=w["Gamma"], kappa=w["kappa"],
                   P_cap=w.get("P_cap", 0.99), ericksen=w.get("ericksen", 1),
-                  diffusion_substeps=w.get("diffusion_substeps", 0))
+                  diffusion_substeps=w.get("diffusion_substeps", 0), walls_y=w.get("walls_y", 0))
 
 
 # ---------------------------------------------------------------------------------------

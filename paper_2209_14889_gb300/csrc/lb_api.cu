@@ -92,6 +92,7 @@ FusedArgs fused_args(lb_handle* h)
     a.dst = h->state[h->cur ^ 1];
     a.prec = h->p.precision == LB_FP32 ? 0 : 1;
     a.scalar = h->p.model == LB_MODEL_SCALAR ? 1 : 0;
+    a.walls_y = h->p.walls_y;
     a.plane = h->plane;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
@@ -133,6 +134,7 @@ NodeArgs node_args(lb_handle* h, int advance)
     a.every = h->p.readout_every;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
+    a.walls_y = h->p.walls_y;
     a.advance = advance;
     a.n_ctas = h->n_node_ctas;
     a.work = h->node_work;
@@ -260,6 +262,9 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
         if (!(C > 0.0) || std::fabs(p.K2222 - C) > tol || std::fabs(p.K1122) > tol || std::fabs(p.K1212 - 0.5 * C) > tol)
             return fail(nullptr, LB_EINVAL, "the scalar model needs K2222 = K1111, K1122 = 0, K1212 = K1111 / 2");
     }
+    if (p.walls_y != 0 && p.walls_y != 1) return fail(nullptr, LB_EINVAL, "walls_y must be 0 or 1");
+    if (p.walls_y && (p.precision != LB_FP32 || p.diffusion_substeps != 0))
+        return fail(nullptr, LB_EINVAL, "walls need the FP32 state and no diffusion sub-steps");
     if (p.diffusion_substeps < 0) return fail(nullptr, LB_EINVAL, "diffusion_substeps < 0");
     if (p.diffusion_substeps > 0 && p.precision != LB_FP32)
         return fail(nullptr, LB_EINVAL, "diffusion sub-steps need the FP32 state");
@@ -434,6 +439,8 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
             mny = std::fmin(mny, dy); mxy = std::fmax(mxy, dy);
             if (!std::isfinite(P[2 * k]) || !std::isfinite(P[2 * k + 1]))
                 return fail(h, LB_EINVAL, "ring %d: non-finite node", r);
+            if (h->p.walls_y && (P[2 * k + 1] < 5.0 || P[2 * k + 1] > ny - 6.0))
+                return fail(h, LB_EINVAL, "ring %d: a node within 5 cells of a wall", r);
             double xw = std::fmod(P[2 * k], (double)nx); if (xw < 0) xw += nx; if (xw >= nx) xw -= nx;
             double yw = std::fmod(P[2 * k + 1], (double)ny); if (yw < 0) yw += ny; if (yw >= ny) yw -= ny;
             X.push_back(make_double2(xw, yw));
@@ -766,6 +773,8 @@ int lb_set_kernel(lb_handle* h, int32_t kernel)
         return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
     if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.model == LB_MODEL_SCALAR)
         return fail(h, LB_EINVAL, "the scalar model runs on the one-cell tile kernel only");
+    if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.walls_y)
+        return fail(h, LB_EINVAL, "walls run on the one-cell tile kernel only");
     if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))
         return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");
     h->kernel = kernel;

@@ -232,6 +232,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem&
                 const double dX = 0.5 * ((double)vx + (double)wx), dY = 0.5 * ((double)vy + (double)wy);
                 if (!(fabs(dX) < 1.0 && fabs(dY) < 1.0)) bad = 1;
                 Xn = make_double2(wrap1(X.x + dX, Lx), wrap1(X.y + dY, Ly));
+                if (a.walls_y && (Xn.y < 4.0 || Xn.y > Ly - 5.0)) bad = 1;   // supports stay off the walls
             }
         }
         if (bad && own) atomicExch(&a.ctl->err_body, 1);

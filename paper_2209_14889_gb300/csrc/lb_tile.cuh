@@ -105,6 +105,30 @@ __device__ __forceinline__ float2 ld_fld2(const void* src, long long NP, int pla
     return make_float2(__uint_as_float((unsigned)lo << 16), __uint_as_float((unsigned)hi << 16));
 }
 
+// Walls in y (App. C, half-way bounce-back): the walls sit at y = -1/2 and y = ny - 1/2, and a
+// row beyond them is the mirror image of the row inside: zero-gradient fields (sigma, P and the
+// Ericksen stress) copy their image, the velocity (zero at the wall) takes it negated.
+__device__ __forceinline__ int mirror_row(int y, int ny)
+{
+    for (int k = 0; k < 8 && (y < 0 || y >= ny); ++k) y = y < 0 ? -1 - y : 2 * ny - 1 - y;
+    return y < 0 ? 0 : (y >= ny ? ny - 1 : y);   // rows this far out are never read
+}
+
+// Rows of a staged region (first row at y = yr, width W, nplanes planes of stride PS, value sign
+// sgn) that lie beyond a wall take the value of their mirror row, where that row is in the region.
+__device__ __forceinline__ void mirror_ghost_rows(float* f, int PS, int nplanes, int W, int H, int yr, int ny,
+                                                  float sgn)
+{
+    for (int q = threadIdx.x; q < W * H; q += NT) {
+        const int ly = q / W, lx = q - ly * W;
+        const int y = yr + ly;
+        if (y >= 0 && y < ny) continue;
+        const int lm = mirror_row(y, ny) - yr;
+        if (lm < 0 || lm >= H) continue;
+        for (int c = 0; c < nplanes; ++c) f[c * PS + ly * W + lx] = sgn * f[c * PS + lm * W + lx];
+    }
+}
+
 // ---- A: wrapped index tables, f_IB cleared, P staged with a 4-cell halo and sigma with 3 ----
 // With nx even every staged row starts at an even column (x0 - 4, wrapped), so the rows are read
 // as aligned pairs that never straddle the periodic seam; each thread issues all its loads
@@ -119,7 +143,7 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
     const long long NP = a.plane;
     const void* src = a.src;
     for (int i = tid; i < R4W; i += NT) m.sXi[i] = wrapn(x0 - 4 + i, nx);
-    for (int i = tid; i < G::R4H; i += NT) m.sYi[i] = wrapn(y0 - 4 + i, ny);
+    for (int i = tid; i < G::R4H; i += NT) m.sYi[i] = a.walls_y ? mirror_row(y0 - 4 + i, ny) : wrapn(y0 - 4 + i, ny);
     for (int i = tid; i < 2 * G::R2; i += NT) m.sFib[i] = 0.f;
     __syncthreads();
     if ((nx & 1) == 0) {
@@ -410,6 +434,7 @@ __device__ __forceinline__ void region_cell(int k, int& lx, int& ly)
 // D2Q9 (Sec. II A): c_n, n = 0..8
 __device__ constexpr int C_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int C_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ constexpr int C_OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};   // c_opp(n) = -c_n
 
 // One TX x TY tile (tile coordinates bx, by) of the step, one cell per thread and iteration;
 // sm: TileGeo<TX, TY>::SMEM_BYTES of shared memory.  Used by the sweep comparison and kept as the
@@ -433,6 +458,8 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const void* src = a.src;
 
     stage<PREC, COH, TX, TY, SCALAR>(a, m, x0, y0);
+    // a tile whose staged rows reach beyond a wall (uniform over the CTA)
+    const bool wall = a.walls_y && (y0 - 4 < 0 || y0 + TY + 4 > ny);
 
     // ---- B: molecular field and Ericksen stress on the halo-3 region (not in the scalar model)
     for (int k = tid; k < (SCALAR ? 0 : R3); k += NT) {
@@ -449,6 +476,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
 #pragma unroll
             for (int c = 0; c < 4; ++c) m.sE[c * R3 + i] = E[c];
         }
+    }
+
+    if (wall && !SCALAR && ph.ericksen) {
+        __syncthreads();
+        mirror_ghost_rows(m.sE, R3, 4, R3W, G::R3H, y0 - 3, ny, 1.f);   // read in C, after the gather's barrier
     }
 
     // The state at t was written two kernels back; the node forces, ring boxes, step counter and
@@ -505,7 +537,20 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
                 out[n] = d[n] + D[n];
             }
-            st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
+            const int gy = y0 + ly - 2;
+            if (PREC == PREC_FP32 && wall && (gy == 0 || gy == ny - 1)) {
+                // half-way bounce-back (FP32 state): a population that would leave through a
+                // wall comes back into its own cell as the opposite population
+                float* dd = reinterpret_cast<float*>(dst);
+#pragma unroll
+                for (int n = 0; n < 9; ++n) {
+                    const int yd = gy + C_CY[n];
+                    if (yd < 0 || yd >= ny) dd[C_OPP[n] * NP + g] = out[n];
+                    else dd[n * NP + gd[n]] = out[n];
+                }
+            } else {
+                st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
+            }
             if (readout) {
                 float dsum = 0.f;
                 double jxs = 0.0, jys = 0.0;
@@ -528,6 +573,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     if (MODE == MODE_MOMENTS) {
         moments_out(a, m, x0, y0);
         return;
+    }
+    if (wall) {
+        // u beyond a wall: the negated image (zero velocity at the wall)
+        mirror_ghost_rows(m.sM + R2, R2, 2, R2W, G::R2H, y0 - 2, ny, -1.f);
+        __syncthreads();
     }
 
     // ---- D: predictor on the halo-1 region --------------------------------------------------
@@ -561,6 +611,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         }
     }
     __syncthreads();
+    if (wall) {
+        // the predictor beyond a wall: the image (zero gradient of sigma and P)
+        mirror_ghost_rows(m.sY, R1, SCALAR ? 3 : 5, R1W, G::R1H, y0 - 1, ny, 1.f);
+        __syncthreads();
+    }
 
     // ---- E: corrector, field stores, box writes, readout sums -------------------------------
     const unsigned bmask = (unsigned)m.sScan[NT / 32 + 1];

@@ -44,7 +44,8 @@ class lb_params(ctypes.Structure):
                 ("P_cap", ctypes.c_double), ("director_angle", ctypes.c_double),
                 ("ericksen", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32),
-                ("diffusion_substeps", ctypes.c_int32), ("model", ctypes.c_int32)]
+                ("diffusion_substeps", ctypes.c_int32), ("model", ctypes.c_int32),
+                ("walls_y", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class lb_ring(ctypes.Structure):
@@ -164,7 +165,8 @@ def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4
                      P_cap=w.get("P_cap", 0.99), director_angle=w["director_angle"],
                      ericksen=w.get("ericksen", 1), precision=precision,
                      readout_every=w.get("every", 10), max_samples=max_samples,
-                     diffusion_substeps=w.get("diffusion_substeps", 0), model=w.get("model", LB_MODEL_TENSORIAL))
+                     diffusion_substeps=w.get("diffusion_substeps", 0), model=w.get("model", LB_MODEL_TENSORIAL),
+                     walls_y=w.get("walls_y", 0))
 
 
 def stiffness_table(P_cap: float = 0.99) -> np.ndarray:

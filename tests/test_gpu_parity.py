@@ -494,3 +494,62 @@ def test_scalar_model_rejections():
     with pytest.raises(lb.LBError):
         lb.Batch([s])
     s.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Walls in y (App. C): half-way bounce-back, zero-gradient sigma and P, zero velocity
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nx,ny,rings", [
+    (64, 48, [W.ring(20, 4.0, (32.3, 24.1), pull_force=1e-3, pull_angle=1.2)]),   # pulled towards a wall
+    (40, 37, [W.ring(16, 3.0, (20.3, 18.2), pull_force=1e-3, pull_angle=0.3)]),   # ragged top tile row
+    (40, 12, []),                                                                  # one tile row, both walls
+])
+def test_walls_vs_oracle(nx, ny, rings):
+    w = W.make(nx, ny, rings=rings, seed=4, walls_y=1, steps=80)
+    got, ref = run_both(w, 80)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, len(rings))
+
+
+def test_walls_scalar_model_vs_oracle_and_node_tail_bitwise():
+    lb = _gpu()
+    w = W.make(64, 48, rings=[W.ring(20, 4.0, (30.7, 22.9), pull_force=1e-3, pull_angle=0.9)], seed=6,
+               walls_y=1, steps=60, **W.scalar_physics())
+    sim = O.Sim.from_workload(w)
+    sim.step(60, every=10)
+    out = []
+    for tail in (True, False):
+        s = lb.Solver.from_workload(w)
+        s.set_node_tail(tail)
+        s.step(60)
+        s.sync()
+        out.append(({k: s.readout(k, device=False) for k in SCALAR_FIELDS}, s.nodes(), s.series()))
+        s.close()
+    for k in SCALAR_FIELDS:
+        assert np.array_equal(out[0][0][k], out[1][0][k]), k
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    ref = dict(fields={k: v for k, v in sim.fields().items() if k in SCALAR_FIELDS},
+               series=np.array(sim.series), X=sim.X.copy())
+    got = dict(fields={k: v.astype(np.float64) for k, v in out[0][0].items()}, series=out[0][2], X=out[0][1])
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+def test_walls_rejections():
+    lb = _gpu()
+    near = W.make(48, 40, rings=[W.ring(12, 3.0, (24.0, 6.5))], seed=2, walls_y=1)
+    with pytest.raises(lb.LBError):
+        lb.Solver.from_workload(near)                     # a node within 5 cells of a wall
+    w = W.make(48, 40, rings=[], seed=2, walls_y=1)
+    for over in (dict(precision=lb.LB_FP16_BF16),):
+        with pytest.raises(lb.LBError):
+            lb.Solver(lb.params_from_workload(w, **over))
+    with pytest.raises(lb.LBError):
+        lb.Solver(lb.params_from_workload(dict(w, Dp=0.3, diffusion_substeps=2)))
+    s = lb.Solver.from_workload(w)
+    with pytest.raises(lb.LBError):
+        s.set_kernel(lb.LB_KERNEL_PAIR)
+    s.close()
