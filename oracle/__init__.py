@@ -12,6 +12,7 @@ the plain h_n (not shifted); node positions are unwrapped FP64 ``[n_nodes, 2]``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass, field
@@ -50,7 +51,8 @@ class _Params(ctypes.Structure):
 class _Ring(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("k_spring", ctypes.c_double), ("eps_angle", ctypes.c_double),
-                ("l_eq", ctypes.c_double), ("pull_x", ctypes.c_double), ("pull_y", ctypes.c_double)]
+                ("l_eq", ctypes.c_double), ("pull_x", ctypes.c_double), ("pull_y", ctypes.c_double),
+                ("trap_k", ctypes.c_double), ("trap_x", ctypes.c_double), ("trap_y", ctypes.c_double)]
 
 
 class _Diag(ctypes.Structure):
@@ -133,10 +135,54 @@ class Ring:
     l_eq: float
     pull_x: float = 0.0
     pull_y: float = 0.0
+    trap_k: float = 0.0      # Eq. Utrap at the current step: k_trap(t) and R_ext(t)
+    trap_x: float = 0.0
+    trap_y: float = 0.0
+    protocol: object = None  # TrapProtocol or None
 
     def c(self) -> _Ring:
         return _Ring(self.n_nodes, 0, self.k_spring, self.eps_angle, self.l_eq, self.pull_x,
-                     self.pull_y)
+                     self.pull_y, self.trap_k, self.trap_x, self.trap_y)
+
+
+@dataclass
+class TrapProtocol:
+    """The pulling protocol of Eq. Utrap (App. C): the trap turns on over the equilibration, moves
+    by d = (dx, dy) from the initial centre of mass R0 during `pull` steps, and turns off after.
+    Every transition is a sigmoid of width `width` steps (the paper gives only the width and the
+    equilibration time; this is the reading, taken from the transitions it names):
+      s(t; c)  = 1 / (1 + exp(-8 (t - c) / width))           (2 % to 98 % within width steps)
+      k(t)     = k_max s(t; width / 2) (1 - s(t; t_eq + pull + width / 2))
+      g(t)     = (width / (8 pull)) [sp(8 (t - t_eq) / width) - sp(8 (t - t_eq - pull) / width)],
+                 sp(z) = log(1 + e^z): the integral of s(t; t_eq) - s(t; t_eq + pull) over pull
+                 (the trap's speed rises and falls by sigmoids), 0 before, 1 after
+      R_ext(t) = R0 + d g(t)."""
+    k_max: float
+    dx: float
+    dy: float
+    t_eq: float = 30.0
+    pull: float = 100.0
+    width: float = 30.0
+    x0: float = 0.0
+    y0: float = 0.0
+
+    def s(self, t, c):
+        return 1.0 / (1.0 + math.exp(-8.0 * (t - c) / self.width))
+
+    @staticmethod
+    def sp(z):
+        return z + math.log1p(math.exp(-z)) if z > 0 else math.log1p(math.exp(z))
+
+    def k(self, t):
+        return self.k_max * self.s(t, self.width / 2) * (1.0 - self.s(t, self.t_eq + self.pull + self.width / 2))
+
+    def g(self, t):
+        a = 8.0 / self.width
+        return (self.sp(a * (t - self.t_eq)) - self.sp(a * (t - self.t_eq - self.pull))) / (a * self.pull)
+
+    def ext(self, t):
+        g = self.g(t)
+        return self.x0 + self.dx * g, self.y0 + self.dy * g
 
 
 def params_from_workload(w: dict) -> Params:
@@ -283,11 +329,18 @@ class Sim:
             P += w["noise"]
         rings, Xs = [], []
         for r in w["rings"]:
+            Xr = np.asarray(r["X"], dtype=np.float64)
+            tp = r.get("trap")
+            prot = None
+            if tp is not None:
+                prot = TrapProtocol(k_max=tp["k"], dx=tp["dx"], dy=tp["dy"], t_eq=tp.get("t_eq", 30.0),
+                                    pull=tp.get("pull", 100.0), width=tp.get("width", 30.0),
+                                    x0=float(Xr[:, 0].mean()), y0=float(Xr[:, 1].mean()))
             rings.append(Ring(n_nodes=len(r["X"]), k_spring=r["k_spring"],
                               eps_angle=r["eps_angle"], l_eq=r["l_eq"],
                               pull_x=r["pull_force"] * np.cos(r["pull_angle"]),
-                              pull_y=r["pull_force"] * np.sin(r["pull_angle"])))
-            Xs.append(np.asarray(r["X"], dtype=np.float64))
+                              pull_y=r["pull_force"] * np.sin(r["pull_angle"]), protocol=prot))
+            Xs.append(Xr)
         X = np.concatenate(Xs) if Xs else np.zeros((0, 2))
         return Sim(p, rings, h, sigma, P, X)
 
@@ -300,6 +353,13 @@ class Sim:
         rc = _rings_c(self.rings)
         nr = len(self.rings)
         for _ in range(n):
+            if any(r.protocol is not None for r in self.rings):
+                # Eq. Utrap at this step
+                for r in self.rings:
+                    if r.protocol is not None:
+                        r.trap_k = r.protocol.k(self.t)
+                        r.trap_x, r.trap_y = r.protocol.ext(self.t)
+                rc = _rings_c(self.rings)
             rec = every > 0 and self.t % every == 0
             d = _Diag()
             fr = np.zeros(2 * max(nr, 1))

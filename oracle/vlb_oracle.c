@@ -165,9 +165,11 @@ double orc_ring_energy(const orc_ring* g, const double* X)
         U += g->eps_angle * (1.0 + cg);
         cx += X[2 * a]; cy += X[2 * a + 1];
     }
-    /* Reading Q15: the trap of Eq. Utrap is replaced by a constant pull F on R_com,
-     * whose potential is -F . R_com. */
+    /* The constant pull F on R_com (reading Q15), potential -F . R_com, and the harmonic trap
+     * of Eq. Utrap, k_trap / 2 |R_ext - R_com|^2 (R_com the plain mean of the positions). */
     U -= g->pull_x * cx / N + g->pull_y * cy / N;
+    const double ex = g->trap_x - cx / N, ey = g->trap_y - cy / N;
+    U += 0.5 * g->trap_k * (ex * ex + ey * ey);
     return U;
 }
 
@@ -200,8 +202,15 @@ void orc_node_forces(const orc_ring* g, const double* X, double* f)
         f[2 * b] -= e * dcdqx;  f[2 * b + 1] -= e * dcdqy;
         f[2 * a] += e * (dcdpx + dcdqx);  f[2 * a + 1] += e * (dcdpy + dcdqy);
     }
+    /* the pull and the trap act on R_com; dR_com / dR_a = 1 / N */
+    double cx = 0.0, cy = 0.0;
+    for (int a = 0; a < N; ++a) { cx += X[2 * a]; cy += X[2 * a + 1]; }
+    cx /= N;
+    cy /= N;
+    const double tx = g->trap_k * (g->trap_x - cx) / N, ty = g->trap_k * (g->trap_y - cy) / N;
     for (int a = 0; a < N; ++a) {
         f[2 * a] += g->pull_x / N;  f[2 * a + 1] += g->pull_y / N;
+        f[2 * a] += tx;  f[2 * a + 1] += ty;
     }
 }
 

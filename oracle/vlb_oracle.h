@@ -47,6 +47,7 @@ typedef struct orc_ring {
     int32_t n_nodes, pad_;
     double k_spring, eps_angle, l_eq;       /* Eq. Const: spring and angle terms              */
     double pull_x, pull_y;                  /* constant total pull force on the ring          */
+    double trap_k, trap_x, trap_y;          /* Eq. Utrap at this step: k_trap(t), R_ext(t)    */
 } orc_ring;
 
 /* Diagnostics of the state at time t (the input of the step). */
@@ -66,7 +67,7 @@ void orc_stiffness(const orc_params* p, double Px, double Py, double* C);
 double orc_phi(double r);
 /* Lagrangian node forces f_a = -grad U (Eq. Const without the trap; constant pull). */
 void orc_node_forces(const orc_ring* ring, const double* X, double* f);
-/* Energy U of one ring (spring + angle + pull potential -F.R_com), for finite-difference pins. */
+/* Energy U of one ring (spring + angle + trap + pull potential -F.R_com), for finite-difference pins. */
 double orc_ring_energy(const orc_ring* ring, const double* X);
 /* Spread node forces onto the lattice: fib[2][ny][nx] is overwritten. */
 void orc_spread(const orc_params* p, int n_nodes, const double* X, const double* f, double* fib);

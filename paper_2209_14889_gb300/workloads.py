@@ -38,13 +38,16 @@ def scalar_physics(C: float = 1.875e-3) -> dict:
 
 
 def ring(n_nodes: int, radius: float, centre, k_spring=0.1, eps_angle=0.01, pull_force=1e-3,
-         pull_angle=0.0, phase=0.0) -> dict:
-    """A closed ring of n_nodes points on a circle (node a at angle phase + 2 pi a / N)."""
+         pull_angle=0.0, phase=0.0, trap=None) -> dict:
+    """A closed ring of n_nodes points on a circle (node a at angle phase + 2 pi a / N).
+    trap: optional harmonic trap of Eq. Utrap, dict(k=k_max, dx=, dy=, t_eq=30, pull=100,
+    width=30) (steps): it holds the ring at its initial centre of mass, drags it by (dx, dy)
+    over `pull` steps after `t_eq` and lets go."""
     a = phase + 2.0 * np.pi * np.arange(n_nodes) / n_nodes
     X = np.stack([centre[0] + radius * np.cos(a), centre[1] + radius * np.sin(a)], axis=1)
     l_eq = float(np.hypot(*(X[1] - X[0])))
     return dict(X=X, k_spring=k_spring, eps_angle=eps_angle, l_eq=l_eq, pull_force=pull_force,
-                pull_angle=pull_angle, radius=radius, centre=tuple(centre))
+                pull_angle=pull_angle, radius=radius, centre=tuple(centre), trap=trap)
 
 
 def make(nx: int, ny: int, rings=(), seed: int = 1, noise_amp: float = 0.05, steps: int = 100,

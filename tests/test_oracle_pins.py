@@ -252,6 +252,42 @@ def test_node_forces_are_minus_gradient_of_energy():
     assert np.allclose(f.sum(0), [1e-3, -2e-3], atol=1e-15)
 
 
+def test_trap_force_is_minus_gradient_of_eq_utrap():
+    # Eq. Utrap: k/2 |R_ext - R_com|^2 with R_com the mean of the nodes; its force on node a is
+    # k (R_ext - R_com) / N, the same on every node
+    rng = np.random.default_rng(10)
+    w = W.ring(10, 2.5, (4.0, 5.0))
+    X = w["X"] + rng.normal(scale=0.2, size=w["X"].shape)
+    ring = O.Ring(10, k_spring=0.1, eps_angle=0.01, l_eq=w["l_eq"], trap_k=0.03, trap_x=5.1, trap_y=4.2)
+    f = O.node_forces(ring, X)
+    h = 1e-5
+    for a in range(10):
+        for c in range(2):
+            Xp = X.copy(); Xp[a, c] += h
+            Xm = X.copy(); Xm[a, c] -= h
+            g = (O.ring_energy(ring, Xp) - O.ring_energy(ring, Xm)) / (2 * h)
+            assert abs(f[a, c] + g) < 1e-7 * max(1e-3, abs(g)), (a, c)
+    com = X.mean(0)
+    assert np.allclose(f.sum(0), 0.03 * (np.array([5.1, 4.2]) - com), rtol=1e-12, atol=1e-15)
+
+
+def test_trap_protocol_limits_and_speed():
+    # the reading of the sigmoid protocol: off at first, holding through the equilibration,
+    # moving by d over `pull` steps with a speed that rises and falls by sigmoids of the given
+    # width, then off; the trap's displacement is the integral of its speed
+    tp = O.TrapProtocol(k_max=2e-3, dx=6.0, dy=-2.0, t_eq=30, pull=120, width=30, x0=10.0, y0=20.0)
+    assert tp.g(-300) < 1e-12 and abs(tp.g(1000) - 1.0) < 1e-12
+    ts = np.arange(-50, 400, 0.5)
+    g = np.array([tp.g(t) for t in ts])
+    assert np.all(np.diff(g) >= -1e-15)
+    for t in (10.0, 30.0, 75.0, 150.0, 170.0):
+        dg = (tp.g(t + 1e-4) - tp.g(t - 1e-4)) / 2e-4
+        assert abs(dg - (tp.s(t, 30) - tp.s(t, 150)) / 120) < 1e-9
+    assert abs(tp.k(90) - 2e-3) < 1e-8 and tp.k(-60) < 1e-9 and tp.k(300) < 1e-9
+    assert abs(tp.s(15 + 15, 15 + 15) - 0.5) < 1e-15 and tp.s(0, 15) < 0.02 and tp.s(30, 15) > 0.98
+    assert np.allclose(tp.ext(1000), (16.0, 18.0)) and np.allclose(tp.ext(-300), (10.0, 20.0))
+
+
 # ----------------------------------------------------------------------------------------
 # Lattice Boltzmann hydrodynamics (Sec. II A)
 # ----------------------------------------------------------------------------------------
