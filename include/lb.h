@@ -109,6 +109,13 @@ typedef struct lb_ring {
     double k_spring, eps_angle;     /* Eq. Const: spring and angle stiffness                   */
     double l_eq;                    /* spring rest length                                      */
     double pull_force, pull_angle;  /* constant total pull on the ring, split over its nodes  */
+    /* Harmonic trap of Eq. Utrap, k(t)/2 |R_ext(t) - R_com|^2, off when trap_k = 0.  Protocol
+     * (App. C: sigmoid transitions of trap_width steps): with s(t; c) = 1 / (1 + exp(-8 (t - c) /
+     * trap_width)), k(t) = trap_k s(t; trap_width / 2) (1 - s(t; trap_t_eq + trap_pull +
+     * trap_width / 2)); the trap starts at the initial centre of mass R0 and moves to
+     * R0 + (trap_dx, trap_dy) with a speed proportional to s(t; trap_t_eq) - s(t; trap_t_eq +
+     * trap_pull) (t in steps).  Its force k (R_ext - R_com) / N acts on every node. */
+    double trap_k, trap_dx, trap_dy, trap_t_eq, trap_pull, trap_width;
 } lb_ring;
 
 typedef struct lb_handle lb_handle;

@@ -350,7 +350,7 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
         const int2 w0 = make_int2(-1, 0);
         if ((e = cudaMalloc(&h->node_work, sizeof(int2))) != cudaSuccess ||
             (e = cudaMemcpy(h->node_work, &w0, sizeof(int2), cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMalloc(&h->node_partials, sizeof(double) * 8)) != cudaSuccess) {
+            (e = cudaMalloc(&h->node_partials, sizeof(double) * NODE_PARTIALS)) != cudaSuccess) {
             rc = cuda_fail(nullptr, e, "cudaMalloc(node work)");
             return bail(rc);
         }
@@ -429,7 +429,11 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
         const lb_ring& g = rings[r];
         if (g.n_nodes < 3 || g.n_nodes > 1024) return fail(h, LB_EINVAL, "ring %d: 3 <= n_nodes <= 1024", r);
         if (!(g.l_eq > 0.0) || g.k_spring < 0.0) return fail(h, LB_EINVAL, "ring %d: bad spring", r);
-        double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300;
+        if (!(g.trap_k >= 0.0) || (g.trap_k > 0.0 && !(g.trap_width > 0.0 && g.trap_pull > 0.0 &&
+                                                       std::isfinite(g.trap_dx) && std::isfinite(g.trap_dy) &&
+                                                       std::isfinite(g.trap_t_eq))))
+            return fail(h, LB_EINVAL, "ring %d: bad trap (k >= 0; width, pull > 0)", r);
+        double mnx = 1e300, mxx = -1e300, mny = 1e300, mxy = -1e300, sdx = 0.0, sdy = 0.0;
         const double* P = xy + 2 * (size_t)off;
         for (int k = 0; k < g.n_nodes; ++k) {
             double dx = P[2 * k] - P[0], dy = P[2 * k + 1] - P[1];
@@ -437,6 +441,8 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
             dy -= ny * std::floor(dy / ny + 0.5);
             mnx = std::fmin(mnx, dx); mxx = std::fmax(mxx, dx);
             mny = std::fmin(mny, dy); mxy = std::fmax(mxy, dy);
+            sdx += dx;
+            sdy += dy;
             if (!std::isfinite(P[2 * k]) || !std::isfinite(P[2 * k + 1]))
                 return fail(h, LB_EINVAL, "ring %d: non-finite node", r);
             if (h->p.walls_y && (P[2 * k + 1] < 5.0 || P[2 * k + 1] > ny - 6.0))
@@ -459,6 +465,19 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
         RingDev& d = rd[r];
         d.n_nodes = g.n_nodes;
         d.node_off = off;
+        // the trap: protocol, initial centre of mass (node 0 plus the mean minimum-image offset,
+        // wrapped), no force before the set-up pass below
+        d.trap_k = g.trap_k;
+        d.trap_dx = g.trap_dx;
+        d.trap_dy = g.trap_dy;
+        d.trap_t_eq = g.trap_t_eq;
+        d.trap_pull = g.trap_pull;
+        d.trap_w = g.trap_width;
+        d.trap_x0 = P[0] + sdx / g.n_nodes;
+        d.trap_y0 = P[1] + sdy / g.n_nodes;
+        d.trap_x0 -= nx * std::floor(d.trap_x0 / nx);
+        d.trap_y0 -= ny * std::floor(d.trap_y0 / ny);
+        d.trap_f[0] = d.trap_f[1] = make_float2(0.f, 0.f);
         d.k_spring = g.k_spring;
         d.eps_angle = g.eps_angle;
         d.l_eq = g.l_eq;
@@ -492,7 +511,7 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
     CK(h, cudaMalloc(&h->ring_cta0, sizeof(int) * cta0.size()));
     CK(h, cudaMalloc(&h->ring_ctas, sizeof(int) * nctas.size()));
     CK(h, cudaMalloc(&h->ring_tickets, sizeof(unsigned) * nctas.size()));
-    CK(h, cudaMalloc(&h->node_partials, sizeof(double) * 8 * work.size()));
+    CK(h, cudaMalloc(&h->node_partials, sizeof(double) * NODE_PARTIALS * work.size()));
     CK(h, cudaMemcpy(h->node_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->ring_cta0, cta0.data(), sizeof(int) * cta0.size(), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->ring_ctas, nctas.data(), sizeof(int) * nctas.size(), cudaMemcpyHostToDevice));

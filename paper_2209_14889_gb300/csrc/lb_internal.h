@@ -30,6 +30,11 @@ struct RingDev {
                                   // its later tiles still run keeps them on the box of step t
     int cap_w, cap_h;             // capacity of the box buffers
     long long box_off;            // offset (floats) of this ring's boxes in the box buffers
+    // harmonic trap (Eq. Utrap; trap_k = 0: none): protocol parameters, the initial centre of
+    // mass, and the force on each node for the steps with even and odd t (written by the node
+    // update of the step before, read by the spreading: the slots alternate like the boxes)
+    double trap_k, trap_dx, trap_dy, trap_t_eq, trap_pull, trap_w, trap_x0, trap_y0;
+    float2 trap_f[2];
 };
 
 __host__ __device__ inline int4 ring_box(const RingDev& R, long long t) { return R.box[t & 1]; }
@@ -65,6 +70,7 @@ struct Ctl {
 
 // Node kernel geometry: NB owned nodes per CTA, NODE_THREADS >= NB + 4 threads.
 constexpr int NB = 60;
+constexpr int NODE_PARTIALS = 10;
 constexpr int NODE_THREADS = 64;
 
 struct NodeArgs {
@@ -75,7 +81,8 @@ struct NodeArgs {
     const int* ring_cta0;        // per ring: first CTA, number of CTAs
     const int* ring_ctas;
     unsigned* ring_tickets;      // per ring: arrival counter
-    double* node_partials;       // per CTA: F_rest (2), COM (2), box min/max (4)
+    double* node_partials;       // per CTA (NODE_PARTIALS): F_rest (2), COM (2), box min/max (4),
+                                 // COM of the advanced positions (2)
     const double2* X;            // FP64 master node positions, wrapped into [0, n) (read)
     double2* X_out;              // the advanced positions (written; a different buffer than X when
                                  // advancing: other CTAs read their halo nodes from X meanwhile)

@@ -92,6 +92,18 @@ __device__ __forceinline__ bool interp_box(const float* box, const RingDev& R, i
     return true;
 }
 
+// The trap protocol at step t (doubles): k(t) and the trap's fraction g(t) of its way, from the
+// sigmoids s(t; c) = 1 / (1 + exp(-8 (t - c) / w)).
+__device__ __forceinline__ double trap_sigmoid(double t, double c, double w) { return 1.0 / (1.0 + exp(-8.0 * (t - c) / w)); }
+__device__ __forceinline__ double trap_softplus(double z) { return z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z)); }
+__device__ __forceinline__ void trap_at(const RingDev& R, double t, double& k, double& g)
+{
+    const double w = R.trap_w, te = R.trap_t_eq, T = R.trap_pull;
+    k = R.trap_k * trap_sigmoid(t, 0.5 * w, w) * (1.0 - trap_sigmoid(t, te + T + 0.5 * w, w));
+    const double a = 8.0 / w;
+    g = (trap_softplus(a * (t - te)) - trap_softplus(a * (t - te - T))) / (a * T);
+}
+
 __device__ __forceinline__ int half_wrap(int d, int n)   // d in (-n, n) -> [-n/2, n/2)
 {
     if (d >= n - n / 2) d -= n;
@@ -272,6 +284,12 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem&
         }
         __syncthreads();
         int mm[4] = {1 << 30, 1 << 30, 1 << 30, 1 << 30};   // min x, -max x, min y, -max y
+        const bool trap = R.trap_k > 0.0;
+        double cn[2] = {0.0, 0.0};                          // advanced positions, for the trap
+        if (own && trap) {
+            cn[0] = mimg1(Xn.x - (double)bx0, Lx);
+            cn[1] = mimg1(Xn.y - (double)by0, Ly);
+        }
         if (own) {
             // f_a = -dU/dR_a: springs (a, a+1) and (a-1, a); angle terms at a-1 (a is its next),
             // a, a+1 (a is its prev); the pull
@@ -292,10 +310,13 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem&
         }
         cta_reduce<4, int>(mm, ired, true);
         if (readout) cta_reduce<4, double>(acc, dred, false);
-        double* np_ = a.node_partials + (long long)cta * 8;
+        if (trap) cta_reduce<2, double>(cn, dred, false);
+        double* np_ = a.node_partials + (long long)cta * NODE_PARTIALS;
         if (tid == 0) {
             for (int q = 0; q < 4; ++q) np_[q] = acc[q];
             for (int q = 0; q < 4; ++q) np_[4 + q] = (double)mm[q];
+            np_[8] = cn[0];
+            np_[9] = cn[1];
             __threadfence();
             const unsigned prev = atomicAdd(&a.ring_tickets[wk.x], 1u);
             s_last = (prev == (unsigned)(a.ring_ctas[wk.x] - 1));
@@ -305,14 +326,25 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem&
             // the ring's last CTA: box of the new positions and the ring's readouts
             __threadfence();
             const int c0 = a.ring_cta0[wk.x], nc = a.ring_ctas[wk.x];
-            double sum[4] = {0.0, 0.0, 0.0, 0.0};
+            double sum[4] = {0.0, 0.0, 0.0, 0.0}, scn[2] = {0.0, 0.0};
             int m[4] = {1 << 30, 1 << 30, 1 << 30, 1 << 30};
             for (int c = 0; c < nc; ++c) {
-                const volatile double* p = a.node_partials + (long long)(c0 + c) * 8;
+                const volatile double* p = a.node_partials + (long long)(c0 + c) * NODE_PARTIALS;
                 for (int q = 0; q < 4; ++q) {
                     sum[q] += p[q];
                     m[q] = min(m[q], (int)p[4 + q]);
                 }
+                scn[0] += p[8];
+                scn[1] += p[9];
+            }
+            if (trap) {
+                // Eq. Utrap at the step the nodes advance to: k (R_ext - R_com) / N on each node
+                const double tn = (double)(t + a.advance);
+                double kt, g;
+                trap_at(R, tn, kt, g);
+                const double ex = mimg1(R.trap_x0 + R.trap_dx * g - ((double)bx0 + scn[0] / n), Lx);
+                const double ey = mimg1(R.trap_y0 + R.trap_dy * g - ((double)by0 + scn[1] / n), Ly);
+                a.rings[wk.x].trap_f[(t + a.advance) & 1] = make_float2((float)(kt * ex / n), (float)(kt * ey / n));
             }
             int w = -m[1] - m[0] + 6, h = -m[3] - m[2] + 6;      // cells min-2 .. max+3
             if (w > R.cap_w || h > R.cap_h) {

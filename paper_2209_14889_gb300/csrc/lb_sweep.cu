@@ -283,6 +283,11 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
                         const int2 cc = a.node_cell[R.node_off + kk];
                         fr = a.node_frac[R.node_off + kk];
                         f = a.node_force[R.node_off + kk];
+                        if (R.trap_k > 0.0) {     // the trap's force, the same on every node
+                            const float2 tf = R.trap_f[t & 1];
+                            f.x += tf.x;
+                            f.y += tf.y;
+                        }
                         // offsets of the node cell from the first C row and the first staged column
                         cy = wrapn(cc.y - gyc0, ny);
                         if (cy > RB) cy -= ny;

@@ -260,6 +260,11 @@ __device__ __forceinline__ void ib_gather(const FusedArgs& a, const TileMem<TX, 
                 const int2 c = a.node_cell[R.node_off + k];
                 fr = a.node_frac[R.node_off + k];
                 f = a.node_force[R.node_off + k];
+                if (R.trap_k > 0.0) {             // the trap's force, the same on every node
+                    const float2 tf = R.trap_f[t & 1];
+                    f.x += tf.x;
+                    f.y += tf.y;
+                }
                 // the image of the node nearest the region: support cells c-1 .. c+2 meet
                 // [0, R2W) iff the offset lies in [-2, R2W]
                 cxr = wrapn(c.x - (x0 - 2), nx);

@@ -52,7 +52,9 @@ class lb_ring(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("k_spring", ctypes.c_double), ("eps_angle", ctypes.c_double),
                 ("l_eq", ctypes.c_double), ("pull_force", ctypes.c_double),
-                ("pull_angle", ctypes.c_double)]
+                ("pull_angle", ctypes.c_double), ("trap_k", ctypes.c_double), ("trap_dx", ctypes.c_double),
+                ("trap_dy", ctypes.c_double), ("trap_t_eq", ctypes.c_double), ("trap_pull", ctypes.c_double),
+                ("trap_width", ctypes.c_double)]
 
 
 _lib = None
@@ -180,6 +182,16 @@ def stiffness_table(P_cap: float = 0.99) -> np.ndarray:
     return out
 
 
+def return_metric(series: np.ndarray, ring: int, d_pull: float, nx: int, ny: int) -> float:
+    """Return = 1 - d_rec / d_pull (Eq. Rec): d_rec is the distance (minimum image) between the
+    ring's centre of mass in the first and the last row of a readout series."""
+    com = series[:, 8 + 4 * ring: 10 + 4 * ring]
+    d = com[-1] - com[0]
+    d[0] -= nx * np.round(d[0] / nx)
+    d[1] -= ny * np.round(d[1] / ny)
+    return 1.0 - float(np.hypot(d[0], d[1])) / d_pull
+
+
 class Solver:
     """One lattice with its rings, driven through the C ABI."""
 
@@ -229,9 +241,13 @@ class Solver:
         arr = (lb_ring * max(1, len(rings)))()
         xy = []
         for i, r in enumerate(rings):
+            tp = r.get("trap") or {}
             arr[i] = lb_ring(n_nodes=len(r["X"]), pad_=0, k_spring=r["k_spring"],
                              eps_angle=r["eps_angle"], l_eq=r["l_eq"],
-                             pull_force=r["pull_force"], pull_angle=r["pull_angle"])
+                             pull_force=r["pull_force"], pull_angle=r["pull_angle"],
+                             trap_k=tp.get("k", 0.0), trap_dx=tp.get("dx", 0.0), trap_dy=tp.get("dy", 0.0),
+                             trap_t_eq=tp.get("t_eq", 30.0), trap_pull=tp.get("pull", 100.0),
+                             trap_width=tp.get("width", 30.0))
             xy.append(np.asarray(r["X"], dtype=np.float64))
         X = np.ascontiguousarray(np.concatenate(xy) if xy else np.zeros((0, 2)))
         _check(self.h, lib().lb_set_body(self.h, len(rings), arr, X.ctypes.data if X.size else None))

@@ -36,10 +36,10 @@ def test_binding_names_match_header():
 
 
 def test_struct_layout_matches_header():
-    # lb_params: 2 int32, 16 doubles, 8 int32 ; lb_ring: 2 int32 + 5 doubles
+    # lb_params: 2 int32, 16 doubles, 8 int32 ; lb_ring: 2 int32 + 11 doubles
     from paper_2209_14889_gb300 import lb
     assert ctypes.sizeof(lb.lb_params) == 8 + 16 * 8 + 32
-    assert ctypes.sizeof(lb.lb_ring) == 8 + 5 * 8
+    assert ctypes.sizeof(lb.lb_ring) == 8 + 11 * 8
 
 
 def test_create_without_gpu_fails_cleanly():

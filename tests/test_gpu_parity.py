@@ -553,3 +553,46 @@ def test_walls_rejections():
     with pytest.raises(lb.LBError):
         s.set_kernel(lb.LB_KERNEL_PAIR)
     s.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Harmonic trap with the sigmoid pulling protocol (Eq. Utrap, App. C), and the Return (Eq. Rec)
+# ------------------------------------------------------------------------------------------
+
+TRAP = dict(k=0.05, dx=4.0, dy=1.0, t_eq=30, pull=120, width=30)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_trap_protocol_vs_oracle(walls):
+    # the paper's experiment in small: the trap holds the ring, drags it by (4, 1) over 120
+    # steps and lets go; the ring then recoils in the viscoelastic fluid
+    lb = _gpu()
+    w = W.make(64, 48, rings=[W.ring(20, 4.0, (24.3, 23.9), pull_force=0.0, trap=TRAP)], seed=8,
+               walls_y=walls, steps=240)
+    got, ref = run_both(w, 240)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+    d_pull = float(np.hypot(TRAP["dx"], TRAP["dy"]))
+    r_gpu = lb.return_metric(got["series"], 0, d_pull, 64, 48)
+    r_orc = lb.return_metric(ref["series"], 0, d_pull, 64, 48)
+    assert abs(r_gpu - r_orc) < 1e-4, (r_gpu, r_orc)
+    # the ring moved with the trap: most of the way, less than all of it
+    assert 0.0 < r_orc < 1.0
+
+
+def test_trap_node_tail_matches_separate_node_kernel_bitwise():
+    lb = _gpu()
+    w = W.make(96, 64, rings=[W.ring(130, 10.0, (40.2, 30.7), pull_force=0.0, trap=TRAP),
+                              W.ring(24, 4.0, (75.1, 40.3), pull_force=1e-3, pull_angle=2.0)], seed=9, steps=0)
+    out = []
+    for tail in (True, False):
+        s = lb.Solver.from_workload(w)
+        s.set_node_tail(tail)
+        s.step(90)
+        s.sync()
+        out.append((s.fields(), s.nodes(), s.series()))
+        s.close()
+    for k in out[0][0]:
+        assert np.array_equal(out[0][0][k], out[1][0][k]), k
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
