@@ -45,7 +45,7 @@ class _Params(ctypes.Structure):
                 ("Gamma", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("P_cap", ctypes.c_double),
                 ("ericksen", ctypes.c_int32), ("walls_y", ctypes.c_int32),
-                ("diffusion_substeps", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("diffusion_substeps", ctypes.c_int32), ("walls_x", ctypes.c_int32)]
 
 
 class _Ring(ctypes.Structure):
@@ -119,12 +119,13 @@ class Params:
     ericksen: int = 1
     walls_y: int = 0
     diffusion_substeps: int = 0
+    walls_x: int = 0
 
     def c(self) -> _Params:
         return _Params(self.nx, self.ny, self.tau, self.rho0, self.K1111, self.K1122, self.K2222,
                        self.K1212, self.eta_p, self.Dp, self.alpha, self.beta, self.xi, self.Gamma,
                        self.kappa, self.P_cap, self.ericksen, self.walls_y,
-                       self.diffusion_substeps, 0)
+                       self.diffusion_substeps, self.walls_x)
 
 
 @dataclass
@@ -197,7 +198,8 @@ def params_from_workload(w: dict) -> Params:
                   K2222=K[2], K1212=K[3], eta_p=eta_p, Dp=w["Dp"], alpha=w["alpha"],
                   beta=w["beta"], xi=w["xi"], Gamma=w["Gamma"], kappa=w["kappa"],
                   P_cap=w.get("P_cap", 0.99), ericksen=w.get("ericksen", 1),
-                  diffusion_substeps=w.get("diffusion_substeps", 0), walls_y=w.get("walls_y", 0))
+                  diffusion_substeps=w.get("diffusion_substeps", 0), walls_y=w.get("walls_y", 0),
+                  walls_x=w.get("walls_x", 0))
 
 
 # ---------------------------------------------------------------------------------------

@@ -38,18 +38,22 @@ enum { BC_NEUMANN = 0, BC_DIRICHLET0 = 1 };
 
 /*
  * Value of component field f at (x, y) with the boundary rule of App. C.
- * x is periodic.  y is periodic unless walls_y, in which case the walls sit half-way
- * between nodes at y = -1/2 and y = ny - 1/2 and a ghost node mirrors its image:
- * zero-gradient (Neumann) fields copy it, zero-value (Dirichlet) fields negate it.
+ * Each axis is periodic unless it has walls (walls_x, walls_y), which sit half-way between
+ * nodes at -1/2 and n - 1/2; a ghost node beyond a wall mirrors its image: zero-gradient
+ * (Neumann) fields copy it, zero-value (Dirichlet) fields negate it (once per mirror).
  * Reading: the paper names the BC types only; mirroring about the half-way wall is the
  * second-order ghost-node form of each.
  */
 static double at(const orc_params* p, const double* f, int x, int y, int bc)
 {
     int nx = p->nx, ny = p->ny;
-    x = wrapi(x, nx);
-    if (!p->walls_y) return f[(size_t)wrapi(y, ny) * nx + x];
     double s = 1.0;
+    if (!p->walls_x) x = wrapi(x, nx);
+    while (x < 0 || x >= nx) {
+        if (x < 0) x = -1 - x; else x = 2 * nx - 1 - x;
+        if (bc == BC_DIRICHLET0) s = -s;
+    }
+    if (!p->walls_y) y = wrapi(y, ny);
     while (y < 0 || y >= ny) {
         if (y < 0) y = -1 - y; else y = 2 * ny - 1 - y;
         if (bc == BC_DIRICHLET0) s = -s;
@@ -226,6 +230,7 @@ void orc_spread(const orc_params* p, int n_nodes, const double* X, const double*
         for (int y = y0 - 1; y <= y0 + 2; ++y) {
             if (p->walls_y && (y < 0 || y >= ny)) continue;
             for (int x = x0 - 1; x <= x0 + 2; ++x) {
+                if (p->walls_x && (x < 0 || x >= nx)) continue;
                 double w = orc_phi(minimg(X[2 * a] - x, nx)) * orc_phi(minimg(X[2 * a + 1] - y, ny));
                 size_t i = (size_t)wrapi(y, ny) * nx + wrapi(x, nx);
                 fib[i] += f[2 * a] * w;
@@ -246,6 +251,7 @@ void orc_interp(const orc_params* p, const double* u, int n_nodes, const double*
         for (int y = y0 - 1; y <= y0 + 2; ++y) {
             if (p->walls_y && (y < 0 || y >= ny)) continue;
             for (int x = x0 - 1; x <= x0 + 2; ++x) {
+                if (p->walls_x && (x < 0 || x >= nx)) continue;
                 double w = orc_phi(minimg(X[2 * a] - x, nx)) * orc_phi(minimg(X[2 * a + 1] - y, ny));
                 size_t i = (size_t)wrapi(y, ny) * nx + wrapi(x, nx);
                 vx += u[i] * w;
@@ -495,13 +501,14 @@ int orc_step(const orc_params* p, const orc_ring* rings, int n_rings,
             hs[n * N + i] = h[n * N + i] - (h[n * N + i] - heq) / tau + S;
         }
     }
-    /* 7. streaming h_n(r + c_n, t+1) = h*_n(r); half-way bounce-back at y walls (App. C). */
+    /* 7. streaming h_n(r + c_n, t+1) = h*_n(r); half-way bounce-back at walls (App. C): a
+     * population whose link crosses a wall returns to its cell as the opposite one. */
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
             for (int n = 0; n < 9; ++n) {
-                int xd = wrapi(x + cxs[n], nx), yd = y + cys[n];
-                if (p->walls_y && (yd < 0 || yd >= ny)) {
+                int xr = x + cxs[n], xd = wrapi(xr, nx), yd = y + cys[n];
+                if ((p->walls_y && (yd < 0 || yd >= ny)) || (p->walls_x && (xr < 0 || xr >= nx))) {
                     h[opp[n] * N + i] = hs[n * N + i];
                 } else {
                     h[n * N + (size_t)wrapi(yd, ny) * nx + xd] = hs[n * N + i];

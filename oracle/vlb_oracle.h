@@ -40,7 +40,7 @@ typedef struct orc_params {
     int32_t walls_y;                        /* 1: halfway bounce-back walls at y=-1/2, ny-1/2 */
     int32_t diffusion_substeps;             /* 0: D_p inside the Heun RHS; s>0: Heun without
                                                diffusion, then s Heun sub-steps of D_p/s      */
-    int32_t pad_;
+    int32_t walls_x;                        /* 1: halfway bounce-back walls at x=-1/2, nx-1/2 */
 } orc_params;
 
 typedef struct orc_ring {

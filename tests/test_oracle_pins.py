@@ -376,6 +376,42 @@ def test_poiseuille_bounce_back_exact_at_magic_tau():
         assert err < tol, (tau, err)
 
 
+def test_poiseuille_between_x_walls_exact_at_magic_tau():
+    # the same flow turned by 90 degrees: walls at x = -1/2, nx - 1/2, force along y
+    tau = 0.5 + math.sqrt(3 / 16)
+    nx, ny, g = 16, 2, 1e-6
+    p = _fluid_only(nx, ny, tau, walls_x=1)
+    fext = np.zeros((2, ny, nx)); fext[1] = g
+    s = O.Sim(p, [], O.equilibrium(np.ones((ny, nx)), np.zeros((2, ny, nx))),
+              np.zeros((3, ny, nx)), np.zeros((2, ny, nx)), np.zeros((0, 2)), fext=fext)
+    nu = (tau - 0.5) / 3
+    s.step(int(25 * nx * nx / nu))
+    x = np.arange(nx)
+    ref = g / (2 * nu) * (x + 0.5) * (nx - 0.5 - x)
+    assert np.abs(s.fields()["uy"][0, :] - ref).max() / ref.max() < 1e-9
+    assert np.abs(s.fields()["ux"]).max() < 1e-13      # zero up to rounding
+
+
+def test_closed_box_conserves_mass_and_damps_a_random_flow():
+    # walls on all four sides (App. C): bounce-back keeps every population inside, so the mass
+    # is exact; with no force the kinetic energy of a random initial flow only decays
+    n = 12
+    p = _fluid_only(n, n, 0.8, walls_x=1, walls_y=1)
+    rng = np.random.default_rng(11)
+    u0 = rng.normal(scale=1e-3, size=(2, n, n))
+    s = O.Sim(p, [], O.equilibrium(np.ones((n, n)), u0), np.zeros((3, n, n)), np.zeros((2, n, n)),
+              np.zeros((0, 2)))
+    m0 = s.h.sum()
+    e_prev = np.inf
+    for _ in range(20):
+        s.step(10)
+        f = s.fields()
+        e = float((f["ux"] ** 2 + f["uy"] ** 2).sum())
+        assert e < e_prev
+        e_prev = e
+    assert abs(s.h.sum() - m0) < 1e-12 * m0
+
+
 # ----------------------------------------------------------------------------------------
 # Polymer stress and orientation dynamics (Eq. StiffCons, Eq. BE)
 # ----------------------------------------------------------------------------------------
