@@ -77,17 +77,17 @@ typedef struct lb_params {
                                     /*   of D_p / s on sigma (needs 8 D_p / s <= 2; FP32 only)  */
     int32_t model;                  /* LB_MODEL_TENSORIAL (0) or LB_MODEL_SCALAR (1), below    */
     int32_t walls_y;                /* 1: walls in y (App. C), below; 0: periodic in y         */
-    int32_t pad_;
+    int32_t walls_x;                /* 1: walls in x, the same; both: the closed box of App. C  */
 } lb_params;
 
 /*
- * Walls in y (App. C; walls_y = 1): no-slip walls half-way between nodes at y = -1/2 and
- * y = ny - 1/2, half-way bounce-back of the populations, zero gradient of sigma^p, P and the
- * Ericksen stress across them (a row beyond a wall mirrors the row inside), zero velocity (the
- * mirrored u is negated); x stays periodic.  Needs the FP32 state, no diffusion sub-steps and the
- * one-cell tile kernel; ring nodes must stay 5 cells from the walls at lb_set_body (else
- * LB_EINVAL) and 4 cells while stepping (else LB_EBODY at lb_sync); batches and the learned
- * stepper take periodic lattices only.
+ * Walls (App. C; walls_y = 1 and/or walls_x = 1): no-slip walls half-way between nodes at
+ * y = -1/2 and y = ny - 1/2 (x = -1/2, nx - 1/2), half-way bounce-back of the populations, zero
+ * gradient of sigma^p, P and the Ericksen stress across them (a cell beyond a wall mirrors the
+ * cell inside), zero velocity (the mirrored u is negated); an axis without walls stays periodic.
+ * Needs the FP32 state, no diffusion sub-steps and the one-cell tile kernel; ring nodes must stay
+ * 5 cells from the walls at lb_set_body (else LB_EINVAL) and 4 cells while stepping (else
+ * LB_EBODY at lb_sync); the learned stepper takes periodic lattices only.
  */
 
 /*

@@ -93,6 +93,7 @@ FusedArgs fused_args(lb_handle* h)
     a.prec = h->p.precision == LB_FP32 ? 0 : 1;
     a.scalar = h->p.model == LB_MODEL_SCALAR ? 1 : 0;
     a.walls_y = h->p.walls_y;
+    a.walls_x = h->p.walls_x;
     a.plane = h->plane;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
@@ -135,6 +136,7 @@ NodeArgs node_args(lb_handle* h, int advance)
     a.nx = h->p.nx;
     a.ny = h->p.ny;
     a.walls_y = h->p.walls_y;
+    a.walls_x = h->p.walls_x;
     a.advance = advance;
     a.n_ctas = h->n_node_ctas;
     a.work = h->node_work;
@@ -263,7 +265,8 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
             return fail(nullptr, LB_EINVAL, "the scalar model needs K2222 = K1111, K1122 = 0, K1212 = K1111 / 2");
     }
     if (p.walls_y != 0 && p.walls_y != 1) return fail(nullptr, LB_EINVAL, "walls_y must be 0 or 1");
-    if (p.walls_y && (p.precision != LB_FP32 || p.diffusion_substeps != 0))
+    if (p.walls_x != 0 && p.walls_x != 1) return fail(nullptr, LB_EINVAL, "walls_x must be 0 or 1");
+    if ((p.walls_y || p.walls_x) && (p.precision != LB_FP32 || p.diffusion_substeps != 0))
         return fail(nullptr, LB_EINVAL, "walls need the FP32 state and no diffusion sub-steps");
     if (p.diffusion_substeps < 0) return fail(nullptr, LB_EINVAL, "diffusion_substeps < 0");
     if (p.diffusion_substeps > 0 && p.precision != LB_FP32)
@@ -445,7 +448,8 @@ int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const doubl
             sdy += dy;
             if (!std::isfinite(P[2 * k]) || !std::isfinite(P[2 * k + 1]))
                 return fail(h, LB_EINVAL, "ring %d: non-finite node", r);
-            if (h->p.walls_y && (P[2 * k + 1] < 5.0 || P[2 * k + 1] > ny - 6.0))
+            if ((h->p.walls_y && (P[2 * k + 1] < 5.0 || P[2 * k + 1] > ny - 6.0)) ||
+                (h->p.walls_x && (P[2 * k] < 5.0 || P[2 * k] > nx - 6.0)))
                 return fail(h, LB_EINVAL, "ring %d: a node within 5 cells of a wall", r);
             double xw = std::fmod(P[2 * k], (double)nx); if (xw < 0) xw += nx; if (xw >= nx) xw -= nx;
             double yw = std::fmod(P[2 * k + 1], (double)ny); if (yw < 0) yw += ny; if (yw >= ny) yw -= ny;
@@ -792,7 +796,7 @@ int lb_set_kernel(lb_handle* h, int32_t kernel)
         return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
     if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.model == LB_MODEL_SCALAR)
         return fail(h, LB_EINVAL, "the scalar model runs on the one-cell tile kernel only");
-    if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.walls_y)
+    if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && (h->p.walls_y || h->p.walls_x))
         return fail(h, LB_EINVAL, "walls run on the one-cell tile kernel only");
     if (kernel == LB_KERNEL_SWEEP && !sweep_eligible(h->p.nx, h->p.ny))
         return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");

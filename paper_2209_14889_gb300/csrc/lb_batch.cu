@@ -401,7 +401,7 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
     for (int i = 0; i < n; ++i) {
         const lb_handle* h = handles[i];
         if (!h || !h->fields_ready || !h->node_work) return LB_ESTATE;
-        if (h->p.precision != LB_FP32 || h->p.model != LB_MODEL_TENSORIAL || h->p.walls_y || h->cur != handles[0]->cur ||
+        if (h->p.precision != LB_FP32 || h->p.model != LB_MODEL_TENSORIAL || h->cur != handles[0]->cur ||
             h->stream != handles[0]->stream)
             return LB_EINVAL;
         for (int k = 0; k < i; ++k)

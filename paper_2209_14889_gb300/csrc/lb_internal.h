@@ -99,6 +99,7 @@ struct NodeArgs {
     int every;
     int nx, ny;
     int walls_y;                 // 1: walls in y; a node closer than 4 cells to one is an error
+    int walls_x;                 // 1: walls in x; the same
     int advance;                 // 0: forces + box only (initial configuration); else the steps
                                  // the positions advance by (1; 15 for a learned jump, the
                                  // velocities on the boxes then carry that factor)
@@ -110,6 +111,7 @@ struct FusedArgs {
     int prec;                    // 0: FP32 state, 1: FP16 populations + BF16 sigma, dP
     int scalar;                  // 1: the scalar model (constant modulus, no P field; FP32 only)
     int walls_y;                 // 1: half-way bounce-back walls at y = -1/2, ny - 1/2 (one-cell tiles, FP32)
+    int walls_x;                 // 1: the same at x = -1/2, nx - 1/2
     long long plane;             // nx * ny
     int nx, ny;
     Phys ph;

@@ -351,7 +351,7 @@ int lb_learned_create(lb_handle* h, lb_net* net, const float* norm, double eps_m
     if (!h || !net || !norm || !out) return LB_EINVAL;
     *out = nullptr;
     if (!h->fields_ready || !h->node_work) return LB_ESTATE;
-    if (h->p.precision != LB_FP32 || h->p.model != LB_MODEL_TENSORIAL || h->p.walls_y || h->p.readout_every % 16 != 0)
+    if (h->p.precision != LB_FP32 || h->p.model != LB_MODEL_TENSORIAL || h->p.walls_y || h->p.walls_x || h->p.readout_every % 16 != 0)
         return LB_EINVAL;
     int32_t nb = 0, nh = 0, nw = 0;
     if (lb_net_shape(net, &nb, &nh, &nw) != LB_OK || nb != 1 || nh != h->p.ny || nw != h->p.nx) return LB_EINVAL;

@@ -245,6 +245,7 @@ __device__ __forceinline__ void node_block(const NodeArgs& a, int cta, NodeSmem&
                 if (!(fabs(dX) < 1.0 && fabs(dY) < 1.0)) bad = 1;
                 Xn = make_double2(wrap1(X.x + dX, Lx), wrap1(X.y + dY, Ly));
                 if (a.walls_y && (Xn.y < 4.0 || Xn.y > Ly - 5.0)) bad = 1;   // supports stay off the walls
+                if (a.walls_x && (Xn.x < 4.0 || Xn.x > Lx - 5.0)) bad = 1;
             }
         }
         if (bad && own) atomicExch(&a.ctl->err_body, 1);

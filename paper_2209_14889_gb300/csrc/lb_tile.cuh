@@ -114,18 +114,21 @@ __device__ __forceinline__ int mirror_row(int y, int ny)
     return y < 0 ? 0 : (y >= ny ? ny - 1 : y);   // rows this far out are never read
 }
 
-// Rows of a staged region (first row at y = yr, width W, nplanes planes of stride PS, value sign
-// sgn) that lie beyond a wall take the value of their mirror row, where that row is in the region.
-__device__ __forceinline__ void mirror_ghost_rows(float* f, int PS, int nplanes, int W, int H, int yr, int ny,
-                                                  float sgn)
+// Cells of a staged region (origin (xr, yr), W x H, nplanes planes of stride PS) that lie beyond
+// a wall take the value of their mirror image, times sgn for each wall crossed, where the image
+// is in the region (images are inside the walls, so no cell is both read and written).
+__device__ __forceinline__ void mirror_ghosts(float* f, int PS, int nplanes, int W, int H, int xr, int yr,
+                                              const FusedArgs& a, float sgn)
 {
     for (int q = threadIdx.x; q < W * H; q += NT) {
         const int ly = q / W, lx = q - ly * W;
-        const int y = yr + ly;
-        if (y >= 0 && y < ny) continue;
-        const int lm = mirror_row(y, ny) - yr;
-        if (lm < 0 || lm >= H) continue;
-        for (int c = 0; c < nplanes; ++c) f[c * PS + ly * W + lx] = sgn * f[c * PS + lm * W + lx];
+        const int x = xr + lx, y = yr + ly;
+        const bool ox = a.walls_x && (x < 0 || x >= a.nx), oy = a.walls_y && (y < 0 || y >= a.ny);
+        if (!ox && !oy) continue;
+        const int mx = (ox ? mirror_row(x, a.nx) : x) - xr, my = (oy ? mirror_row(y, a.ny) : y) - yr;
+        if (mx < 0 || mx >= W || my < 0 || my >= H) continue;
+        const float s = (ox ? sgn : 1.f) * (oy ? sgn : 1.f);
+        for (int c = 0; c < nplanes; ++c) f[c * PS + ly * W + lx] = s * f[c * PS + my * W + mx];
     }
 }
 
@@ -142,11 +145,12 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
     const int nx = a.nx, ny = a.ny;
     const long long NP = a.plane;
     const void* src = a.src;
-    for (int i = tid; i < R4W; i += NT) m.sXi[i] = wrapn(x0 - 4 + i, nx);
+    for (int i = tid; i < R4W; i += NT) m.sXi[i] = a.walls_x ? mirror_row(x0 - 4 + i, nx) : wrapn(x0 - 4 + i, nx);
     for (int i = tid; i < G::R4H; i += NT) m.sYi[i] = a.walls_y ? mirror_row(y0 - 4 + i, ny) : wrapn(y0 - 4 + i, ny);
     for (int i = tid; i < 2 * G::R2; i += NT) m.sFib[i] = 0.f;
     __syncthreads();
-    if ((nx & 1) == 0) {
+    // pairs need consecutive columns: not where mirrored columns (walls in x) enter the tile
+    if ((nx & 1) == 0 && !(a.walls_x && (x0 - 4 < 0 || x0 + TX + 4 > nx))) {
         // P: pairs of the halo-4 rows; sigma: pairs of the rows y0-3 .. y0+TY+2 over the halo-4
         // columns, of which the outermost column on each side is dropped
         constexpr int HP = R4W / 2;                      // pairs per row
@@ -463,8 +467,8 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const void* src = a.src;
 
     stage<PREC, COH, TX, TY, SCALAR>(a, m, x0, y0);
-    // a tile whose staged rows reach beyond a wall (uniform over the CTA)
-    const bool wall = a.walls_y && (y0 - 4 < 0 || y0 + TY + 4 > ny);
+    // a tile whose staged cells reach beyond a wall (uniform over the CTA)
+    const bool wall = (a.walls_y && (y0 - 4 < 0 || y0 + TY + 4 > ny)) || (a.walls_x && (x0 - 4 < 0 || x0 + TX + 4 > nx));
 
     // ---- B: molecular field and Ericksen stress on the halo-3 region (not in the scalar model)
     for (int k = tid; k < (SCALAR ? 0 : R3); k += NT) {
@@ -485,7 +489,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
 
     if (wall && !SCALAR && ph.ericksen) {
         __syncthreads();
-        mirror_ghost_rows(m.sE, R3, 4, R3W, G::R3H, y0 - 3, ny, 1.f);   // read in C, after the gather's barrier
+        mirror_ghosts(m.sE, R3, 4, R3W, G::R3H, x0 - 3, y0 - 3, a, 1.f);   // read in C, after the gather's barrier
     }
 
     // The state at t was written two kernels back; the node forces, ring boxes, step counter and
@@ -542,16 +546,19 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
                 out[n] = d[n] + D[n];
             }
-            const int gy = y0 + ly - 2;
-            if (PREC == PREC_FP32 && wall && (gy == 0 || gy == ny - 1)) {
+            const int gy = y0 + ly - 2, gxo = x0 + lx - 2;
+            if (PREC == PREC_FP32 && wall &&
+                ((a.walls_y && (gy == 0 || gy == ny - 1)) || (a.walls_x && (gxo == 0 || gxo == nx - 1)))) {
                 // half-way bounce-back (FP32 state): a population that would leave through a
                 // wall comes back into its own cell as the opposite population
                 float* dd = reinterpret_cast<float*>(dst);
 #pragma unroll
                 for (int n = 0; n < 9; ++n) {
-                    const int yd = gy + C_CY[n];
-                    if (yd < 0 || yd >= ny) dd[C_OPP[n] * NP + g] = out[n];
-                    else dd[n * NP + gd[n]] = out[n];
+                    const int yd = gy + C_CY[n], xd = gxo + C_CX[n];
+                    if ((a.walls_y && (yd < 0 || yd >= ny)) || (a.walls_x && (xd < 0 || xd >= nx)))
+                        dd[C_OPP[n] * NP + g] = out[n];
+                    else
+                        dd[n * NP + gd[n]] = out[n];
                 }
             } else {
                 st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
@@ -581,7 +588,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     }
     if (wall) {
         // u beyond a wall: the negated image (zero velocity at the wall)
-        mirror_ghost_rows(m.sM + R2, R2, 2, R2W, G::R2H, y0 - 2, ny, -1.f);
+        mirror_ghosts(m.sM + R2, R2, 2, R2W, G::R2H, x0 - 2, y0 - 2, a, -1.f);
         __syncthreads();
     }
 
@@ -618,7 +625,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     __syncthreads();
     if (wall) {
         // the predictor beyond a wall: the image (zero gradient of sigma and P)
-        mirror_ghost_rows(m.sY, R1, SCALAR ? 3 : 5, R1W, G::R1H, y0 - 1, ny, 1.f);
+        mirror_ghosts(m.sY, R1, SCALAR ? 3 : 5, R1W, G::R1H, x0 - 1, y0 - 1, a, 1.f);
         __syncthreads();
     }
 

@@ -45,7 +45,7 @@ class lb_params(ctypes.Structure):
                 ("ericksen", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("readout_every", ctypes.c_int32), ("max_samples", ctypes.c_int32),
                 ("diffusion_substeps", ctypes.c_int32), ("model", ctypes.c_int32),
-                ("walls_y", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("walls_y", ctypes.c_int32), ("walls_x", ctypes.c_int32)]
 
 
 class lb_ring(ctypes.Structure):
@@ -168,7 +168,7 @@ def params_from_workload(w: dict, precision: int = LB_FP32, max_samples: int = 4
                      ericksen=w.get("ericksen", 1), precision=precision,
                      readout_every=w.get("every", 10), max_samples=max_samples,
                      diffusion_substeps=w.get("diffusion_substeps", 0), model=w.get("model", LB_MODEL_TENSORIAL),
-                     walls_y=w.get("walls_y", 0))
+                     walls_y=w.get("walls_y", 0), walls_x=w.get("walls_x", 0))
 
 
 def stiffness_table(P_cap: float = 0.99) -> np.ndarray:

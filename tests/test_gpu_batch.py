@@ -250,3 +250,23 @@ def test_batch_rejects_bad_handles():
         lb.Batch([a, d])
     for s in (a, c, d):
         s.close()
+
+
+def test_batch_with_walls_and_traps_matches_single_handles_bitwise():
+    # the paper's protocol in a batch: walls in y, trapped rings dragged at different D_p
+    lb = _gpu()
+    trap = dict(k=0.05, dx=3.0, dy=0.5, t_eq=30, pull=60, width=30)
+    ws = [W.make(64 + 16 * i, 48, rings=[W.ring(20, 4.0, (20.3 + i, 23.7), pull_force=0.0, trap=trap)],
+                 seed=50 + i, walls_y=1, walls_x=i % 2, Dp=dp, steps=0) for i, dp in enumerate((0.001, 0.02, 0.2))]
+    ws.append(W.small(64, 64, seed=53, n_nodes=24, radius=5.0))          # a periodic one beside them
+    steps = 45
+    ref = _reference(lb, ws, steps)
+    ss = _solvers(lb, ws)
+    b = lb.Batch(ss)
+    b.step(steps)
+    b.sync()
+    for s, r in zip(ss, ref):
+        _assert_bitwise(_state(s), r)
+    b.close()
+    for s in ss:
+        s.close()

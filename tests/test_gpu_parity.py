@@ -500,13 +500,16 @@ def test_scalar_model_rejections():
 # Walls in y (App. C): half-way bounce-back, zero-gradient sigma and P, zero velocity
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("nx,ny,rings", [
-    (64, 48, [W.ring(20, 4.0, (32.3, 24.1), pull_force=1e-3, pull_angle=1.2)]),   # pulled towards a wall
-    (40, 37, [W.ring(16, 3.0, (20.3, 18.2), pull_force=1e-3, pull_angle=0.3)]),   # ragged top tile row
-    (40, 12, []),                                                                  # one tile row, both walls
+@pytest.mark.parametrize("nx,ny,rings,wx,wy", [
+    (64, 48, [W.ring(20, 4.0, (32.3, 24.1), pull_force=1e-3, pull_angle=1.2)], 0, 1),   # pulled towards a wall
+    (40, 37, [W.ring(16, 3.0, (20.3, 18.2), pull_force=1e-3, pull_angle=0.3)], 0, 1),   # ragged top tile row
+    (40, 12, [], 0, 1),                                                                  # one tile row, both walls
+    (70, 40, [W.ring(20, 4.0, (35.2, 19.6), pull_force=1e-3, pull_angle=0.2)], 1, 0),   # x walls, ragged last column
+    (70, 37, [W.ring(20, 4.0, (30.8, 17.4), pull_force=1e-3, pull_angle=2.5)], 1, 1),   # closed box
+    (20, 12, [], 1, 1),                                                                  # one tile, all four walls
 ])
-def test_walls_vs_oracle(nx, ny, rings):
-    w = W.make(nx, ny, rings=rings, seed=4, walls_y=1, steps=80)
+def test_walls_vs_oracle(nx, ny, rings, wx, wy):
+    w = W.make(nx, ny, rings=rings, seed=4, walls_y=wy, walls_x=wx, steps=80)
     got, ref = run_both(w, 80)
     check_fields(got, ref)
     check_nodes(got, ref, w)
@@ -562,13 +565,14 @@ def test_walls_rejections():
 TRAP = dict(k=0.05, dx=4.0, dy=1.0, t_eq=30, pull=120, width=30)
 
 
-@pytest.mark.parametrize("walls", [0, 1])
+@pytest.mark.parametrize("walls", [0, 1, 2])
 def test_trap_protocol_vs_oracle(walls):
     # the paper's experiment in small: the trap holds the ring, drags it by (4, 1) over 120
-    # steps and lets go; the ring then recoils in the viscoelastic fluid
+    # steps and lets go; the ring then recoils in the viscoelastic fluid (periodic; walls in y;
+    # the closed box of App. C)
     lb = _gpu()
     w = W.make(64, 48, rings=[W.ring(20, 4.0, (24.3, 23.9), pull_force=0.0, trap=TRAP)], seed=8,
-               walls_y=walls, steps=240)
+               walls_y=1 if walls else 0, walls_x=1 if walls == 2 else 0, steps=240)
     got, ref = run_both(w, 240)
     check_fields(got, ref)
     check_nodes(got, ref, w)
@@ -584,7 +588,8 @@ def test_trap_protocol_vs_oracle(walls):
 def test_trap_node_tail_matches_separate_node_kernel_bitwise():
     lb = _gpu()
     w = W.make(96, 64, rings=[W.ring(130, 10.0, (40.2, 30.7), pull_force=0.0, trap=TRAP),
-                              W.ring(24, 4.0, (75.1, 40.3), pull_force=1e-3, pull_angle=2.0)], seed=9, steps=0)
+                              W.ring(24, 4.0, (75.1, 40.3), pull_force=1e-3, pull_angle=2.0)], seed=9, steps=0,
+               walls_x=1, walls_y=1)
     out = []
     for tail in (True, False):
         s = lb.Solver.from_workload(w)
