@@ -601,7 +601,10 @@ def main():
     forms = None if world > 1 else measure_forms(args, lb, W, torch)
     if forms is not None and not args.no_batched:
         forms["batched"] = measure_batched(args, lb, W, torch)
-        forms["protocol"] = measure_protocol(args, lb, W, torch)
+        try:
+            forms["protocol"] = measure_protocol(args, lb, W, torch)
+        except lb.LBError as e:
+            forms["protocol"] = {"error": str(e)}
     if forms is not None and args.learned_seconds > 0:
         forms["learned"] = measure_learned(args, lb, torch)
     if rank != 0:
