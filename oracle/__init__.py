@@ -168,7 +168,11 @@ class TrapProtocol:
     y0: float = 0.0
 
     def s(self, t, c):
-        return 1.0 / (1.0 + math.exp(-8.0 * (t - c) / self.width))
+        z = 8.0 * (t - c) / self.width
+        if z >= 0:
+            return 1.0 / (1.0 + math.exp(-z))
+        e = math.exp(z)                  # the same value, without overflow far before c
+        return e / (1.0 + e)
 
     @staticmethod
     def sp(z):

@@ -286,6 +286,8 @@ def test_trap_protocol_limits_and_speed():
     assert abs(tp.k(90) - 2e-3) < 1e-8 and tp.k(-60) < 1e-9 and tp.k(300) < 1e-9
     assert abs(tp.s(15 + 15, 15 + 15) - 0.5) < 1e-15 and tp.s(0, 15) < 0.02 and tp.s(30, 15) > 0.98
     assert np.allclose(tp.ext(1000), (16.0, 18.0)) and np.allclose(tp.ext(-300), (10.0, 20.0))
+    # far from every transition (long protocols): no overflow, exact limits
+    assert tp.k(1e6) == 0.0 and tp.g(1e6) == 1.0 and tp.s(-1e6, 0.0) == 0.0
 
 
 # ----------------------------------------------------------------------------------------
