@@ -359,12 +359,7 @@ class Sim:
         rc = _rings_c(self.rings)
         nr = len(self.rings)
         for _ in range(n):
-            if any(r.protocol is not None for r in self.rings):
-                # Eq. Utrap at this step
-                for r in self.rings:
-                    if r.protocol is not None:
-                        r.trap_k = r.protocol.k(self.t)
-                        r.trap_x, r.trap_y = r.protocol.ext(self.t)
+            if self._set_trap():
                 rc = _rings_c(self.rings)
             rec = every > 0 and self.t % every == 0
             d = _Diag()
@@ -388,8 +383,19 @@ class Sim:
             self.t += 1
         return self
 
+    def _set_trap(self) -> bool:
+        """Eq. Utrap at the current step t on every trapped ring; False if there is none."""
+        trapped = False
+        for r in self.rings:
+            if r.protocol is not None:
+                r.trap_k = r.protocol.k(self.t)
+                r.trap_x, r.trap_y = r.protocol.ext(self.t)
+                trapped = True
+        return trapped
+
     def fields(self):
         """rho - rho0, u (with the half-force correction) of the current state, sigma, P."""
+        self._set_trap()          # the force of the state at t includes the trap at t
         F, fp = forces(self.p, self.rings, self.sigma, self.P, self.X, self.fext)
         rho, u = moments(self.p, self.h, F)
         return {"drho": rho - self.p.rho0, "ux": u[0], "uy": u[1], "sxx": self.sigma[0],
