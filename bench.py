@@ -243,35 +243,41 @@ def measure_forms(args, lb, W, torch):
 
 
 def measure_protocol(args, lb, W, torch):
-    """The paper's pulling experiment (Sec. III, App. C) as one batched run: eight 250 x 250
-    closed boxes (walls on all four sides), a ring of 128 nodes (radius 16) held by the harmonic trap, dragged
-    by 40 cells over 8000 steps after 30 steps of equilibration and released, then left to recoil
-    until step 20000; D_p log-spaced over [1e-3, 0.25], relaxation 2000 steps.  Reports the
-    Return (Eq. Rec) per D_p and the batch's throughput.  Synthetic stand-in for the paper's
-    runs: same protocol shape and lattice size, these lattice-unit parameters."""
+    """The paper's pulling experiment of its scalar-viscoelasticity results (Sec. III: Return
+    against D_p): eight 250 x 250 closed boxes (walls on all four sides, App. C), one per CUDA
+    stream, with the scalar model, a ring of 128 nodes (radius 16) held by the harmonic trap,
+    dragged by 40 cells over 8000 steps after 30 steps of equilibration and released, then left to
+    recoil until step 20000; D_p log-spaced over [1e-3, 0.25], relaxation 2000 steps.  Reports the
+    Return (Eq. Rec) per D_p and the throughput over the wall-clock time of the run.  Synthetic
+    stand-in for the paper's runs: same protocol shape and lattice size, these lattice-unit
+    parameters."""
     import numpy as np
     n_steps, d_pull = 20000, 40.0
     dps = [float(x) for x in np.geomspace(1e-3, 0.25, 8)]
     trap = dict(k=0.02, dx=d_pull, dy=0.0, t_eq=30, pull=8000, width=30)
     ws = [W.make(250, 250, rings=[W.ring(128, 16.0, (60.3, 125.2), pull_force=0.0, trap=trap)],
-                 seed=700 + i, walls_y=1, walls_x=1, Dp=dp, lambda_steps=2000.0, every=100, steps=n_steps)
+                 seed=700 + i, walls_y=1, walls_x=1, Dp=dp, lambda_steps=2000.0, every=100, steps=n_steps,
+                 **W.scalar_physics())
           for i, dp in enumerate(dps)]
-    ss = [lb.Solver.from_workload(w, max_samples=n_steps // 100 + 2) for w in ws]
-    b = lb.Batch(ss)
+    # one lattice per stream (the batched kernel takes the tensorial model only)
+    ss = []
+    for w in ws:
+        s_ = lb.Solver(lb.params_from_workload(w, max_samples=n_steps // 100 + 2), stream=torch.cuda.Stream())
+        s_.init_fields(w["noise"])
+        s_.set_body(w["rings"])
+        ss.append(s_)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(torch.cuda.current_stream())
-    b.step(n_steps)
-    e1.record(torch.cuda.current_stream())
-    b.sync()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    for s_ in ss:
+        s_.step(n_steps)
+    for s_ in ss:
+        s_.sync()
+    ms = (time.perf_counter() - t0) * 1e3
     rets = [lb.return_metric(s_.series(), 0, d_pull, 250, 250) for s_ in ss]
-    b.close()
     for s_ in ss:
         s_.close()
     cells = 8 * 250 * 250
-    return {"workload": "8 x 250x250 closed boxes, trapped ring (128 nodes, r 16) dragged 40 cells over "
+    return {"workload": "8 x 250x250 closed boxes, scalar model, trapped ring (128 nodes, r 16) dragged 40 cells over "
                         "8000 steps then released, 20000 steps, relaxation 2000 steps",
             "Dp": dps, "return": rets, "value": cells * n_steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
             "seconds": ms * 1e-3}
