@@ -244,11 +244,11 @@ def measure_forms(args, lb, W, torch):
 
 def measure_protocol(args, lb, W, torch):
     """The paper's pulling experiment of its scalar-viscoelasticity results (Sec. III: Return
-    against D_p): eight 250 x 250 closed boxes (walls on all four sides, App. C), one per CUDA
-    stream, with the scalar model, a ring of 128 nodes (radius 16) held by the harmonic trap,
+    against D_p) as one batched run: eight 250 x 250 closed boxes (walls on all four sides,
+    App. C) with the scalar model, a ring of 128 nodes (radius 16) held by the harmonic trap,
     dragged by 40 cells over 8000 steps after 30 steps of equilibration and released, then left to
     recoil until step 20000; D_p log-spaced over [1e-3, 0.25], relaxation 2000 steps.  Reports the
-    Return (Eq. Rec) per D_p and the throughput over the wall-clock time of the run.  Synthetic
+    Return (Eq. Rec) per D_p and the batch's throughput.  Synthetic
     stand-in for the paper's runs: same protocol shape and lattice size, these lattice-unit
     parameters."""
     import numpy as np
@@ -259,21 +259,18 @@ def measure_protocol(args, lb, W, torch):
                  seed=700 + i, walls_y=1, walls_x=1, Dp=dp, lambda_steps=2000.0, every=100, steps=n_steps,
                  **W.scalar_physics())
           for i, dp in enumerate(dps)]
-    # one lattice per stream (the batched kernel takes the tensorial model only)
-    ss = []
-    for w in ws:
-        s_ = lb.Solver(lb.params_from_workload(w, max_samples=n_steps // 100 + 2), stream=torch.cuda.Stream())
-        s_.init_fields(w["noise"])
-        s_.set_body(w["rings"])
-        ss.append(s_)
+    ss = [lb.Solver.from_workload(w, max_samples=n_steps // 100 + 2) for w in ws]
+    b = lb.Batch(ss)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s_ in ss:
-        s_.step(n_steps)
-    for s_ in ss:
-        s_.sync()
-    ms = (time.perf_counter() - t0) * 1e3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    b.step(n_steps)
+    e1.record(torch.cuda.current_stream())
+    b.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
     rets = [lb.return_metric(s_.series(), 0, d_pull, 250, 250) for s_ in ss]
+    b.close()
     for s_ in ss:
         s_.close()
     cells = 8 * 250 * 250

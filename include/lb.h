@@ -262,7 +262,7 @@ void lb_destroy(lb_handle* h);
  * equal; the readout sums of the lattice may differ in the last bits with the tile shape).
  *
  * lb_batch_create: handles[0..n-1] (n >= 1) must be distinct, have their fields and bodies set
- *   (lb_init_fields, lb_set_body), use the FP32 state and the tensorial model, share one stream and be at the same
+ *   (lb_init_fields, lb_set_body), use the FP32 state and one model (all tensorial or all scalar), share one stream and be at the same
  *   buffer parity (an equal step count mod 2).  The batch keeps the pointers: the handles must
  *   outlive it and must not be stepped with lb_step while it exists.  Readouts (lb_readout,
  *   lb_series, ...) on the handles stay valid and are ordered after the batch's steps.

@@ -116,7 +116,7 @@ __device__ bool grid_sync(const BatchArgs& B)
 // runs its own persistent launch (one tile body per kernel keeps within the register budget of
 // two 256-thread CTAs per SM; the instances are independent, so the groups need no common
 // barrier).
-template <int TX, int TY>
+template <int TX, int TY, bool SCALAR>
 __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
 {
     extern __shared__ __align__(16) float sm[];
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
             const int by = local / I.tiles_x, bx = local - by * I.tiles_x;
             // the tile step of lb_step; coherent loads: the state was written by the previous step
             // of this launch
-            tile::tile_step<MODE_STEP, cell::PREC_FP32, TX, TY, true>(I.fa[par], bx, by, local, sm);
+            tile::tile_step<MODE_STEP, cell::PREC_FP32, TX, TY, true, SCALAR>(I.fa[par], bx, by, local, sm);
             __syncthreads();     // shared memory is reused by the next item
         }
         ok = grid_sync(B);
@@ -190,6 +190,7 @@ struct lb_batch {
     cudaStream_t stream = nullptr;          // the batch's own stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<int> shape;                 // per instance
+    bool scalar = false;                    // every instance runs the scalar model (else none does)
     // per tile shape: the group of instances with that shape (device descriptors, prefix sums)
     BatchInst* d_inst[N_SHAPES] = {};
     int* d_tile_begin[N_SHAPES] = {};
@@ -315,7 +316,8 @@ cudaError_t launch_shape(const lb_batch* b, int sh, int nsteps)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch<TX, TY>, a, nsteps);
+    return b->scalar ? cudaLaunchKernelEx(&cfg, k_batch<TX, TY, true>, a, nsteps)
+                     : cudaLaunchKernelEx(&cfg, k_batch<TX, TY, false>, a, nsteps);
 }
 
 // one persistent launch per non-empty shape group, one after another on the batch stream
@@ -334,10 +336,11 @@ template <int TX, int TY>
 cudaError_t setup_shape(lb_batch* b, int sh, int n_sm)
 {
     const size_t smem = batch_smem<TX, TY>();
-    cudaError_t e = cudaFuncSetAttribute(k_batch<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = b->scalar ? k_batch<TX, TY, true> : k_batch<TX, TY, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TX, TY>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     b->grid[sh] = n_sm * per_sm;
@@ -401,7 +404,7 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
     for (int i = 0; i < n; ++i) {
         const lb_handle* h = handles[i];
         if (!h || !h->fields_ready || !h->node_work) return LB_ESTATE;
-        if (h->p.precision != LB_FP32 || h->p.model != LB_MODEL_TENSORIAL || h->cur != handles[0]->cur ||
+        if (h->p.precision != LB_FP32 || h->p.model != handles[0]->p.model || h->cur != handles[0]->cur ||
             h->stream != handles[0]->stream)
             return LB_EINVAL;
         for (int k = 0; k < i; ++k)
@@ -412,6 +415,7 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
     b->user = handles[0]->stream;
     b->chunk = std::max(1, handles[0]->p.readout_every);
     b->shape.assign(n, 0);
+    b->scalar = handles[0]->p.model == LB_MODEL_SCALAR;
     auto cleanup = [&](int code) { lb_batch_destroy(b); return code; };
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||

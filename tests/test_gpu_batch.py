@@ -270,3 +270,25 @@ def test_batch_with_walls_and_traps_matches_single_handles_bitwise():
     b.close()
     for s in ss:
         s.close()
+
+
+def test_scalar_model_batch_matches_single_handles_bitwise():
+    # the scalar model in the batched kernel (its own instantiation), closed boxes with traps
+    lb = _gpu()
+    trap = dict(k=0.05, dx=3.0, dy=0.5, t_eq=30, pull=60, width=30)
+    ws = [W.make(48 + 16 * i, 48, rings=[W.ring(20, 4.0, (20.3 + i, 23.7), pull_force=0.0, trap=trap)],
+                 seed=60 + i, walls_y=1, walls_x=1, Dp=dp, steps=0, **W.scalar_physics())
+          for i, dp in enumerate((0.001, 0.05, 0.25))]
+    steps = 35
+    ref = _reference(lb, ws, steps)
+    ss = _solvers(lb, ws)
+    b = lb.Batch(ss)
+    for i in range(len(ws)):
+        b.set_shape(i % 4, inst=i)
+    b.step(steps)
+    b.sync()
+    for s, r in zip(ss, ref):
+        _assert_bitwise(_state(s), r)
+    b.close()
+    for s in ss:
+        s.close()

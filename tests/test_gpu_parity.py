@@ -491,9 +491,11 @@ def test_scalar_model_rejections():
             s.set_kernel(k)
     with pytest.raises(lb.LBError):
         s.write_field("Px", np.zeros((w["ny"], w["nx"]), dtype=np.float32))
+    t = lb.Solver.from_workload(dict(w, model=lb.LB_MODEL_TENSORIAL))
     with pytest.raises(lb.LBError):
-        lb.Batch([s])
+        lb.Batch([s, t])                                  # one model per batch
     s.close()
+    t.close()
 
 
 # ------------------------------------------------------------------------------------------
