@@ -42,6 +42,18 @@ def dist_env():
         int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The largest value over the ranks (the slowest rank's time sets the whole job's), or the
+    value itself on one rank.  device: where the process group's backend reduces (cuda for NCCL,
+    cpu for gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -543,10 +555,7 @@ def main():
     s.sync()
     kt = s.kernel_time()
     s.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     total_cells = cells * LB_STEPS_PER_STEP * args.steps * world
     value = total_cells / (ms * 1e-3) / 1e6
 
