@@ -38,3 +38,23 @@ def test_recipes_are_reproducible():
         assert np.array_equal(x["rings"][0]["X"], y["rings"][0]["X"])
     c = W.cfg1()
     assert np.array_equal(c["noise"], W.cfg1()["noise"])
+
+
+def test_return_metric_of_eq_rec():
+    # Return = 1 - d_rec / d_pull from the first and last centre of mass of a readout series;
+    # d_rec is taken as a minimum image on the periodic lattice
+    from paper_2209_14889_gb300 import lb
+    rows = np.zeros((3, 14))
+    rows[:, 8:10] = [[10.0, 20.0], [30.0, 20.0], [13.0, 24.0]]     # ring 0: back to 5 cells off
+    rows[:, 12:14] = [[1.0, 5.0], [50.0, 5.0], [63.0, 5.0]]        # ring 1: 2 cells across the seam
+    assert abs(lb.return_metric(rows, 0, 20.0, 64, 64) - (1 - 5.0 / 20.0)) < 1e-15
+    assert abs(lb.return_metric(rows, 1, 40.0, 64, 64) - (1 - 2.0 / 40.0)) < 1e-15
+
+
+def test_scalar_physics_is_the_isotropic_stiffness():
+    p = W.scalar_physics(2e-3)
+    K1111, K1122, K2222, K1212 = p["K"]
+    assert K2222 == K1111 and K1122 == 0.0 and K1212 == K1111 / 2
+    assert p["ericksen"] == 0 and p["model"] == 1
+    # Delta K = K1111 - K2222 and X = K1111 - 2 K1122 - 4 K1212 + K2222 vanish: C~ = C I (App. B)
+    assert K1111 - K2222 == 0.0 and K1111 - 2 * K1122 - 4 * K1212 + K2222 == 0.0
