@@ -133,7 +133,8 @@ int lb_create(const lb_params* p, void* stream, lb_handle** out);
  * Initial state: h_n = w_n rho0 (fluid at rest), sigma^p = 0,
  * P = P_eq (cos theta_d, sin theta_d) + noise with P_eq = sqrt(-alpha/beta) (Sec. III B)
  * (0 if alpha >= 0).  noise: host FP64 [2][ny][nx] added to P, or NULL.
- * Resets the step counter to 0 and clears the readout series.
+ * Resets the step counter to 0 and clears the readout series; rings already set keep their
+ * positions, and their forces and work boxes are recomputed for the restart.
  */
 int lb_init_fields(lb_handle* h, const double* noise);
 
@@ -145,7 +146,8 @@ int lb_init_fields(lb_handle* h, const double* noise);
  */
 int lb_set_body(lb_handle* h, int32_t n_rings, const lb_ring* rings, const double* xy);
 
-/* Advance n time steps, asynchronously on the handle's stream. */
+/* Advance n time steps, asynchronously on the handle's stream (one kernel launch per step with
+ * the default settings: see lb_set_node_tail and lb_launches_per_step). */
 int lb_step(lb_handle* h, int64_t n);
 
 /* Synchronise the stream and return LB_OK or the first device-side error (LB_ENONFINITE,
