@@ -292,6 +292,87 @@ def measure_protocol(args, lb, W, torch):
             "seconds": ms * 1e-3}
 
 
+ANISO_THETAS = [0.0, math.pi / 6, math.pi / 3, math.pi / 2, 2 * math.pi / 3, 5 * math.pi / 6, math.pi]
+ANISO_ALPHAS = [0.0, -0.45, -0.9]
+
+
+def measure_anisotropy(args, lb, W, torch):
+    """The paper's anisotropy study (Sec. III C): the Return (Eq. Rec) of the trapped ring against
+    the equilibrium polarisation P = sqrt(-alpha/beta) (beta = 1, alpha in {0, -0.45, -0.9}) and
+    the initial director angle theta0 to the pulling axis x (0 .. pi by pi/6; at alpha = 0 only
+    theta0 = 0 and pi/3), with the tensorial model in 250 x 250 closed boxes: no orientation
+    noise, the ring (128 nodes, radius 16) on the box's mirror line, the trap of the protocol form
+    (dragged 40 cells over 8000 steps, released, 20000 steps), relaxation 2000 steps, D_p = 0.01,
+    and the Ericksen force off (with it, closed tensorial boxes are not stable over these runs).
+    One batch per alpha.  Reports, per alpha, the Return per theta0, its residuals under theta0 ->
+    theta0 + pi and theta0 -> pi - theta0, and the deflection (centre of mass across the pulling
+    axis, cells) and rotation (of the node that starts on the +x side, about the centre of mass,
+    degrees) at the end of each run."""
+    import numpy as np
+    n_steps, d_pull, side, cy = 20000, 40.0, 250, 124.5
+    trap = dict(k=0.02, dx=d_pull, dy=0.0, t_eq=30, pull=8000, width=30)
+    out = {"workload": "250x250 closed boxes, tensorial model without the Ericksen force, no noise, "
+                       "trapped ring (128 nodes, r 16) on the mirror line dragged 40 cells along x over "
+                       "8000 steps then released, 20000 steps, relaxation 2000 steps, D_p 0.01",
+           "theta0": ANISO_THETAS, "alpha": ANISO_ALPHAS, "per_alpha": {}}
+    cells_steps, seconds = 0, 0.0
+    for alpha in ANISO_ALPHAS:
+        thetas = ANISO_THETAS if alpha != 0.0 else [0.0, math.pi / 3]
+        ws = [W.make(side, side, rings=[W.ring(128, 16.0, (60.3, cy), pull_force=0.0, trap=trap)],
+                     seed=900, noise_amp=0.0, walls_y=1, walls_x=1, Dp=0.01, lambda_steps=2000.0,
+                     every=100, steps=n_steps, ericksen=0, alpha=alpha, director_angle=th)
+              for th in thetas]
+        ss = [lb.Solver.from_workload(w, max_samples=n_steps // 100 + 2) for w in ws]
+        X0 = [s_.nodes() for s_ in ss]
+        b = lb.Batch(ss)
+        rec = {"theta0": thetas}
+        try:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())
+            b.step(n_steps)
+            e1.record(torch.cuda.current_stream())
+            b.sync()
+            torch.cuda.synchronize()
+            seconds += e0.elapsed_time(e1) * 1e-3
+            cells_steps += len(ss) * side * side * n_steps
+            rets, defl, rot = [], [], []
+            for s_, x0 in zip(ss, X0):
+                ser = s_.series()
+                rets.append(lb.return_metric(ser, 0, d_pull, side, side))
+                x1 = s_.nodes()
+                c0, c1 = x0.mean(0), x1.mean(0)
+                defl.append(float(c1[1] - c0[1]))
+                a0 = math.atan2(x0[0, 1] - c0[1], x0[0, 0] - c0[0])
+                a1 = math.atan2(x1[0, 1] - c1[1], x1[0, 0] - c1[0])
+                rot.append(math.degrees(math.remainder(a1 - a0, 2 * math.pi)))
+            rec.update(ret=rets, deflection=defl, rotation_deg=rot)
+            if len(thetas) == len(ANISO_THETAS):
+                rec["period_pi_residual"] = abs(rets[0] - rets[-1])
+                rec["mirror_pi_2_residual"] = max(abs(rets[i] - rets[-1 - i]) for i in range(len(rets)))
+                rec["theta0_spread"] = max(rets) - min(rets)
+            else:
+                rec["theta0_spread"] = max(rets) - min(rets)
+        except lb.LBError as e:
+            rec["error"] = str(e)
+        finally:
+            b.close()
+            for s_ in ss:
+                s_.close()
+        out["per_alpha"]["%g" % alpha] = rec
+    out["value"] = cells_steps / seconds / 1e6 if seconds > 0 else None
+    out["unit"] = "MLUPS"
+    out["seconds"] = seconds
+    return out
+
+
+def run_only_aniso(args):
+    """The anisotropy form alone (one JSON line)."""
+    import torch
+    from paper_2209_14889_gb300 import lb, workloads as W
+    print(json.dumps({"anisotropy": measure_anisotropy(args, lb, W, torch)}))
+
+
 def measure_batched(args, lb, W, torch):
     """The batched workload: 256 independent periodic lattices of sides {128, ..., 512} (28.9M
     cells, 3.2 GB of FP32 state, larger than L2, so no flush) with one ring each, advanced by the
@@ -485,6 +566,8 @@ def main():
                     help="run the node step as its own kernel instead of in the tile kernel's tail")
     ap.add_argument("--only-net", action="store_true",
                     help="time the network's forward pass at 256^2 (batch 1) only (for profiling)")
+    ap.add_argument("--only-aniso", action="store_true",
+                    help="run the anisotropy study (Return against alpha and theta0) only")
     ap.add_argument("--learned-seconds", type=float, default=45.0,
                     help="training budget of the learned form (0: skip it)")
     ap.add_argument("--tune-cache", default=None,
@@ -497,6 +580,8 @@ def main():
         return run_reference(args, rank, world)
     if args.only_net:
         return run_only_net(args)
+    if args.only_aniso:
+        return run_only_aniso(args)
 
     import numpy as np
     import torch
@@ -617,6 +702,10 @@ def main():
             forms["protocol"] = measure_protocol(args, lb, W, torch)
         except lb.LBError as e:
             forms["protocol"] = {"error": str(e)}
+        try:
+            forms["anisotropy"] = measure_anisotropy(args, lb, W, torch)
+        except lb.LBError as e:
+            forms["anisotropy"] = {"error": str(e)}
     if forms is not None and args.learned_seconds > 0:
         forms["learned"] = measure_learned(args, lb, torch)
     if rank != 0:

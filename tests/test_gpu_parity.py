@@ -603,3 +603,46 @@ def test_trap_node_tail_matches_separate_node_kernel_bitwise():
     for k in out[0][0]:
         assert np.array_equal(out[0][0][k], out[1][0][k]), k
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+# ------------------------------------------------------------------------------------------
+# The anisotropy study's configuration (Sec. III C): tensorial model, closed box, no noise, the
+# director at theta0 to the pulling axis x, the Ericksen force off (as in the bench's sweep)
+# ------------------------------------------------------------------------------------------
+
+ANISO_TRAP = dict(k=0.05, dx=4.0, dy=0.0, t_eq=30, pull=100, width=30)
+MIRROR_SIGNS = [("drho", 1), ("ux", 1), ("uy", -1), ("sxx", 1), ("syy", 1), ("sxy", -1), ("Px", 1), ("Py", -1)]
+
+
+def _aniso(theta0, alpha):
+    return W.make(64, 48, rings=[W.ring(20, 4.0, (24.3, 23.5), pull_force=0.0, trap=ANISO_TRAP)], seed=8,
+                  noise_amp=0.0, walls_x=1, walls_y=1, director_angle=theta0, alpha=alpha, ericksen=0,
+                  steps=200)
+
+
+@pytest.mark.parametrize("theta0,alpha", [(math.pi / 3, -0.9), (math.pi / 6, -0.45)])
+def test_anisotropy_closed_box_vs_oracle_and_mirror(theta0, alpha):
+    lb = _gpu()
+    w = _aniso(theta0, alpha)
+    got, ref = run_both(w, 200)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+    # the run at -theta0 is the mirror image (y -> 47 - y) of the run at theta0
+    s = lb.Solver.from_workload(_aniso(-theta0, alpha))
+    s.step(200)
+    s.sync()
+    fm, Xm, sm = s.fields(), s.nodes(), s.series()
+    s.close()
+    for k, sgn in MIRROR_SIGNS:
+        assert rel_l2(sgn * fm[k][::-1], got["fields"][k]) <= FIELD_TOL, k
+    mate = (-np.arange(20)) % 20                        # node a of the mirror run is node -a here
+    assert np.abs(Xm[:, 0] - got["X"][mate, 0]).max() < 1e-4
+    assert np.abs((47.0 - Xm[:, 1]) - got["X"][mate, 1]).max() < 1e-4
+    # the oblique director deflects the ring off the pulling axis (oracle: by 1.6e-3 cells at
+    # theta0 = pi/3, alpha = -0.9; by 1.5e-5 at pi/6, -0.45), the mirror run to the other side
+    ya, yb = got["series"][:, 9] - 23.5, sm[:, 9] - 23.5
+    dref = ref["series"][-1, 9] - 23.5
+    assert abs(dref) > 1e-5
+    assert abs(ya[-1] - dref) <= 1e-3 * abs(dref) + 5e-6
+    assert np.abs(ya + yb).max() <= 1e-3 * abs(dref) + 5e-6
