@@ -519,6 +519,55 @@ def test_stress_pulse_second_moment_grows_4Dt():
     assert abs((m2b - m2a) - 4 * D * steps * m0) < 1e-6 * (4 * D * steps * m0)
 
 
+def _viscoelastic_shear_wave(N, U0=1e-6, kvm=3.0, g=4.0, r=0.5, d=0.2, T=2.0):
+    """A transverse wave u_y = U(t) sin(kx), sigma_xy = S(t) cos(kx) in the oriented polymer fluid
+    (director along x with |P| = P_eq, so P stays put to first order in U0; Ericksen force off).
+    Linearised, Eq. StiffCons gives dS/dt = G k U / 2 - (G / eta_p + D_p k^2) S with G the shear
+    entry of C~(P) (the factor 1/2 is Psi_xy = (1/2) d_x u_y), and the momentum balance with
+    f = div sigma^p gives dU/dt = -nu k^2 U - k S / rho.  G is taken from the quadrature of the
+    App. B definition (_quad_mandel), not from the oracle.  Diffusive scaling: G, eta_p and D_p
+    are fixed multiples of nu^2 k^2, G / (nu k^2) and nu, and the run lasts T / (nu k^2) steps.
+    Returns the error of U and S at the end relative to U0 and to max |S|."""
+    from scipy.linalg import expm
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    k = 2 * np.pi / N
+    P_eq = iv(1, kvm) / iv(0, kvm)
+    Kshape = (2.0, 1.0, 1.0, 1.0)
+    G_shape = _quad_mandel(Kshape, kvm, 0.0, M=1024)[2, 2]
+    G = g * nu * nu * k * k
+    K = tuple(G / G_shape * v for v in Kshape)
+    eta_p = G / (r * nu * k * k)
+    Dp = d * nu
+    p = O.Params(nx=N, ny=4, tau=tau, K1111=K[0], K1122=K[1], K2222=K[2], K1212=K[3], eta_p=eta_p,
+                 Dp=Dp, alpha=-P_eq * P_eq, beta=1.0, xi=1.1, Gamma=1.0, kappa=1e-3, ericksen=0)
+    x = np.arange(N, dtype=float)[None, :] * np.ones((4, 1))
+    u = np.stack([np.zeros_like(x), U0 * np.sin(k * x)])
+    P = np.stack([np.full_like(x, P_eq), np.zeros_like(x)])
+    s = O.Sim(p, [], O.equilibrium(np.ones_like(x), u), np.zeros((3, 4, N)), P, np.zeros((0, 2)))
+    n = int(round(T / (nu * k * k)))
+    s.step(n)
+    f = s.fields()
+    U = 2.0 / N * (f["uy"][0] * np.sin(k * x[0])).sum()
+    S = 2.0 / N * (f["sxy"][0] * np.cos(k * x[0])).sum()
+    a = G / eta_p + Dp * k * k
+    A = np.array([[-nu * k * k, -k], [G * k / 2, -a]])
+    ts = np.linspace(0.0, n, 41)
+    traj = np.array([expm(A * t) @ np.array([U0, 0.0]) for t in ts])
+    Ue, Se = traj[-1]
+    return abs(U - Ue) / U0, abs(S - Se) / np.abs(traj[:, 1]).max()
+
+
+def test_viscoelastic_shear_wave_second_order():
+    # the coupling of Eq. StiffCons to the flow through Psi and f^p = div sigma^p, with the
+    # anisotropic shear modulus of App. B at k = 3 (P_eq = I1(3)/I0(3)) and stress diffusion:
+    # the oracle converges to the linear two-mode solution at second order in dx
+    e = [_viscoelastic_shear_wave(N) for N in (16, 32, 64)]
+    eu, es = [x[0] for x in e], [x[1] for x in e]
+    assert eu[2] < 5e-3 and es[2] < 5e-3, e
+    assert 3.0 < eu[1] / eu[2] < 5.5 and 3.0 < es[1] / es[2] < 5.5, e
+
+
 def _P_relax(Gamma, steps, p0=0.3, alpha=-0.9, beta=1.0):
     n = 4
     p = O.Params(nx=n, ny=n, tau=0.8, eta_p=1.0, alpha=alpha, beta=beta, xi=1.1, Gamma=Gamma,
