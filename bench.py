@@ -303,15 +303,14 @@ def measure_anisotropy(args, lb, W, torch):
     theta0 = 0 and pi/3), with the tensorial model in 250 x 250 closed boxes: no orientation
     noise, the ring (128 nodes, radius 16) on the box's mirror line, the trap of the protocol form
     (dragged 40 cells over 8000 steps, released, 20000 steps), relaxation 2000 steps, D_p = 0.01,
-    and the Ericksen force off (with it, closed tensorial boxes are not stable over these runs).
-    One batch per alpha.  Reports, per alpha, the Return per theta0, its residuals under theta0 ->
+    and the Ericksen force on.  One batch per alpha.  Reports, per alpha, the Return per theta0, its residuals under theta0 ->
     theta0 + pi and theta0 -> pi - theta0, and the deflection (centre of mass across the pulling
     axis, cells) and rotation (of the node that starts on the +x side, about the centre of mass,
     degrees) at the end of each run."""
     import numpy as np
     n_steps, d_pull, side, cy = 20000, 40.0, 250, 124.5
     trap = dict(k=0.02, dx=d_pull, dy=0.0, t_eq=30, pull=8000, width=30)
-    out = {"workload": "250x250 closed boxes, tensorial model without the Ericksen force, no noise, "
+    out = {"workload": "250x250 closed boxes, tensorial model with the Ericksen force, no noise, "
                        "trapped ring (128 nodes, r 16) on the mirror line dragged 40 cells along x over "
                        "8000 steps then released, 20000 steps, relaxation 2000 steps, D_p 0.01",
            "theta0": ANISO_THETAS, "alpha": ANISO_ALPHAS, "per_alpha": {}}
@@ -320,7 +319,7 @@ def measure_anisotropy(args, lb, W, torch):
         thetas = ANISO_THETAS if alpha != 0.0 else [0.0, math.pi / 3]
         ws = [W.make(side, side, rings=[W.ring(128, 16.0, (60.3, cy), pull_force=0.0, trap=trap)],
                      seed=900, noise_amp=0.0, walls_y=1, walls_x=1, Dp=0.01, lambda_steps=2000.0,
-                     every=100, steps=n_steps, ericksen=0, alpha=alpha, director_angle=th)
+                     every=100, steps=n_steps, alpha=alpha, director_angle=th)
               for th in thetas]
         ss = [lb.Solver.from_workload(w, max_samples=n_steps // 100 + 2) for w in ws]
         X0 = [s_.nodes() for s_ in ss]

@@ -83,9 +83,11 @@ typedef struct lb_params {
 /*
  * Walls (App. C; walls_y = 1 and/or walls_x = 1): no-slip walls half-way between nodes at
  * y = -1/2 and y = ny - 1/2 (x = -1/2, nx - 1/2), half-way bounce-back of the populations, zero
- * gradient of sigma^p, P and the Ericksen stress across them (a cell beyond a wall mirrors the
- * cell inside), zero velocity (the mirrored u is negated); an axis without walls stays periodic.
- * Needs the FP32 state, no diffusion sub-steps and the one-cell tile kernel; ring nodes must stay
+ * gradient of sigma^p and P across them (a cell beyond a wall mirrors the cell inside), zero
+ * velocity and zero Ericksen stress at the wall (their mirrored values are negated, so the
+ * Ericksen force moves no momentum into the walls); an axis without walls stays periodic.
+ * Needs at least 4 cells across each walled axis (else LB_EINVAL at lb_create), the FP32 state,
+ * no diffusion sub-steps and the one-cell tile kernel; ring nodes must stay
  * 5 cells from the walls at lb_set_body (else LB_EINVAL) and 4 cells while stepping (else
  * LB_EBODY at lb_sync); the learned stepper takes periodic lattices only.
  */

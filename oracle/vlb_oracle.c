@@ -329,11 +329,16 @@ void orc_forces(const orc_params* p, const orc_ring* rings, int n_rings, const d
             /* f^p_i = d_j sigma^p_ij (Sec. II B); sigma = (xx, yy, xy) */
             double fpx = Dx(p, sigma, x, y, BC_NEUMANN) + Dy(p, sigma + 2 * N, x, y, BC_NEUMANN);
             double fpy = Dx(p, sigma + 2 * N, x, y, BC_NEUMANN) + Dy(p, sigma + N, x, y, BC_NEUMANN);
-            /* f^E_i = d_j sigma^E_ij (Sec. II C 1) */
+            /* f^E_i = d_j sigma^E_ij (Sec. II C 1).  Reading (App. C names no condition for
+             * sigma^E): beyond a wall the Ericksen stress is the negated image, i.e. it vanishes
+             * at the wall, so the divergence telescopes to zero over a closed box as over a
+             * periodic one and the polar field hands no momentum to a free-anchoring wall.  (Its
+             * zero-gradient image instead let a grid-scale mode at x walls grow without bound
+             * once a flow ran along the wall.) */
             double fex = 0.0, fey = 0.0;
             if (p->ericksen) {
-                fex = Dx(p, sE, x, y, BC_NEUMANN) + Dy(p, sE + N, x, y, BC_NEUMANN);
-                fey = Dx(p, sE + 2 * N, x, y, BC_NEUMANN) + Dy(p, sE + 3 * N, x, y, BC_NEUMANN);
+                fex = Dx(p, sE, x, y, BC_DIRICHLET0) + Dy(p, sE + N, x, y, BC_DIRICHLET0);
+                fey = Dx(p, sE + 2 * N, x, y, BC_DIRICHLET0) + Dy(p, sE + 3 * N, x, y, BC_DIRICHLET0);
             }
             double ex = fext ? fext[i] : 0.0, ey = fext ? fext[N + i] : 0.0;
             F[i] = fib[i] + fpx + fex + ex;

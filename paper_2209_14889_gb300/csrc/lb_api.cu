@@ -266,6 +266,9 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     }
     if (p.walls_y != 0 && p.walls_y != 1) return fail(nullptr, LB_EINVAL, "walls_y must be 0 or 1");
     if (p.walls_x != 0 && p.walls_x != 1) return fail(nullptr, LB_EINVAL, "walls_x must be 0 or 1");
+    // a ghost cell is then at most one mirror away from its image (a negated image is negated once)
+    if ((p.walls_y && p.ny < 4) || (p.walls_x && p.nx < 4))
+        return fail(nullptr, LB_EINVAL, "a walled axis needs at least 4 cells");
     if ((p.walls_y || p.walls_x) && (p.precision != LB_FP32 || p.diffusion_substeps != 0))
         return fail(nullptr, LB_EINVAL, "walls need the FP32 state and no diffusion sub-steps");
     if (p.diffusion_substeps < 0) return fail(nullptr, LB_EINVAL, "diffusion_substeps < 0");

@@ -106,8 +106,9 @@ __device__ __forceinline__ float2 ld_fld2(const void* src, long long NP, int pla
 }
 
 // Walls in y (App. C, half-way bounce-back): the walls sit at y = -1/2 and y = ny - 1/2, and a
-// row beyond them is the mirror image of the row inside: zero-gradient fields (sigma, P and the
-// Ericksen stress) copy their image, the velocity (zero at the wall) takes it negated.
+// row beyond them is the mirror image of the row inside: zero-gradient fields (sigma, P) copy
+// their image, the velocity (zero at the wall) and the Ericksen stress take it negated (the
+// polar field exerts no traction on a free-anchoring wall, so f^E hands no momentum to it).
 __device__ __forceinline__ int mirror_row(int y, int ny)
 {
     for (int k = 0; k < 8 && (y < 0 || y >= ny); ++k) y = y < 0 ? -1 - y : 2 * ny - 1 - y;
@@ -489,7 +490,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
 
     if (wall && !SCALAR && ph.ericksen) {
         __syncthreads();
-        mirror_ghosts(m.sE, R3, 4, R3W, G::R3H, x0 - 3, y0 - 3, a, 1.f);   // read in C, after the gather's barrier
+        mirror_ghosts(m.sE, R3, 4, R3W, G::R3H, x0 - 3, y0 - 3, a, -1.f);   // read in C, after the gather's barrier
     }
 
     // The state at t was written two kernels back; the node forces, ring boxes, step counter and

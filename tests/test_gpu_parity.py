@@ -554,6 +554,9 @@ def test_walls_rejections():
             lb.Solver(lb.params_from_workload(w, **over))
     with pytest.raises(lb.LBError):
         lb.Solver(lb.params_from_workload(dict(w, Dp=0.3, diffusion_substeps=2)))
+    for nx, ny, wx, wy in [(3, 40, 1, 0), (48, 2, 0, 1)]:         # a walled axis under 4 cells
+        with pytest.raises(lb.LBError):
+            lb.Solver(lb.params_from_workload(dict(w, nx=nx, ny=ny, walls_x=wx, walls_y=wy)))
     s = lb.Solver.from_workload(w)
     with pytest.raises(lb.LBError):
         s.set_kernel(lb.LB_KERNEL_PAIR)
@@ -606,8 +609,8 @@ def test_trap_node_tail_matches_separate_node_kernel_bitwise():
 
 
 # ------------------------------------------------------------------------------------------
-# The anisotropy study's configuration (Sec. III C): tensorial model, closed box, no noise, the
-# director at theta0 to the pulling axis x, the Ericksen force off (as in the bench's sweep)
+# The anisotropy study's configuration (Sec. III C): tensorial model with the Ericksen force,
+# closed box, no noise, the director at theta0 to the pulling axis x
 # ------------------------------------------------------------------------------------------
 
 ANISO_TRAP = dict(k=0.05, dx=4.0, dy=0.0, t_eq=30, pull=100, width=30)
@@ -616,8 +619,7 @@ MIRROR_SIGNS = [("drho", 1), ("ux", 1), ("uy", -1), ("sxx", 1), ("syy", 1), ("sx
 
 def _aniso(theta0, alpha):
     return W.make(64, 48, rings=[W.ring(20, 4.0, (24.3, 23.5), pull_force=0.0, trap=ANISO_TRAP)], seed=8,
-                  noise_amp=0.0, walls_x=1, walls_y=1, director_angle=theta0, alpha=alpha, ericksen=0,
-                  steps=200)
+                  noise_amp=0.0, walls_x=1, walls_y=1, director_angle=theta0, alpha=alpha, steps=200)
 
 
 @pytest.mark.parametrize("theta0,alpha", [(math.pi / 3, -0.9), (math.pi / 6, -0.45)])
@@ -639,10 +641,10 @@ def test_anisotropy_closed_box_vs_oracle_and_mirror(theta0, alpha):
     mate = (-np.arange(20)) % 20                        # node a of the mirror run is node -a here
     assert np.abs(Xm[:, 0] - got["X"][mate, 0]).max() < 1e-4
     assert np.abs((47.0 - Xm[:, 1]) - got["X"][mate, 1]).max() < 1e-4
-    # the oblique director deflects the ring off the pulling axis (oracle: by 1.6e-3 cells at
-    # theta0 = pi/3, alpha = -0.9; by 1.5e-5 at pi/6, -0.45), the mirror run to the other side
+    # the oblique director deflects the ring off the pulling axis (oracle: by 0.027 cells at
+    # theta0 = pi/3, alpha = -0.9; by 0.016 at pi/6, -0.45), the mirror run to the other side
     ya, yb = got["series"][:, 9] - 23.5, sm[:, 9] - 23.5
     dref = ref["series"][-1, 9] - 23.5
-    assert abs(dref) > 1e-5
+    assert abs(dref) > 1e-2
     assert abs(ya[-1] - dref) <= 1e-3 * abs(dref) + 5e-6
     assert np.abs(ya + yb).max() <= 1e-3 * abs(dref) + 5e-6
