@@ -254,42 +254,61 @@ def measure_forms(args, lb, W, torch):
     return out
 
 
-def measure_protocol(args, lb, W, torch):
-    """The paper's pulling experiment of its scalar-viscoelasticity results (Sec. III: Return
-    against D_p) as one batched run: eight 250 x 250 closed boxes (walls on all four sides,
-    App. C) with the scalar model, a ring of 128 nodes (radius 16) held by the harmonic trap,
-    dragged by 40 cells over 8000 steps after 30 steps of equilibration and released, then left to
-    recoil until step 20000; D_p log-spaced over [1e-3, 0.25], relaxation 2000 steps.  Reports the
-    Return (Eq. Rec) per D_p and the batch's throughput.  Synthetic
-    stand-in for the paper's runs: same protocol shape and lattice size, these lattice-unit
-    parameters."""
-    import numpy as np
-    n_steps, d_pull = 20000, 40.0
-    dps = [float(x) for x in np.geomspace(1e-3, 0.25, 8)]
-    trap = dict(k=0.02, dx=d_pull, dy=0.0, t_eq=30, pull=8000, width=30)
-    ws = [W.make(250, 250, rings=[W.ring(128, 16.0, (60.3, 125.2), pull_force=0.0, trap=trap)],
-                 seed=700 + i, walls_y=1, walls_x=1, Dp=dp, lambda_steps=2000.0, every=100, steps=n_steps,
+def _protocol_batch(lb, W, torch, runs, n_steps, d_pull=40.0):
+    """One batch of 250 x 250 closed boxes (walls on all four sides, App. C) with the scalar model:
+    per run (radius, nodes, pull steps, D_p, seed) a ring held by the harmonic trap, dragged by
+    d_pull cells along x after 30 steps of equilibration and released, relaxation 2000 steps.
+    Returns the Return (Eq. Rec) of each run at n_steps and the batch's device time (ms)."""
+    ws = [W.make(250, 250, rings=[W.ring(nodes, radius, (60.3, 125.2), pull_force=0.0,
+                                         trap=dict(k=0.02, dx=d_pull, dy=0.0, t_eq=30, pull=pull, width=30))],
+                 seed=seed, walls_y=1, walls_x=1, Dp=dp, lambda_steps=2000.0, every=100, steps=n_steps,
                  **W.scalar_physics())
-          for i, dp in enumerate(dps)]
+          for radius, nodes, pull, dp, seed in runs]
     ss = [lb.Solver.from_workload(w, max_samples=n_steps // 100 + 2) for w in ws]
     b = lb.Batch(ss)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(torch.cuda.current_stream())
-    b.step(n_steps)
-    e1.record(torch.cuda.current_stream())
-    b.sync()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    rets = [lb.return_metric(s_.series(), 0, d_pull, 250, 250) for s_ in ss]
-    b.close()
-    for s_ in ss:
-        s_.close()
-    cells = 8 * 250 * 250
-    return {"workload": "8 x 250x250 closed boxes, scalar model, trapped ring (128 nodes, r 16) dragged 40 cells over "
-                        "8000 steps then released, 20000 steps, relaxation 2000 steps",
-            "Dp": dps, "return": rets, "value": cells * n_steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
-            "seconds": ms * 1e-3}
+    try:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        b.step(n_steps)
+        e1.record(torch.cuda.current_stream())
+        b.sync()
+        torch.cuda.synchronize()
+        rets = [lb.return_metric(s_.series(), 0, d_pull, 250, 250) for s_ in ss]
+        return rets, e0.elapsed_time(e1)
+    finally:
+        b.close()
+        for s_ in ss:
+            s_.close()
+
+
+def measure_protocol(args, lb, W, torch):
+    """The paper's pulling experiments of its scalar-viscoelasticity results (Sec. III B) as
+    batched runs of 250 x 250 closed boxes with the scalar model: the trapped ring is dragged by
+    40 cells and released.  (1) Return against D_p: eight boxes, D_p log-spaced over [1e-3, 0.25],
+    a ring of 128 nodes (radius 16), dragged over 8000 steps, 20000 steps.  (2) Return against the
+    ring's radius: 8 .. 28 cells (nodes at 0.785-cell spacing), D_p = 0.01, the same protocol.
+    (3) Return against the pulling time: 2000 .. 16000 steps over the same 40 cells, radius 16,
+    D_p = 0.01, 30000 steps.  Synthetic stand-in for the paper's runs: same protocol shape and
+    lattice size, these lattice-unit parameters."""
+    import numpy as np
+    dps = [float(x) for x in np.geomspace(1e-3, 0.25, 8)]
+    rets, ms = _protocol_batch(lb, W, torch, [(16.0, 128, 8000, dp, 700 + i) for i, dp in enumerate(dps)], 20000)
+    out = {"workload": "8 x 250x250 closed boxes, scalar model, trapped ring (128 nodes, r 16) dragged 40 cells over "
+                       "8000 steps then released, 20000 steps, relaxation 2000 steps",
+           "Dp": dps, "return": rets, "value": 8 * 250 * 250 * 20000 / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+           "seconds": ms * 1e-3}
+    radii = [8.0, 12.0, 16.0, 20.0, 24.0, 28.0]
+    rr, ms_r = _protocol_batch(lb, W, torch, [(r, int(round(2 * math.pi * r / 0.785)), 8000, 0.01, 720 + i)
+                                             for i, r in enumerate(radii)], 20000)
+    out["radius_sweep"] = {"workload": "6 boxes, D_p 0.01, radius 8..28 (nodes at 0.785 spacing), dragged 40 cells "
+                                       "over 8000 steps, 20000 steps", "radius": radii, "return": rr,
+                           "seconds": ms_r * 1e-3}
+    pulls = [2000, 4000, 8000, 12000, 16000]
+    rp, ms_p = _protocol_batch(lb, W, torch, [(16.0, 128, tp, 0.01, 740 + i) for i, tp in enumerate(pulls)], 30000)
+    out["pull_time_sweep"] = {"workload": "5 boxes, D_p 0.01, radius 16, dragged 40 cells over 2000..16000 steps, "
+                                          "30000 steps", "pull_steps": pulls, "return": rp, "seconds": ms_p * 1e-3}
+    return out
 
 
 ANISO_THETAS = [0.0, math.pi / 6, math.pi / 3, math.pi / 2, 2 * math.pi / 3, 5 * math.pi / 6, math.pi]
