@@ -252,6 +252,51 @@ def test_node_forces_are_minus_gradient_of_energy():
     assert np.allclose(f.sum(0), [1e-3, -2e-3], atol=1e-15)
 
 
+def _ring_drag(L, a, tau=1.5, F=2e-4, n=24, steps=4000):
+    """Terminal drag coefficient F/U of a ring of n nodes (radius a) pulled with total force F
+    through a periodic L x L box of plain fluid, the net force balanced by a uniform body force
+    -F/L^2 on the fluid (the mean-pressure-gradient frame of a periodic array of cylinders)."""
+    p = O.Params(nx=L, ny=L, tau=tau, eta_p=1.0, ericksen=0)
+    r = W.ring(n, a, (L / 2 + 0.3, L / 2 + 0.1), k_spring=0.5, eps_angle=0.05, pull_force=F, pull_angle=0.0)
+    ring = O.Ring(n_nodes=n, k_spring=r["k_spring"], eps_angle=r["eps_angle"], l_eq=r["l_eq"], pull_x=F, pull_y=0.0)
+    fext = np.zeros((2, L, L))
+    fext[0] = -F / (L * L)
+    s = O.Sim(p, [ring], O.equilibrium(np.ones((L, L)), np.zeros((2, L, L))), np.zeros((3, L, L)),
+              np.zeros((2, L, L)), r["X"].copy(), fext=fext)
+    s.step(steps - 1000)
+    x0 = s.X[:, 0].mean()
+    s.step(500)
+    x1 = s.X[:, 0].mean()
+    s.step(500)
+    x2 = s.X[:, 0].mean()
+    assert abs((x2 - x1) - (x1 - x0)) < 1e-3 * (x2 - x1)        # terminal velocity reached
+    return F / ((x2 - x1) / 500.0)
+
+
+def _hasimoto_drag(L, a, nu):
+    # drag per unit length and velocity of a square array of cylinders (radius a, period L) in
+    # Stokes flow: 4 pi mu / (-ln(c)/2 - 0.738 + c - 0.887 c^2 + 2.039 c^3), c = pi a^2 / L^2
+    # (Hasimoto 1959; the higher terms of Sangani and Acrivos 1982); mu = rho nu with rho = 1
+    c = math.pi * a * a / (L * L)
+    return 4 * math.pi * nu / (-0.5 * math.log(c) - 0.738 + c - 0.887 * c * c + 2.039 * c ** 3)
+
+
+def test_ring_drag_matches_periodic_cylinder_array():
+    # the coupled IB-LB step (spreading, Guo forcing, BGK, interpolation, node advection) against
+    # a published Stokes-flow result: the terminal drag of the pulled ring equals the drag of a
+    # cylinder array of the same period whose radius is the ring's plus a fixed fraction of a cell
+    # (the kernel's width), the same fraction for two box sizes at equal area fraction
+    from scipy.optimize import brentq
+    nu = (1.5 - 0.5) / 3
+    offs = []
+    for L, a in [(32, 4.0), (48, 6.0)]:
+        K = _ring_drag(L, a)
+        a_eff = brentq(lambda x: _hasimoto_drag(L, x, nu) - K, 0.5 * a, 2.0 * a)
+        offs.append(a_eff - a)
+    assert all(0.2 < o < 0.7 for o in offs), offs
+    assert abs(offs[0] - offs[1]) < 0.15, offs
+
+
 def test_trap_force_is_minus_gradient_of_eq_utrap():
     # Eq. Utrap: k/2 |R_ext - R_com|^2 with R_com the mean of the nodes; its force on node a is
     # k (R_ext - R_com) / N, the same on every node
