@@ -562,6 +562,37 @@ def cpu_baseline_sample():
             "sample": "1 LB time step of the 1024x1024 workload (%.1f s)" % dt}
 
 
+_OMP_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import oracle as O
+from paper_2209_14889_gb300 import workloads as W
+assert O._OPENMP
+O.lib()
+sim = O.Sim.from_workload(W.cfg2())
+sim.step(1)
+t0 = time.perf_counter()
+sim.step(3)
+print(json.dumps({"dt": time.perf_counter() - t0}))
+"""
+
+
+def cpu_baseline_openmp():
+    """The same oracle source built with OpenMP over rows (bitwise the serial results) on all host
+    cores, in a child process: three LB time steps of the 1024 x 1024 lattice after one untimed."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, VLB_ORACLE_OPENMP="1", OMP_NUM_THREADS=str(cores))
+    try:
+        r = subprocess.run([sys.executable, "-c", _OMP_CHILD, ROOT], env=env, cwd=ROOT, capture_output=True,
+                           text=True, timeout=600)
+        dt = json.loads(r.stdout.strip().splitlines()[-1])["dt"]
+    except Exception as e:                     # the figure is context only: report why it is missing
+        return {"error": str(e)[:200]}
+    return {"value": 3 * 1024 * 1024 / dt / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle, OpenMP over rows (same source, bitwise the serial results)",
+            "sample": "3 LB time steps of the 1024x1024 workload after one untimed (%.1f s)" % dt}
+
+
 KERNEL_NAMES = {"auto": "k_fused (fused lattice step, one cell per thread)",
                 "pair": "k_fused_pair (fused lattice step, two cells per thread)",
                 "tile": "k_fused (fused lattice step, one cell per thread)",
@@ -732,6 +763,7 @@ def main():
         return
     frest_err = frest_error_check()
     cpu = None if args.no_cpu_baseline else cpu_baseline_sample()
+    cpu_omp = None if args.no_cpu_baseline else cpu_baseline_openmp()
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -740,7 +772,7 @@ def main():
                        "lb_steps_per_step": LB_STEPS_PER_STEP,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_openmp": cpu_omp, "e2e": e2e, "clocks": clk.summary(),
             "gpu_launches": launches_per_step * LB_STEPS_PER_STEP * args.steps,
             "kernel_timing": "roofline durations from a second pass with events around each launch",
             "frest_err_vs_fp64": {"value": frest_err, "workload": "64x64, 200 steps, 20 readouts"},

@@ -21,16 +21,20 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vlb_oracle.c")
-_LIB = os.path.join(_HERE, "libvlb_oracle.so")
+# VLB_ORACLE_OPENMP=1 (read at import) loads the same source built with OpenMP: its per-cell loops
+# write only their own cell and every sum stays serial, so the results are bitwise the serial ones
+_OPENMP = os.environ.get("VLB_ORACLE_OPENMP", "") == "1"
+_LIB = os.path.join(_HERE, "libvlb_oracle_omp.so" if _OPENMP else "libvlb_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile vlb_oracle.c into an in-tree shared library (gcc, -O2, no FP contraction)."""
+    """Compile vlb_oracle.c into an in-tree shared library (gcc, -O2, no FP contraction; with
+    -fopenmp when VLB_ORACLE_OPENMP=1)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "vlb_oracle.h"))):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared"]
+                              + (["-fopenmp"] if _OPENMP else []) + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 

@@ -303,6 +303,7 @@ void orc_forces(const orc_params* p, const orc_ring* rings, int n_rings, const d
      *                              - kappa d_i P_k d_j P_k
      * Reading Q7: the printed gradient term carries no kappa; kappa is restored so that
      * the stress has the units of the free-energy density. */
+    #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
@@ -323,6 +324,7 @@ void orc_forces(const orc_params* p, const orc_ring* rings, int n_rings, const d
                             - ka * (dyPx * dyPx + dyPy * dyPy);                       /* yy */
         }
 
+    #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
@@ -352,6 +354,7 @@ void orc_moments(const orc_params* p, const double* h, const double* F, double* 
 {
     /* Eq. rhoDef, Eq. vDef with the Guo half-force correction (Reading Q2). */
     size_t N = (size_t)p->nx * p->ny;
+    #pragma omp parallel for
     for (size_t i = 0; i < N; ++i) {
         double r = 0.0, jx = 0.0, jy = 0.0;
         for (int n = 0; n < 9; ++n) {
@@ -369,6 +372,7 @@ static void velocity_gradient(const orc_params* p, const double* u, double* psi,
 {
     int nx = p->nx, ny = p->ny;
     size_t N = (size_t)nx * ny;
+    #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
@@ -386,6 +390,7 @@ void orc_rhs(const orc_params* p, const double* sigma, const double* P, const do
 {
     int nx = p->nx, ny = p->ny;
     size_t N = (size_t)nx * ny;
+    #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
@@ -494,6 +499,7 @@ int orc_step(const orc_params* p, const orc_ring* rings, int n_rings,
     /* 6. BGK collision with Guo forcing (Eq. LB, Eq. BGK; Readings Q1, Q2):
      * h* = h - (h - h^eq)/tau + (1 - 1/(2 tau)) w_n [3(c_n - u) + 9 (c_n.u) c_n] . F */
     double tau = p->tau;
+    #pragma omp parallel for
     for (size_t i = 0; i < N; ++i) {
         double ux = u[i], uy = u[N + i], r = rho[i], Fx = F[i], Fy = F[N + i];
         double uu = ux * ux + uy * uy;
@@ -508,6 +514,7 @@ int orc_step(const orc_params* p, const orc_ring* rings, int n_rings,
     }
     /* 7. streaming h_n(r + c_n, t+1) = h*_n(r); half-way bounce-back at walls (App. C): a
      * population whose link crosses a wall returns to its cell as the opposite one. */
+    #pragma omp parallel for
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             size_t i = (size_t)y * nx + x;
@@ -527,25 +534,33 @@ int orc_step(const orc_params* p, const orc_ring* rings, int n_rings,
     /* 9. predictor-corrector (Reading Q3: Heun) on (sigma, P) jointly. */
     int sub = p->diffusion_substeps;
     orc_rhs(p, sigma, P, u, psi, om, sub == 0, ds0, dP0);
+    #pragma omp parallel for
     for (size_t i = 0; i < 3 * N; ++i) s1[i] = sigma[i] + ds0[i];
+    #pragma omp parallel for
     for (size_t i = 0; i < 2 * N; ++i) P1[i] = P[i] + dP0[i];
     orc_rhs(p, s1, P1, u, psi, om, sub == 0, ds1, dP1);
+    #pragma omp parallel for
     for (size_t i = 0; i < 3 * N; ++i) sigma[i] += 0.5 * (ds0[i] + ds1[i]);
+    #pragma omp parallel for
     for (size_t i = 0; i < 2 * N; ++i) P[i] += 0.5 * (dP0[i] + dP1[i]);
     if (sub > 0) {
         /* Reading Q13: explicit stress diffusion beyond the Heun bound, in s sub-steps. */
         orc_params q = *p;
         q.Dp = p->Dp / sub;
         for (int k = 0; k < sub; ++k) {
+            #pragma omp parallel for collapse(2)
             for (int c = 0; c < 3; ++c)
                 for (int y = 0; y < ny; ++y)
                     for (int x = 0; x < nx; ++x)
                         ds0[c * N + (size_t)y * nx + x] = q.Dp * Lap(&q, sigma + c * N, x, y, BC_NEUMANN);
+            #pragma omp parallel for
             for (size_t i = 0; i < 3 * N; ++i) s1[i] = sigma[i] + ds0[i];
+            #pragma omp parallel for collapse(2)
             for (int c = 0; c < 3; ++c)
                 for (int y = 0; y < ny; ++y)
                     for (int x = 0; x < nx; ++x)
                         ds1[c * N + (size_t)y * nx + x] = q.Dp * Lap(&q, s1 + c * N, x, y, BC_NEUMANN);
+            #pragma omp parallel for
             for (size_t i = 0; i < 3 * N; ++i) sigma[i] += 0.5 * (ds0[i] + ds1[i]);
         }
     }
