@@ -197,6 +197,26 @@ int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, i
 int lb_series(lb_handle* h, double* dst, int32_t max_rows, int32_t* rows_written);
 int32_t lb_series_row_len(const lb_handle* h);
 
+/*
+ * Checkpoint and resume (the paper has no counterpart: its runs are single jobs).  lb_save
+ * finishes the handle's queued work and writes to the file `path` a raw snapshot of everything
+ * a step carries over to the next: both state buffers and which one is current, the step
+ * counter, the control block, the readout partials and series ring buffer and, with rings, the
+ * ring records (parameters, trap protocol and its origin, work-box extents), both node position
+ * buffers, the per-node cell, fraction and force, the work boxes, the tail's tickets and claims
+ * and the node partial sums.  Native byte order; a file is read only by this library version.
+ * lb_load reads such a file into a handle that was created with equal lb_params (every field)
+ * and given the same ring layout by lb_set_body (the same number of rings and nodes per ring;
+ * positions, ring parameters and protocol then come from the file) and replaces its state, so
+ * that stepping on continues exactly (bitwise) as the saved run would have.  Kernel choice and
+ * node-tail setting stay the handle's own.  Neither call may run while the handle is stepped
+ * by an lb_batch (sync the batch first).  Errors: LB_EINVAL (null argument, a file that cannot
+ * be written or read, or that belongs to another version, parameter set or ring layout; the
+ * handle is then unchanged), LB_ECUDA.  Synchronises the stream.
+ */
+int lb_save(lb_handle* h, const char* path);
+int lb_load(lb_handle* h, const char* path);
+
 /* Restoring force of ring `ring` for the recorded rows: host FP64 [max_k][2]. */
 int lb_restoring_force(lb_handle* h, int32_t ring, double* dst, int32_t max_k, int32_t* k_written);
 

@@ -335,6 +335,7 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     h->sweep_chunk = sweep_chunk(p.nx, p.ny, n_sm);
     h->n_partials = fused_ctas(p.nx, p.ny);
     const int partial_cap = std::max(h->n_partials, sweep_ctas(p.nx, p.ny, h->sweep_chunk));
+    h->partial_cap = partial_cap;
     h->series_cap = p.max_samples;
     cudaError_t e;
     if ((e = cudaMalloc(&h->lut, sizeof(float) * lut.size())) != cudaSuccess ||

@@ -25,6 +25,7 @@ struct lb_handle {
     float2* lut = nullptr;
     Ctl* ctl = nullptr;
     double* partials = nullptr;
+    int partial_cap = 0;                    // capacity of partials (tiles of the largest launch)
     int n_partials = 0;                     // partial sums written by the last lattice launch
     int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP
     int sweep_chunk = 0;

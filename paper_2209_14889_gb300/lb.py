@@ -89,6 +89,8 @@ def lib():
             "lb_write_field": (ctypes.c_int, [_H, i32, vp, sz, i32]),
             "lb_series": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
             "lb_series_row_len": (i32, [_H]),
+            "lb_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
+            "lb_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
             "lb_restoring_force": (ctypes.c_int, [_H, i32, vp, i32, ctypes.POINTER(i32)]),
             "lb_timing": (ctypes.c_int, [_H, i32]),
             "lb_kernel_time": (ctypes.c_int, [_H, dp, ctypes.POINTER(i64), dp,
@@ -325,6 +327,14 @@ class Solver:
                                             ctypes.byref(g), ctypes.byref(m)))
         return {"fused_ms": f.value, "fused_launches": n.value, "node_ms": g.value,
                 "node_launches": m.value}
+
+    def save(self, path: str):
+        """Checkpoint the whole state to a file (lb_save)."""
+        _check(self.h, lib().lb_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Resume from a checkpoint of a solver with equal parameters and ring layout (lb_load)."""
+        _check(self.h, lib().lb_load(self.h, os.fsencode(path)))
 
     @property
     def bytes_per_cell(self) -> float:
