@@ -212,7 +212,8 @@ int32_t lb_series_row_len(const lb_handle* h);
  * node-tail setting stay the handle's own.  Neither call may run while the handle is stepped
  * by an lb_batch (sync the batch first).  Errors: LB_EINVAL (null argument, a file that cannot
  * be written or read, or that belongs to another version, parameter set or ring layout; the
- * handle is then unchanged), LB_ECUDA.  Synchronises the stream.
+ * handle is then unchanged), LB_ESTATE (lb_save before lb_init_fields), LB_ECUDA.  Synchronises
+ * the stream.
  */
 int lb_save(lb_handle* h, const char* path);
 int lb_load(lb_handle* h, const char* path);

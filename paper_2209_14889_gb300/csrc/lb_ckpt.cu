@@ -139,6 +139,7 @@ int lb_save(lb_handle* h, const char* path)
 {
     if (!h) return LB_EINVAL;
     if (!path) return set_err(h, LB_EINVAL, "lb_save: null path");
+    if (!h->fields_ready) return set_err(h, LB_ESTATE, "lb_save: lb_init_fields not called");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_err(h, e, "lb_save: cudaStreamSynchronize");
     const std::vector<Buf> bufs = snapshot_bufs(h);
