@@ -3,14 +3,16 @@
  * tensorial viscoelastic fluid (Floyd, Vaikuntanathan, Dinner, arXiv 2209.14889).
  *
  * One time step (Fig. 2; every field is updated from the state at t):
- *   node forces f_a = -grad U (App. A, Eq. Const, with a constant pull in place of the trap),
+ *   node forces f_a = -grad U (App. A, Eq. Const, plus a constant pull and/or the harmonic trap
+ *   of Eq. Utrap with its pulling protocol),
  *   spreading f_IB = sum_a f_a K(R_a - r) (App. A), polymer force f^p = div sigma^p (Sec. II B),
  *   Ericksen force f^E = div sigma^E (Sec. II C 1), D2Q9 BGK collide + stream with the Guo
  *   body force (Sec. II A, Eq. LB, Eq. BGK), predictor-corrector updates of sigma^p
  *   (Eq. StiffCons with C~(P) of App. B) and of P (Eq. BE), and overdamped advection of the
  *   nodes by the interpolated velocity (App. A).
  *
- * Units: lattice units (dx = dt = 1, c_s^2 = 1/3).  Periodic lattice in x and y.
+ * Units: lattice units (dx = dt = 1, c_s^2 = 1/3).  Periodic in x and y unless walls are set
+ * (App. C; see "Walls" below).
  * Fields are [y][x] planes, x fastest, FP32 on the device.
  *
  * Ownership: the handle owns every device buffer it allocates (cudaMalloc in lb_create and
