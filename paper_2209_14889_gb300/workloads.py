@@ -142,3 +142,60 @@ def cfg4(seed: int = 4, n_instances: int = 256, sides=(128, 192, 256, 384, 512),
                  diffusion_substeps=sub)
         out.append(w)
     return out
+
+
+# ------------------------------------------------------------------------------------------
+# The paper's own setup (App. C, Tables I-IV) in lattice units
+# ------------------------------------------------------------------------------------------
+
+# SI values of Tables I (lattice), II (droplet and protocol) and IV (viscoelastic stress; the
+# Beris-Edwards parameters of Table III are already dimensionless and sit in DEFAULT_PHYSICS)
+PAPER_SI = dict(dx=4e-8, dt=8e-6, rho=2e7, eta_s=1e-3, nx=250, ny=250, n_steps=187500,
+                l_eq=2e-8, R=5e-7, k_spring=1e-5, eps_angle=1e-20, k_trap=1e-6, d_pull=4e-6, T_pull=0.2,
+                C=0.01, eta_p=0.1, Dp=1e-13, K=(0.01, 0.005, 0.005, 0.005))
+
+
+def lattice_units(si: dict = PAPER_SI) -> dict:
+    """The paper's SI parameters in lattice units, with dx, dt and the solvent density as the units
+    of length, time and mass density.  tau = 1/2 + 3 nu dt / dx^2 (Eq. BGK, c_s^2 = 1/3); a stress or
+    modulus sigma [Pa] becomes sigma dt^2 / (rho dx^2), a viscosity eta [Pa s] eta dt / (rho dx^2), a
+    diffusivity D [m^2/s] D dt / dx^2.  Reading for the two-dimensional model (the paper states its
+    droplet constants in three-dimensional units): a lattice cell is dx deep, so a force [N] acts on
+    a layer of cells and a stiffness k [N/m] becomes k dt^2 / (rho dx^3), a bending stiffness eps
+    [N m] eps dt^2 / (rho dx^5)."""
+    dx, dt, rho = si["dx"], si["dt"], si["rho"]
+    stress = dt * dt / (rho * dx * dx)
+    return dict(
+        tau=0.5 + 3.0 * si["eta_s"] / rho * dt / (dx * dx),
+        C=si["C"] * stress, K=tuple(k * stress for k in si["K"]),
+        eta_p=si["eta_p"] * dt / (rho * dx * dx), Dp=si["Dp"] * dt / (dx * dx),
+        R=si["R"] / dx, l_eq=si["l_eq"] / dx, d_pull=si["d_pull"] / dx, T_pull=si["T_pull"] / dt,
+        k_spring=si["k_spring"] * dt * dt / (rho * dx ** 3), eps_angle=si["eps_angle"] * dt * dt / (rho * dx ** 5),
+        k_trap=si["k_trap"] * dt * dt / (rho * dx ** 3), nx=si["nx"], ny=si["ny"], n_steps=si["n_steps"])
+
+
+def paper_setup(model: str = "scalar", seed: int = 1, every: int = 100, **si_overrides) -> dict:
+    """The paper's pulling experiment with its default parameters (App. C): a 250^2 closed box, the
+    droplet (radius 0.5 um, nodes 20 nm apart) centred 2 um left of the box centre on its mid-line,
+    held by the trap, dragged 4 um along x over 0.2 s after 30 steps of equilibration (sigmoid width
+    30 steps) and left to recoil to 187 500 steps; Table IV's scalar modulus (model="scalar") or its
+    K^x with the Beris-Edwards field of Table III (model="tensorial", director along x, no noise).
+    si_overrides replace entries of PAPER_SI (e.g. Dp=1e-15, R=3.2e-7, T_pull=0.1)."""
+    si = dict(PAPER_SI)
+    si.update(si_overrides)
+    lu = lattice_units(si)
+    n_nodes = int(round(2.0 * math.pi * lu["R"] / lu["l_eq"]))
+    x_mid, y_mid = (lu["nx"] - 1) / 2.0, (lu["ny"] - 1) / 2.0
+    centre = (x_mid - 2e-6 / si["dx"], y_mid)
+    trap = dict(k=lu["k_trap"], dx=lu["d_pull"], dy=0.0, t_eq=30, pull=float(round(lu["T_pull"])), width=30)
+    rings = [ring(n_nodes, lu["R"], centre, k_spring=lu["k_spring"], eps_angle=lu["eps_angle"],
+                  pull_force=0.0, trap=trap)]
+    if model == "scalar":
+        physics = scalar_physics(lu["C"])
+    elif model == "tensorial":
+        physics = dict(K=lu["K"])
+    else:
+        raise ValueError("model must be 'scalar' or 'tensorial'")
+    physics.update(tau=lu["tau"], eta_p=lu["eta_p"], Dp=lu["Dp"], walls_x=1, walls_y=1)
+    return make(lu["nx"], lu["ny"], rings=rings, seed=seed, noise_amp=0.0, steps=lu["n_steps"], every=every,
+                **physics)
