@@ -14,6 +14,13 @@ roofline  fused lattice kernel (the node step runs in its tail; --separate-nodes
           the same steps), against the measured HBM copy bandwidth.
 e2e       the same metric through the C ABI with host buffers: per step the whole state is
           uploaded from pinned host memory, ten steps run, and the readout row is copied back.
+cpu_baseline         the FP64 oracle on one host core, one LB step of the 1024 x 1024 workload;
+cpu_baseline_openmp  the same oracle source with OpenMP on all host cores (bitwise the same).
+forms     the 4096^2 sixteen-ring workload in FP32, in the FP16/BF16 storage form and with the
+          scalar model; the batched form (256 lattices); the protocol form (Return against D_p,
+          radius and pulling time in 250^2 closed boxes, scalar model); the anisotropy form
+          (Return, deflection and rotation against alpha and theta0, tensorial model); the
+          learned form (a 16-step U-Net stepper with residual checks).
 --impl reference   the FP64 CPU oracle on the host cores, on a bounded sample (512 x 512 with
           the same physics and ring), one LB time step per bench step.
 """
