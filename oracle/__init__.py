@@ -1,7 +1,8 @@
 """FP64 CPU oracle for the fused IB-LB viscoelastic time step (arXiv 2209.14889).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this package.
+``cpu_baseline`` legs (serial, and OpenMP in a child process) and ``--impl reference`` leg of
+``bench.py`` may import this package.
 The product path (``paper_2209_14889_gb300``) never imports it, and it never imports
 the product path.  The arithmetic lives in ``vlb_oracle.c`` (plain C99, FP64); this
 module only builds it and marshals numpy arrays.
