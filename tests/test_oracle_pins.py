@@ -878,3 +878,107 @@ def test_ericksen_stress_balances_beris_edwards_power():
     r32, r64 = _ericksen_power_residual(32), _ericksen_power_residual(64)
     assert r64 < 3e-3
     assert 3.5 < r32 / r64 < 4.5                              # second order in dx
+
+
+# ----------------------------------------------------------------------------------------
+# The restoring-force readout (Sec. III A: f^p = div sigma^p interpolated to the nodes with the
+# kernel of App. A and summed over the ring) and the Heun advance of the nodes (App. A)
+# ----------------------------------------------------------------------------------------
+
+def _first_moment(X):
+    """sum_j (X - j) phi(X - j) over the four support cells of the cosine kernel of App. A,
+    written out: with f = X - floor(X) the offsets are f + 1, f, f - 1, f - 2, the cosines pair
+    up as -sin, cos, sin, -cos of pi f / 2, and the sum is f - 1/2 + (cos - sin)(pi f / 2) / 2.
+    The kernel is a partition of unity but its first moment is not zero (it vanishes only at
+    f = 0 and f = 1/2), which tells it apart from kernels with a vanishing first moment."""
+    f = np.asarray(X) - np.floor(X)
+    return f - 0.5 + 0.5 * (np.cos(0.5 * np.pi * f) - np.sin(0.5 * np.pi * f))
+
+
+def _frest_workload(n=48):
+    # a ring with spring, bending and pull forces (f_IB != 0) in an oriented fluid with noisy P
+    # and the Ericksen force on (f^E != 0 near the ring), centred away from the periodic seam
+    return W.make(n, n, rings=[W.ring(20, 5.0, (23.3, 24.6), pull_force=1e-3, pull_angle=0.4)],
+                  noise_amp=0.05, lambda_steps=50.0, Dp=0.05)
+
+
+def test_restoring_force_of_a_uniform_polymer_force():
+    # sigma^p linear in x and y around the ring: the central differences give a uniform
+    # f^p = (a + b, c + d) on every support cell, so by the partition of unity of phi the
+    # readout is N f^p exactly, whatever the node positions.
+    n, N = 48, 20
+    w = _frest_workload(n)
+    sim = O.Sim.from_workload(w)
+    y, x = np.mgrid[0:n, 0:n].astype(float) - 24.0
+    a, b, c, d = 3e-4, -1e-4, 2e-4, 5e-5
+    sim.sigma[0] = a * x
+    sim.sigma[1] = d * y
+    sim.sigma[2] = b * y + c * x
+    X0 = sim.X.copy()
+    sim.step(1, every=1)
+    fr = np.array(sim.series[0][6:8])
+    expect = N * np.array([a + b, c + d])
+    assert np.abs(fr - expect).max() <= 1e-12 * np.abs(expect).max()
+    # the total force F differs from f^p at the nodes (ring forces, Ericksen force), and f^p
+    # summed over the cells is not the interpolated sum: either readout would fail the pin
+    F, fp = O.forces(sim.p, sim.rings, np.stack([a * x, d * y, b * y + c * x]), O.Sim.from_workload(w).P, X0)
+    assert np.abs(O.interp(sim.p, F, X0).sum(0) - expect).max() > 1e-2 * np.abs(expect).max()
+    assert np.abs(fp.sum((1, 2)) - expect).max() > 1e-2 * np.abs(expect).max()
+
+
+def test_restoring_force_of_a_linear_polymer_force():
+    # sigma_xx = a x^2 / 2 and sigma_yy = b y^2 / 2 around the ring: f^p = (a x, b y) exactly on
+    # the support cells (central differences are exact on quadratics), and interpolating a
+    # linear field with the cosine kernel returns the field at X minus the kernel's first
+    # moment, so F_rest = sum_a (a (X_a - m(X_a)), b (Y_a - m(Y_a))) in centred coordinates.
+    # A wrong kernel weight or width changes m and fails this, as does interpolating F.
+    n = 48
+    w = _frest_workload(n)
+    sim = O.Sim.from_workload(w)
+    y, x = np.mgrid[0:n, 0:n].astype(float) - 24.0
+    a, b = 2e-4, -3e-4
+    sim.sigma[0] = 0.5 * a * x * x
+    sim.sigma[1] = 0.5 * b * y * y
+    sim.sigma[2] = 0.0
+    X0 = sim.X.copy()
+    sim.step(1, every=1)
+    fr = np.array(sim.series[0][6:8])
+    expect = np.array([(a * (X0[:, 0] - 24.0 - _first_moment(X0[:, 0]))).sum(),
+                       (b * (X0[:, 1] - 24.0 - _first_moment(X0[:, 1]))).sum()])
+    assert np.abs(fr - expect).max() <= 1e-12 * np.abs(expect).max()
+    # the first-moment term matters at this size (a kernel without it would be off by this much)
+    off = np.array([(a * _first_moment(X0[:, 0])).sum(), (b * _first_moment(X0[:, 1])).sum()])
+    assert np.abs(off).max() > 1e-6 * np.abs(expect).max()
+
+
+def _rotation_populations(n, w0, xc, yc):
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    u = np.stack([-w0 * (y - yc), w0 * (x - xc)])
+    return O.equilibrium(np.ones((n, n)), u)
+
+
+def test_node_advance_is_heun_on_the_frozen_velocity():
+    # App. A with the predictor-corrector read as Heun: R* = R + V(R), R' = R + (V(R) + V(R*))/2
+    # with V the interpolated u(t).  A rigid rotation u = w0 J (r - r_c) (J the quarter turn),
+    # imposed as the equilibrium populations at rho = 1 with every force zero (no spring, bend or
+    # pull; sigma = 0; uniform P), interpolates to V(R) = w0 J (R - r_c - m(R)) with m the
+    # kernel's first moment per axis.  Euler (R + V(R)) and R + V(R*) each miss the update by
+    # (V(R*) - V(R))/2 ~ w0 |V| and fail.
+    n, w0, xc, yc = 64, 0.01, 32.0, 31.5
+    w = W.make(n, n, rings=[W.ring(24, 10.0, (31.7, 32.2), k_spring=0.0, eps_angle=0.0, pull_force=0.0)],
+               noise_amp=0.0, lambda_steps=50.0, Dp=0.05)
+    sim = O.Sim.from_workload(w)
+    sim.h = _rotation_populations(n, w0, xc, yc)
+    X = sim.X.copy()
+    sim.step(1)
+
+    def V(R):
+        m = _first_moment(R)
+        return np.stack([-w0 * (R[:, 1] - yc - m[:, 1]), w0 * (R[:, 0] - xc - m[:, 0])], axis=1)
+
+    V0 = V(X)
+    Xs = X + V0
+    heun = X + 0.5 * (V0 + V(Xs))
+    assert np.abs(sim.X - heun).max() <= 1e-13
+    assert np.abs(sim.X - (X + V0)).max() > 1e-5          # Euler would be this far off
+    assert np.abs(sim.X - (X + V(Xs))).max() > 1e-5
