@@ -238,6 +238,7 @@ def measure_forms(args, lb, W, torch):
         fused_s = kt["fused_ms"] * 1e-3 / max(kt["fused_launches"], 1)
         gbs = s.bytes_per_cell * cells / fused_s / 1e9
         out[name] = {"value": cells * LB_STEPS_PER_STEP * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                     "kernel": s.lattice_kernel,
                      "bytes_per_cell_step": s.bytes_per_cell, "fused_mean_us": fused_s * 1e6,
                      "node_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1),
                      "roofline_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "steps": steps}

@@ -178,7 +178,9 @@ int lb_readout(lb_handle* h, int32_t field, void* dst, size_t bytes, int32_t dst
  * array compiled into the library: 3 x 2^20 FP32 (12 MiB), held on every GPU that loads the
  * library until the process exits.  Lattices above 2^20 cells return LB_EINVAL.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before capturing the stream into a graph.  All calls share the array: calls whose
+ * first call before capturing the stream into a graph; threads making their first calls on a
+ * device at the same time may each look it up and store the same value, which is harmless.
+ * The call itself allocates nothing on any call.  All calls share the array: calls whose
  * work overlaps on the GPU (several handles, streams or threads at once) race on it.
  * Synchronises the stream.
  */
@@ -208,13 +210,14 @@ int32_t lb_series_row_len(const lb_handle* h);
  * buffers, the per-node cell, fraction and force, the work boxes, the tail's tickets and claims
  * and the node partial sums.  Native byte order; a file is read only by this library version.
  * lb_load reads such a file into a handle that was created with equal lb_params (every field)
- * and given the same ring layout by lb_set_body (the same number of rings and nodes per ring;
- * positions, ring parameters and protocol then come from the file) and replaces its state, so
+ * and given the same rings by lb_set_body (the same number of rings and nodes per ring, and
+ * equal spring constant, angle constant, rest length, pull and trap protocol per ring; the node
+ * positions and the trap's origin then come from the file) and replaces its state, so
  * that stepping on continues exactly (bitwise) as the saved run would have.  Kernel choice and
  * node-tail setting stay the handle's own.  Neither call may run while the handle is stepped
  * by an lb_batch (sync the batch first).  Errors: LB_EINVAL (null argument, a file that cannot
- * be written or read, or that belongs to another version, parameter set or ring layout; the
- * handle is then unchanged), LB_ESTATE (lb_save before lb_init_fields), LB_ECUDA.  Synchronises
+ * be written or read, or that belongs to another version, parameter set, ring layout or ring
+ * parameters; the handle is then unchanged), LB_ESTATE (lb_save before lb_init_fields), LB_ECUDA.  Synchronises
  * the stream.
  */
 int lb_save(lb_handle* h, const char* path);
@@ -238,14 +241,23 @@ int lb_kernel_time(lb_handle* h, double* fused_ms, int64_t* fused_launches, doub
  * (any lattice).  LB_KERNEL_PAIR: the same tiles with two neighbouring cells per thread on
  * paired FP32 instructions (any lattice).  LB_KERNEL_SWEEP: column strips swept row by row,
  * rows streamed by asynchronous bulk copies (needs nx % 4 == 0, nx >= 256, ny >= 16, FP32 state,
- * else LB_EINVAL).  LB_KERNEL_AUTO (default): the kernel measured fastest on GB300, currently
- * the one-cell tile kernel.
+ * else LB_EINVAL).  LB_KERNEL_STRIP: one warp per strip of 32 columns (24 stored) swept along y,
+ * stencil neighbours from registers and warp shuffles, no shared-memory staging; the node step
+ * in the separate node kernel (periodic lattices with nx >= 64, ny >= 32, either precision,
+ * either model, else LB_EINVAL); its fields and nodes equal the tile kernel's bit for bit.
+ * LB_KERNEL_AUTO (default): the kernel measured fastest on GB300 for the lattice: the strip
+ * kernel where it applies and the lattice fills at least four waves of its CTAs (4096^2 and
+ * larger), else the one-cell tile kernel (with the node step in its tail).
  */
 #define LB_KERNEL_AUTO 0
 #define LB_KERNEL_TILE 1
 #define LB_KERNEL_SWEEP 2
 #define LB_KERNEL_PAIR 3
+#define LB_KERNEL_STRIP 4
 int lb_set_kernel(lb_handle* h, int32_t kernel);
+/* The lattice kernel lb_step launches for this handle: LB_KERNEL_TILE, _PAIR, _SWEEP or _STRIP
+ * (LB_KERNEL_AUTO resolved), or LB_EINVAL for a null handle. */
+int32_t lb_lattice_kernel(const lb_handle* h);
 
 /*
  * Where lb_step runs the node step (App. A: interpolation of u onto the nodes, their advection
@@ -254,7 +266,8 @@ int lb_set_kernel(lb_handle* h, int32_t kernel);
  * per step: once the last tile whose region meets a ring's work box is done, that ring's node
  * blocks run in tiles that finish later while the other tiles still run.  enable = 0: a separate
  * node kernel after each lattice kernel.  Both compute the same values bit for bit;
- * LB_KERNEL_SWEEP always takes the separate kernel.  LB_EINVAL for other values.
+ * LB_KERNEL_SWEEP and LB_KERNEL_STRIP always take the separate kernel.  LB_EINVAL for other
+ * values.
  */
 int lb_set_node_tail(lb_handle* h, int32_t enable);
 

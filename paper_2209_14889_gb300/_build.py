@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
-SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu", "lb_diffuse.cu",
+SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_strip.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu", "lb_diffuse.cu",
            "lb_batch.cu", "lb_unet.cu", "lb_learned.cu", "lb_ckpt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic contraction of a product and a sum into one FMA.  The one-cell

@@ -114,6 +114,15 @@ FusedArgs fused_args(lb_handle* h)
     return a;
 }
 
+// the lattice kernel of lb_step is the warp-strip kernel: chosen, or LB_KERNEL_AUTO where it
+// applies and measured faster than the tile kernel
+bool uses_strip(const lb_handle* h)
+{
+    if (h->kernel == LB_KERNEL_STRIP) return true;
+    return h->kernel == LB_KERNEL_AUTO && strip_eligible(h->p.nx, h->p.ny, h->p.walls_x || h->p.walls_y) &&
+           strip_preferred(h->p.nx, h->p.ny, h->n_sm);
+}
+
 NodeArgs node_args(lb_handle* h, int advance)
 {
     NodeArgs a;
@@ -333,8 +342,11 @@ int lb_create(const lb_params* pin, void* stream, lb_handle** out)
     int dev = 0, n_sm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     h->sweep_chunk = sweep_chunk(p.nx, p.ny, n_sm);
+    h->n_sm = n_sm;
+    h->strip_chunk = strip_chunk(p.nx, p.ny, n_sm);
     h->n_partials = fused_ctas(p.nx, p.ny);
-    const int partial_cap = std::max(h->n_partials, sweep_ctas(p.nx, p.ny, h->sweep_chunk));
+    const int partial_cap = std::max(std::max(h->n_partials, sweep_ctas(p.nx, p.ny, h->sweep_chunk)),
+                                     strip_ctas(p.nx, p.ny, h->strip_chunk));
     h->partial_cap = partial_cap;
     h->series_cap = p.max_samples;
     cudaError_t e;
@@ -566,19 +578,21 @@ int lb_step(lb_handle* h, int64_t n)
             e1 = ev_get(h->ev_fused, h->ev_fused_used);
             if (e0) cudaEventRecord(e0, h->stream);
         }
-        // LB_KERNEL_AUTO takes the one-cell tile kernel: measured fastest on GB300 (1024^2:
-        // 74 us per launch against 88 us for the paired kernel, whose 126 registers leave two
-        // CTAs per SM, and 121 us for the sweep)
         const bool sweep = h->kernel == LB_KERNEL_SWEEP;
         const bool pair = h->kernel == LB_KERNEL_PAIR;
+        const bool strip = uses_strip(h);
         // consecutive kernels overlap by programmatic dependent launch, except when per-kernel
         // timing brackets each launch with events
         const bool pdl = !h->timing;
         // the tile kernels run the node step in their tail: one launch per step
-        const bool tail = h->node_tail && !sweep;
+        const bool tail = h->node_tail && !sweep && !strip;
         if (sweep) {
             CK(h, launch_sweep(fa, h->sweep_chunk, h->stream));
             h->n_partials = sweep_ctas(h->p.nx, h->p.ny, h->sweep_chunk);
+        } else if (strip) {
+            fa.t = h->t;
+            CK(h, launch_strip(fa, h->strip_chunk, h->stream, pdl));
+            h->n_partials = strip_ctas(h->p.nx, h->p.ny, h->strip_chunk);
         } else {
             if (tail) {
                 h->n_partials = fused_ctas(h->p.nx, h->p.ny);
@@ -769,7 +783,7 @@ int32_t lb_launches_per_step(const lb_handle* h)
 {
     if (!h) return 0;
     const int s = h->p.diffusion_substeps;
-    const bool tail = h->node_tail && h->kernel != LB_KERNEL_SWEEP;
+    const bool tail = h->node_tail && h->kernel != LB_KERNEL_SWEEP && !uses_strip(h);
     return (tail ? 1 : 2) + (s > 0 ? s + (s & 1) : 0);
 }
 
@@ -795,7 +809,9 @@ int32_t lb_stiffness_table(double P_cap, float* dst, int32_t max_entries)
 int lb_set_kernel(lb_handle* h, int32_t kernel)
 {
     if (!h) return fail(nullptr, LB_EINVAL, "null handle");
-    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_PAIR) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
+    if (kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_STRIP) return fail(h, LB_EINVAL, "unknown kernel %d", kernel);
+    if (kernel == LB_KERNEL_STRIP && !strip_eligible(h->p.nx, h->p.ny, h->p.walls_x || h->p.walls_y))
+        return fail(h, LB_EINVAL, "the strip kernel needs a periodic lattice with nx >= 64, ny >= 32");
     if (kernel == LB_KERNEL_SWEEP && h->p.precision != LB_FP32)
         return fail(h, LB_EINVAL, "the sweep kernel stores FP32 only");
     if ((kernel == LB_KERNEL_SWEEP || kernel == LB_KERNEL_PAIR) && h->p.model == LB_MODEL_SCALAR)
@@ -806,6 +822,13 @@ int lb_set_kernel(lb_handle* h, int32_t kernel)
         return fail(h, LB_EINVAL, "the sweep kernel needs nx %% 4 == 0, nx >= 256, ny >= 16");
     h->kernel = kernel;
     return LB_OK;
+}
+
+int32_t lb_lattice_kernel(const lb_handle* h)
+{
+    if (!h) return LB_EINVAL;
+    if (uses_strip(h)) return LB_KERNEL_STRIP;
+    return h->kernel == LB_KERNEL_AUTO ? LB_KERNEL_TILE : h->kernel;
 }
 
 double lb_bytes_per_cell(const lb_handle* h)

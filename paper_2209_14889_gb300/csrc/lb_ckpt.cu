@@ -211,11 +211,20 @@ int lb_load(lb_handle* h, const char* path)
                             h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_err(h, e, "lb_load: ring records");
-        for (size_t r = 0; r < ours.size(); ++r)
-            if (theirs[r].n_nodes != ours[r].n_nodes || theirs[r].node_off != ours[r].node_off ||
-                theirs[r].cap_w != ours[r].cap_w || theirs[r].cap_h != ours[r].cap_h ||
-                theirs[r].box_off != ours[r].box_off)
+        for (size_t r = 0; r < ours.size(); ++r) {
+            const vlb::RingDev &a = theirs[r], &b = ours[r];
+            if (a.n_nodes != b.n_nodes || a.node_off != b.node_off || a.cap_w != b.cap_w ||
+                a.cap_h != b.cap_h || a.box_off != b.box_off)
                 return set_err(h, LB_EINVAL, "lb_load: the checkpoint's ring layout differs from the handle's");
+            // the ring's constant physics (spring, angle term, rest length, pull, trap protocol)
+            // must be the handle's: a load restores the state of a run, not its parameters.  The
+            // trap's origin and force slots are state and come from the file.
+            if (a.k_spring != b.k_spring || a.eps_angle != b.eps_angle || a.l_eq != b.l_eq ||
+                a.pull_x != b.pull_x || a.pull_y != b.pull_y || a.trap_k != b.trap_k ||
+                a.trap_dx != b.trap_dx || a.trap_dy != b.trap_dy || a.trap_t_eq != b.trap_t_eq ||
+                a.trap_pull != b.trap_pull || a.trap_w != b.trap_w)
+                return set_err(h, LB_EINVAL, "lb_load: ring " + std::to_string(r) + "'s parameters differ from the handle's");
+        }
     }
     size_t off = 0;
     for (const Buf& b : bufs) {

@@ -225,13 +225,15 @@ int fused_tile_rot(int nx, int ny, double y_top)
 template <int MODE, int PREC, bool PAIR, bool SCALAR = false>
 static cudaError_t launch_one(const FusedArgs& a, dim3 grid, cudaStream_t s, bool pdl)
 {
-    static bool attr_done = false;
+    static unsigned long long attr_done = 0;     // per device
     auto kern = PAIR ? k_fused_pair<MODE, PREC> : k_fused<MODE, PREC, SCALAR>;
-    if (!attr_done) {
+    if (!done_on_device(attr_done)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)TileGeo<TILE_X, TILE_Y>::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
+        if (e != cudaSuccess) {
+            attr_done = 0;
+            return e;
+        }
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;

@@ -27,8 +27,10 @@ struct lb_handle {
     double* partials = nullptr;
     int partial_cap = 0;                    // capacity of partials (tiles of the largest launch)
     int n_partials = 0;                     // partial sums written by the last lattice launch
-    int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP
+    int kernel = 0;                         // LB_KERNEL_AUTO / TILE / SWEEP / PAIR / STRIP
     int sweep_chunk = 0;
+    int strip_chunk = 0;                    // rows per warp of the strip kernel
+    int n_sm = 152;                         // multiprocessors of the handle's device
     double* series = nullptr;
     int series_cap = 0;
     int row_len = 6;

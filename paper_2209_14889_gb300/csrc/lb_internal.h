@@ -145,6 +145,19 @@ struct FusedArgs {
     NodeArgs na;                 // node step of this time step (node_tail)
 };
 
+// Per-device one-time set-up (a function's shared-memory opt-in applies to one device only):
+// returns false the first time it is called for the current device with this flag word, and
+// marks the device; up to 64 devices.  Not thread-safe, like the handles that call it.
+inline bool done_on_device(unsigned long long& flags)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    const unsigned long long bit = 1ull << dev;
+    if (flags & bit) return true;
+    flags |= bit;
+    return false;
+}
+
 // Launchers (return cudaError_t of the launch).
 // pair: the tile kernel with two cells per thread (paired FP32 instructions)
 cudaError_t launch_fused(const FusedArgs& a, int mode, cudaStream_t s, int* grid_ctas, bool pdl = false,
@@ -155,6 +168,13 @@ int sweep_chunk(int nx, int ny, int n_sm);
 int sweep_ctas(int nx, int ny, int chunk);
 cudaError_t launch_sweep(const FusedArgs& a, int chunk, cudaStream_t s);
 cudaError_t launch_nodes(const NodeArgs& a, cudaStream_t s, bool pdl = false);
+// warp-strip kernel (lb_strip.cu): eligibility (walls: any wall), rows per warp chunk, CTA count,
+// launch (FusedArgs::t carries the step index)
+bool strip_eligible(int nx, int ny, int walls);
+bool strip_preferred(int nx, int ny, int n_sm);      // faster than the tile kernel (measured)
+int strip_chunk(int nx, int ny, int n_sm);
+int strip_ctas(int nx, int ny, int chunk);
+cudaError_t launch_strip(const FusedArgs& a, int chunk, cudaStream_t s, bool pdl);
 int fused_ctas(int nx, int ny);
 // the tile row holding the cell row y_top (any real value; wrapped): where the launch order of
 // the tile kernel with the node tail starts

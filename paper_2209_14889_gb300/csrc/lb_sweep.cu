@@ -523,11 +523,13 @@ int sweep_ctas(int nx, int ny, int chunk) { return ((nx + TW - 1) / TW) * ((ny +
 
 cudaError_t launch_sweep(const FusedArgs& a, int chunk, cudaStream_t s)
 {
-    static bool attr_done = false;
-    if (!attr_done) {
+    static unsigned long long attr_done = 0;     // per device
+    if (!done_on_device(attr_done)) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
+        if (e != cudaSuccess) {
+            attr_done = 0;
+            return e;
+        }
     }
     dim3 grid((a.nx + TW - 1) / TW, (a.ny + chunk - 1) / chunk);
     k_sweep<<<grid, NT, SMEM_BYTES, s>>>(a, chunk);

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/lb.h"
+#include "lb_internal.h"
 
 namespace vlb {
 namespace net {
@@ -740,12 +741,14 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16* x, long long ldx, int xoff, con
     a.x = x; a.ldx = ldx; a.xoff = xoff; a.w = w; a.bias = bias; a.y = y; a.yf = yf; a.ldy = ldy; a.yoff = yoff;
     a.B = B; a.H = H; a.W = W; a.Ci = Ci; a.Co = Co; a.act = act;
     if (g_conv_kernel == 1) {
-        static bool attr = false;
-        if (!attr) {
+        static unsigned long long attr = 0;      // per device
+        if (!vlb::done_on_device(attr)) {
             cudaError_t e =
                 cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, t2_smem_bytes(T2_COMAX));
-            if (e != cudaSuccess) return e;
-            attr = true;
+            if (e != cudaSuccess) {
+                attr = 0;
+                return e;
+            }
         }
         if (!g_conv_err) {
             cudaError_t e = cudaMalloc(&g_conv_err, sizeof(int));

@@ -19,7 +19,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_EUNSTABLE, LB_EBODY, LB
 LB_ETIMEOUT = -8
 LB_FP32 = 0
 LB_FP16_BF16 = 1
-LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP, LB_KERNEL_PAIR = 0, 1, 2, 3
+LB_KERNEL_AUTO, LB_KERNEL_TILE, LB_KERNEL_SWEEP, LB_KERNEL_PAIR, LB_KERNEL_STRIP = 0, 1, 2, 3, 4
 FIELDS = {"drho": 0, "ux": 1, "uy": 2, "sxx": 3, "syy": 4, "sxy": 5, "Px": 6, "Py": 7}
 LB_MODEL_TENSORIAL, LB_MODEL_SCALAR = 0, 1
 LB_FIELD_POP0 = 8
@@ -98,6 +98,7 @@ def lib():
             "lb_launches_per_step": (i32, [_H]),
             "lb_set_kernel": (ctypes.c_int, [_H, i32]),
             "lb_set_node_tail": (ctypes.c_int, [_H, i32]),
+            "lb_lattice_kernel": (i32, [_H]),
             "lb_stiffness_table": (i32, [ctypes.c_double, vp, i32]),
             "lb_bytes_per_cell": (ctypes.c_double, [_H]),
             "lb_last_error": (ctypes.c_char_p, [_H]),
@@ -309,8 +310,16 @@ class Solver:
         return buf[:n.value].copy()
 
     def set_kernel(self, kernel: int):
-        """LB_KERNEL_AUTO (the fastest measured), LB_KERNEL_TILE, LB_KERNEL_PAIR or LB_KERNEL_SWEEP."""
+        """LB_KERNEL_AUTO (the fastest measured), LB_KERNEL_TILE, LB_KERNEL_PAIR, LB_KERNEL_SWEEP or
+        LB_KERNEL_STRIP."""
         _check(self.h, lib().lb_set_kernel(self.h, int(kernel)))
+
+    @property
+    def lattice_kernel(self) -> str:
+        """The lattice kernel lb_step launches ("tile", "sweep", "pair" or "strip")."""
+        k = lib().lb_lattice_kernel(self.h)
+        return {LB_KERNEL_TILE: "tile", LB_KERNEL_SWEEP: "sweep", LB_KERNEL_PAIR: "pair",
+                LB_KERNEL_STRIP: "strip"}[k]
 
     def set_node_tail(self, enable: bool):
         """Node step in the tail of the tile kernels (True, default: one launch per step) or in a

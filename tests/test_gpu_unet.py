@@ -177,6 +177,68 @@ def test_network_forward_and_gradients_vs_oracle(conv_kernel):
     assert max(errs.values()) < 5e-3, " ".join("%s=%.1e" % kv for kv in errs.items())
 
 
+def _bf16_output_bound(P, x, seed=11):
+    """First-order bound on the relative L2 error of the network's output when every weight and
+    every stored activation (each activated convolution output and each pooled value) carries a
+    relative rounding error of at most u = 2^-9 (BF16 keeps 8 significant bits; round to nearest).
+    For each such tensor the unrounded FP64 network is run with that tensor alone scaled by
+    (1 + u s), s = +-1 at random per element, and the output changes are added: to first order
+    the errors of different tensors add, and their sum bounds the combined error.  It needs no
+    knowledge of where a kernel rounds beyond what the BF16 format stores."""
+    u = 2.0 ** -9
+    r = np.random.Generator(np.random.PCG64(seed))
+    y0, _ = U.forward(P, x)
+    total = 0.0
+    n_points = 17        # 14 activated convolution outputs and 3 pooled tensors, in call order
+    for k in range(n_points):
+        calls = [0]
+
+        def q(v, k=k):
+            hit = calls[0] == k
+            calls[0] += 1
+            return v * (1.0 + u * r.choice([-1.0, 1.0], size=v.shape)) if hit else v
+        yk, _ = U.forward(P, x, q=q)
+        assert calls[0] == n_points
+        total += np.linalg.norm(yk - y0)
+    for name, _, _, _ in U.LAYERS:
+        Pk = dict(P)
+        Pk[name + ".w"] = P[name + ".w"] * (1.0 + u * r.choice([-1.0, 1.0], size=P[name + ".w"].shape))
+        yk, _ = U.forward(Pk, x)
+        total += np.linalg.norm(yk - y0)
+    return y0, total / np.linalg.norm(y0)
+
+
+def test_network_forward_vs_unrounded_fp64_within_derived_bound(conv_kernel):
+    # The GPU network (BF16 weights and activations, FP32 accumulation) against the FP64 network
+    # with no rounding at all, on the FP32 weights before their BF16 rounding: the difference
+    # must stay within the first-order bound of BF16 storage derived above.  This check does not
+    # rely on the rounded oracle reproducing the kernels' rounding points.
+    torch, lb = _gpu()
+    B, H, W = 2, 32, 32
+    P = U.init_params(seed=5)
+    for name, _, _, _ in U.LAYERS:
+        P[name + ".b"] = np.random.Generator(np.random.PCG64(3 + len(name))).normal(0, 0.05, P[name + ".b"].shape)
+    flat = _flat(P).astype(np.float32)
+    net = lb.Net(B, H, W, seed=1)
+    net.set_params(flat)
+    P64 = _unflat(flat.astype(np.float64))
+    r = np.random.Generator(np.random.PCG64(12))
+    xt, x = bf(torch, r.normal(size=(B, H, W, 16)))
+    y = net.forward(xt)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy().astype(np.float64)
+    yref, bound = _bf16_output_bound(P64, x)
+    err = rel_l2(y, yref)
+    assert 0.0 < err <= bound, (err, bound)
+    # the bound is tight enough to catch a fault: one layer's taps mirrored moves the output by
+    # far more than it
+    Pbad = dict(P64)
+    Pbad["d1b.w"] = P64["d1b.w"][::-1].copy()
+    ybad, _ = U.forward(Pbad, x)
+    assert rel_l2(ybad, yref) > 3 * bound
+    net.close()
+
+
 def test_training_reduces_loss_and_is_deterministic():
     torch, lb = _gpu()
     B, H, W = 2, 32, 32

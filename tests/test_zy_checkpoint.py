@@ -79,7 +79,12 @@ def test_load_refuses_other_parameters_layout_and_bad_files(tmp_path):
     open(short, "wb").write(raw[: len(raw) // 2])
     longer = str(tmp_path / "long.ckpt")
     open(longer, "wb").write(raw + b"x")
-    others = [dict(w, tau=0.9), dict(w, rings=w["rings"][:1]), dict(w, rings=w["rings"][::-1])]
+    r0, r1 = w["rings"][0], w["rings"][1]
+    others = [dict(w, tau=0.9), dict(w, rings=w["rings"][:1]), dict(w, rings=w["rings"][::-1]),
+              # the same layout (rings and node counts) with other ring physics
+              dict(w, rings=[dict(r0, k_spring=2 * r0["k_spring"]), r1]),
+              dict(w, rings=[r0, dict(r1, pull_force=2 * r1["pull_force"])]),
+              dict(w, rings=[r0, dict(r1, eps_angle=0.5 * r1["eps_angle"])])]
     for o in others:
         s = lb.Solver.from_workload(o)
         with pytest.raises(lb.LBError):
