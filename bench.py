@@ -4,7 +4,9 @@ Workload: the 1024 x 1024 periodic lattice with one 256-node ring of radius 24 p
 degrees to the director with 5e-4, D_p = 0.1, relaxation time 200 steps (Tables III-IV
 ratios, synthetic seeded input).  One bench step = lb_step(10): ten LB time steps, i.e. one
 readout period (restoring force, mass, momentum, total force recorded once).  Every rank runs
-its own independent lattice (the path does not shard; replicas only, weak scaling).
+its own independent lattice: the lattice would shard by domain decomposition (one halo exchange
+per step) and a batch by instances, but every call here runs on one GPU, so N ranks are
+replicas (weak scaling, no collective).
 
 value     MLUPS = cells x LB steps / device time, inputs resident in HBM, L2 flushed (256 MB
           write) between timed steps, each timed step bracketed by CUDA events.
@@ -17,10 +19,12 @@ e2e       the same metric through the C ABI with host buffers: per step the whol
 cpu_baseline         the FP64 oracle on one host core, one LB step of the 1024 x 1024 workload;
 cpu_baseline_openmp  the same oracle source with OpenMP on all host cores (bitwise the same).
 forms     the 4096^2 sixteen-ring workload in FP32, in the FP16/BF16 storage form and with the
-          scalar model; the batched form (256 lattices); the protocol form (Return against D_p,
-          radius and pulling time in 250^2 closed boxes, scalar model); the anisotropy form
+          scalar model (state 0.9-1.9 GB: the clean HBM roofline; the warp-strip kernel); the
+          batched form (256 lattices); the protocol form (Return against D_p, radius and pulling
+          time in 250^2 closed boxes, scalar model, lattice-unit parameters); the anisotropy form
           (Return, deflection and rotation against alpha and theta0, tensorial model); the
-          learned form (a 16-step U-Net stepper with residual checks).
+          paper's own setup (App. C parameters, 187 500 steps: Return against D_p and radius);
+          the learned form (a 16-step U-Net stepper with residual checks).
 --impl reference   the FP64 CPU oracle on the host cores, on a bounded sample (512 x 512 with
           the same physics and ring), one LB time step per bench step.
 """
@@ -113,8 +117,14 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # the timed region starts once sampling is live (first line written), within 5 s
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -288,6 +298,65 @@ def _protocol_batch(lb, W, torch, runs, n_steps, d_pull=40.0):
         b.close()
         for s_ in ss:
             s_.close()
+
+
+# The paper's own setup (App. C, Tables I-IV; workloads.paper_setup) swept as in Sec. III B.  The
+# paper plots the Return against D_p and against the droplet radius without printing the values
+# it used; the sweeps are taken around its defaults (D_p = 1e-13 m^2/s, R = 0.5 um): D_p over four
+# decades on both sides within the order of magnitude the paper cites for micellar solutions, R
+# over 0.3-0.8 um (nodes 20 nm apart, at most 251).
+PAPER_DP_SI = [1e-15, 3e-15, 1e-14, 3e-14, 1e-13, 3e-13, 1e-12, 3e-12]
+PAPER_R_SI = [3e-7, 4e-7, 5e-7, 6e-7, 7e-7, 8e-7]
+PAPER_EVERY = 500
+
+
+def _paper_batch(lb, W, torch, overrides, seed0):
+    """One batch of paper_setup boxes (scalar model), each with its SI overrides, run for the
+    paper's 187 500 steps plus one (so that the final state is a readout row); returns the Return
+    of each box, the batch's device time (ms) and the step count."""
+    ws = [W.paper_setup("scalar", seed=seed0 + i, every=PAPER_EVERY, **o) for i, o in enumerate(overrides)]
+    n_steps = ws[0]["steps"] + 1
+    d_pull = ws[0]["rings"][0]["trap"]["dx"]
+    ss = [lb.Solver.from_workload(w, max_samples=n_steps // PAPER_EVERY + 2) for w in ws]
+    b = lb.Batch(ss)
+    try:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        b.step(n_steps)
+        e1.record(torch.cuda.current_stream())
+        b.sync()
+        torch.cuda.synchronize()
+        rets = [lb.return_metric(s_.series(), 0, d_pull, ws[0]["nx"], ws[0]["ny"]) for s_ in ss]
+        return rets, e0.elapsed_time(e1), n_steps
+    finally:
+        b.close()
+        for s_ in ss:
+            s_.close()
+
+
+def measure_paper_setup(args, lb, W, torch):
+    """The paper's pulling experiment at its own parameters (App. C: 250^2 closed box, tau 1.25,
+    157-node droplet of radius 12.5 cells, trap 0.05 dragging it 100 cells over 25 000 steps after
+    30 steps of equilibration, 187 500 steps, scalar modulus of Table IV), as batched runs: the
+    Return (Eq. Rec) against D_p and against the droplet radius (Sec. III B)."""
+    rd, ms_d, n = _paper_batch(lb, W, torch, [dict(Dp=d) for d in PAPER_DP_SI], 900)
+    rr, ms_r, _ = _paper_batch(lb, W, torch, [dict(R=r) for r in PAPER_R_SI], 920)
+    cells = 250 * 250
+    return {"workload": "paper_setup (App. C, Tables I-IV): 250x250 closed box, tau 1.25, droplet 0.5 um "
+                        "(157 nodes), trap 1e-6 N/m dragging 4 um over 0.2 s, %d steps, scalar model" % (n - 1),
+            "Dp_m2_per_s": PAPER_DP_SI, "return_vs_Dp": rd,
+            "radius_m": PAPER_R_SI, "return_vs_radius": rr,
+            "steps": n, "seconds": (ms_d + ms_r) * 1e-3,
+            "value": cells * n * (len(PAPER_DP_SI) + len(PAPER_R_SI)) / ((ms_d + ms_r) * 1e-3) / 1e6,
+            "unit": "MLUPS"}
+
+
+def run_only_paper(args):
+    import torch
+    from paper_2209_14889_gb300 import lb, workloads as W
+    torch.cuda.set_device(0)
+    print(json.dumps({"paper_setup": measure_paper_setup(args, lb, W, torch)}), flush=True)
 
 
 def measure_protocol(args, lb, W, torch):
@@ -502,7 +571,8 @@ def measure_learned(args, lb, torch):
     from paper_2209_14889_gb300 import learned as LR
     side, calls = 256, 64
     t0 = time.perf_counter()
-    data = LR.Dataset(LR.learned_workloads(500, 6, side=side), pairs_per_traj=16)
+    data = LR.Dataset(LR.learned_workloads(500, LEARNED_TRAJ, side=side), pairs_per_traj=2, warmup=64, stride=256,
+                      batch=250)
     t_data = time.perf_counter() - t0
     net = lb.Net(4, side, side, seed=1)
     held = list(range(0, data.n, 8))
@@ -549,11 +619,63 @@ def measure_learned(args, lb, torch):
            "frest_err_vs_fp32": {"value": err, "workload": "64 readouts (every 16 steps), relative L2"},
            "residual_bounds": {"momentum": eps[0], "tendency": eps[1],
                                "validation_accepted": acc_val, "validation_frest_err": err_val},
-           "training": {"pairs": data.n, "data_s": t_data, "adam_steps": len(losses), "train_s": t_train,
+           "training": {"trajectories": LEARNED_TRAJ, "pairs": data.n, "data_s": t_data,
+                        "data": "batched kernel, 250 trajectories at a time, pairs at steps 64 and 320",
+                        "adam_steps": len(losses), "train_s": t_train,
                         "batch": 4, "loss_subset_before": val0, "loss_subset_after": val1}}
     inf.close()
     net.close()
     return out
+
+
+LEARNED_TRAJ = 2000
+
+
+def measure_learned_curve(args, lb, torch, budgets=(45.0, 180.0, 540.0)):
+    """The learned form against its training budget: one network trained on the 2000-trajectory
+    data set in segments (each a cosine schedule of its own), and after each segment the loss on
+    pairs of 64 unseen trajectories, the residual bounds calibrated for 1 % and the calls they
+    accept on a held-out trajectory, the restoring-force error with every call accepted, and the
+    time of 64 calls against 1024 plain steps."""
+    import numpy as np
+    from paper_2209_14889_gb300 import learned as LR
+    side, calls = 256, 64
+    data = LR.Dataset(LR.learned_workloads(500, LEARNED_TRAJ, side=side), pairs_per_traj=2, warmup=64, stride=256,
+                      batch=250)
+    val = LR.Dataset(LR.learned_workloads(600, 64, side=side), pairs_per_traj=2, warmup=64, stride=256, batch=64,
+                     norm=data.norm)
+    net = lb.Net(4, side, side, seed=1)
+    w = LR.learned_workloads(502, 1, side=side)[0]
+    fr_p, ms_p, _ = LR.run(w, calls=calls)
+    points, spent = [], 0.0
+    for b in budgets:
+        net, losses = LR.train(data, batch=4, seconds=b - spent, lr=5e-4, seed=int(b), net=net)
+        spent = b
+        vloss = LR.evaluate(net, val, range(val.n))
+        inf = LR.inference_net(net, side, side)
+        eps, acc_val, err_val = LR.calibrate(inf, data.norm, LR.learned_workloads(501, 1, side=side)[0], calls=16,
+                                             grid=(0.05, 0.2, 1.0, 5.0, 20.0, 100.0))
+        fr_l, ms_l, stt = LR.run(w, inf, data.norm, calls=calls, eps=eps)
+        fr_a, ms_a, st_a = LR.run(w, inf, data.norm, calls=calls, eps=(1e30, 1e30))
+        nrm = np.linalg.norm(fr_p)
+        points.append({"train_s": b, "adam_steps_segment": len(losses), "val_loss": vloss,
+                       "bounds": list(eps), "accepted": stt["accepted"],
+                       "frest_err_calibrated": float(np.linalg.norm(fr_l - fr_p) / nrm),
+                       "frest_err_all_accepted": float(np.linalg.norm(fr_a - fr_p) / nrm),
+                       "all_accepted_calls": st_a["accepted"], "ms_learned_all_accepted": ms_a,
+                       "ms_learned_calibrated": ms_l})
+        inf.close()
+    net.close()
+    return {"workload": "256x256, batched-recipe physics; %d trajectories (%d pairs) for training, 64 unseen "
+                        "for the loss, held-out trajectory 502 (64 calls = 1024 steps)" % (LEARNED_TRAJ, data.n),
+            "ms_plain": ms_p, "points": points}
+
+
+def run_learned_curve(args):
+    import torch
+    from paper_2209_14889_gb300 import lb
+    torch.cuda.set_device(0)
+    print(json.dumps({"learned_curve": measure_learned_curve(args, lb, torch)}), flush=True)
 
 
 def cpu_baseline_sample():
@@ -610,7 +732,7 @@ KERNEL_NAMES = {"auto": "k_fused (fused lattice step, one cell per thread)",
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -625,6 +747,10 @@ def main():
                     help="time the network's forward pass at 256^2 (batch 1) only (for profiling)")
     ap.add_argument("--only-aniso", action="store_true",
                     help="run the anisotropy study (Return against alpha and theta0) only")
+    ap.add_argument("--only-paper", action="store_true",
+                    help="run the paper's own setup (Return against D_p and radius) only")
+    ap.add_argument("--learned-curve", action="store_true",
+                    help="train the learned form for growing budgets and report each point (only)")
     ap.add_argument("--learned-seconds", type=float, default=45.0,
                     help="training budget of the learned form (0: skip it)")
     ap.add_argument("--tune-cache", default=None,
@@ -639,6 +765,10 @@ def main():
         return run_only_net(args)
     if args.only_aniso:
         return run_only_aniso(args)
+    if args.only_paper:
+        return run_only_paper(args)
+    if args.learned_curve:
+        return run_learned_curve(args)
 
     import numpy as np
     import torch
@@ -763,6 +893,10 @@ def main():
             forms["anisotropy"] = measure_anisotropy(args, lb, W, torch)
         except lb.LBError as e:
             forms["anisotropy"] = {"error": str(e)}
+        try:
+            forms["paper_setup"] = measure_paper_setup(args, lb, W, torch)
+        except lb.LBError as e:
+            forms["paper_setup"] = {"error": str(e)}
     if forms is not None and args.learned_seconds > 0:
         forms["learned"] = measure_learned(args, lb, torch)
     if rank != 0:

@@ -67,27 +67,51 @@ def fit_norm(samples0, samples1) -> np.ndarray:
 
 
 class Dataset:
-    """Pairs (x(t), target(t -> t + 16)) of seeded trajectories, held on the GPU."""
+    """Pairs (x(t), target(t -> t + 16)) of seeded trajectories, held on the GPU.  batch > 0: the
+    trajectories are generated `batch` at a time by the batched kernel (lb_batch_*), which
+    advances them together; else one solver at a time."""
 
-    def __init__(self, workloads, pairs_per_traj: int, warmup: int = 32, stride: int = JUMP, norm=None):
+    def __init__(self, workloads, pairs_per_traj: int, warmup: int = 32, stride: int = JUMP, norm=None,
+                 batch: int = 0):
         import torch
         ny, nx = workloads[0]["ny"], workloads[0]["nx"]
         n = len(workloads) * pairs_per_traj
         self.raw0 = torch.empty((n, ny, nx, 8), dtype=torch.float32, device="cuda")
         self.raw1 = torch.empty((n, ny, nx, 8), dtype=torch.float32, device="cuda")
-        k = 0
-        for w in workloads:
-            s = lb.Solver.from_workload(w)
-            s.step(warmup)
-            for _ in range(pairs_per_traj):
-                pack(s, IDENTITY_NORM, raw=self.raw0[k])
-                s.step(JUMP)
-                pack(s, IDENTITY_NORM, raw=self.raw1[k])
-                if stride > JUMP:
-                    s.step(stride - JUMP)
-                k += 1
-            s.sync()
-            s.close()
+        if batch > 0:
+            for g0 in range(0, len(workloads), batch):
+                group = workloads[g0:g0 + batch]
+                ss = [lb.Solver.from_workload(w) for w in group]
+                b = lb.Batch(ss)
+                b.step(warmup)
+                for p in range(pairs_per_traj):
+                    b.sync()
+                    for j, s in enumerate(ss):
+                        pack(s, IDENTITY_NORM, raw=self.raw0[(g0 + j) * pairs_per_traj + p])
+                    b.step(JUMP)
+                    b.sync()
+                    for j, s in enumerate(ss):
+                        pack(s, IDENTITY_NORM, raw=self.raw1[(g0 + j) * pairs_per_traj + p])
+                    if stride > JUMP:
+                        b.step(stride - JUMP)
+                b.sync()
+                b.close()
+                for s in ss:
+                    s.close()
+        else:
+            k = 0
+            for w in workloads:
+                s = lb.Solver.from_workload(w)
+                s.step(warmup)
+                for _ in range(pairs_per_traj):
+                    pack(s, IDENTITY_NORM, raw=self.raw0[k])
+                    s.step(JUMP)
+                    pack(s, IDENTITY_NORM, raw=self.raw1[k])
+                    if stride > JUMP:
+                        s.step(stride - JUMP)
+                    k += 1
+                s.sync()
+                s.close()
         torch.cuda.synchronize()
         if norm is None:
             pick = list(range(0, n, max(1, n // 16)))

@@ -126,14 +126,16 @@ def test_accept_path_writes_the_network_state():
 
 
 def test_trained_network_gain_against_plain_solver():
-    """Train briefly on seeded trajectories of the batched recipe's physics (64^2 here to keep
-    the test short), then run 32 learned calls (512 steps) on a held-out seed and report what
-    the network gains: accepted calls, restoring-force error against the plain FP32 run on the
-    same GPU, and the time per lattice step of both.  The gain may be a loss (every rejected
-    call costs a network pass on top of 16 plain steps); the error bound holds either way."""
+    """Train briefly on seeded trajectories of the batched recipe's physics (64^2, generated by the
+    batched kernel, to keep the test short), then run 32 learned calls (512 steps) on a held-out
+    seed against the plain FP32 run on the same GPU.  Asserted: the restoring force stays within
+    1 % of the plain run (the bound the residual check is calibrated for), and the time is
+    accounted for: with calls accepted the stepper must not be slower than the network passes
+    it replaces plain steps with; with none accepted (every call falls back to the plain steps)
+    it is slower than the plain run by at least the network passes it made, a measured loss."""
     torch, lb, LR = _gpu()
     side = 64
-    data = LR.Dataset(LR.learned_workloads(11, 4, side=side), pairs_per_traj=24)
+    data = LR.Dataset(LR.learned_workloads(11, 32, side=side), pairs_per_traj=3, batch=32)
     net = lb.Net(8, side, side, seed=1)
     held = list(range(0, data.n, 12))                 # a fixed subset of the pairs
     val0 = LR.evaluate(net, data, held)
@@ -144,15 +146,33 @@ def test_trained_network_gain_against_plain_solver():
           % (len(losses), np.mean(losses[:k]), np.mean(losses[-k:]), val0, val1))
     assert val1 < val0
     inf = LR.inference_net(net, side, side)
+    # the time of one network pass at this size (the cost an accepted call pays instead of 16 steps)
+    x = torch.zeros((1, side, side, 16), dtype=torch.bfloat16, device="cuda")
+    for _ in range(3):
+        inf.forward(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        inf.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_net = e0.elapsed_time(e1) / 10
     # residual bounds fixed on a validation trajectory, then one held-out trajectory
     eps, acc_val, err_val = LR.calibrate(inf, data.norm, LR.learned_workloads(98, 1, side=side)[0], calls=32)
     w = LR.learned_workloads(99, 1, side=side)[0]
     fr_p, ms_p, _ = LR.run(w, calls=32)
     fr_l, ms_l, stt = LR.run(w, inf, data.norm, calls=32, eps=eps)
     err = float(np.linalg.norm(fr_l - fr_p) / np.linalg.norm(fr_p))
+    acc = stt["accepted"]
     print("learned stepper: bounds %s (validation: %d accepted, error %.2e); held-out: accepted %d/32, "
-          "restoring-force error vs plain %.3e, plain %.2f ms, learned %.2f ms (speed ratio %.3f)"
-          % (eps, acc_val, err_val, stt["accepted"], err, ms_p, ms_l, ms_p / ms_l))
+          "restoring-force error vs plain %.3e, plain %.2f ms, learned %.2f ms (speed ratio %.3f), "
+          "network pass %.3f ms" % (eps, acc_val, err_val, acc, err, ms_p, ms_l, ms_p / ms_l, ms_net))
     assert stt["calls"] == 32
-    # the bound the bounds were fixed for holds on the held-out trajectory within a factor 2
-    assert err <= 2e-2
+    assert err <= 1e-2
+    if acc == 0:
+        # every call ran its network pass and then the 16 plain steps: a loss of at least the passes
+        assert ms_l >= ms_p + 0.5 * 32 * ms_net, (ms_l, ms_p, ms_net)
+    else:
+        # accepted calls replaced 16 plain steps each by a network pass and a check step
+        per_step = ms_p / (32 * 16)
+        assert ms_l <= ms_p + 32 * ms_net - acc * 14 * per_step + 0.5 * ms_p, (ms_l, ms_p, ms_net, acc)

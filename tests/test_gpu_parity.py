@@ -69,7 +69,7 @@ def check_nodes(got, ref, w, tol=1e-5):
     assert np.abs(d).max() < tol, np.abs(d).max()
 
 
-def check_series(got, ref, n_rings, tol=FREST_TOL):
+def check_series(got, ref, n_rings, tol=FREST_TOL, cells=4096):
     gs, rs = got["series"], ref["series"]
     assert gs.shape == rs.shape, (gs.shape, rs.shape)
     assert np.array_equal(gs[:, 0], rs[:, 0])
@@ -79,8 +79,9 @@ def check_series(got, ref, n_rings, tol=FREST_TOL):
         if np.linalg.norm(fr_r) > 0:
             assert rel_l2(fr_g, fr_r) <= tol, rel_l2(fr_g, fr_r)
     # total force: the per-cell forces (up to ~0.1 where the initial P noise is relaxing) are
-    # summed from FP32 values, so the telescoping f^p and f^E leave rounding of O(1e-7)
-    assert np.abs(gs[:, 4:6] - rs[:, 4:6]).max() <= 1e-6
+    # summed from FP32 values, so the telescoping f^p and f^E leave rounding of O(1e-7) on a 64^2
+    # lattice, growing as a random walk with the square root of the cell count
+    assert np.abs(gs[:, 4:6] - rs[:, 4:6]).max() <= 1e-6 * max(1.0, math.sqrt(cells / 4096.0))
 
 
 def test_cfg1_one_step():
@@ -588,6 +589,66 @@ def test_trap_protocol_vs_oracle(walls):
     assert abs(r_gpu - r_orc) < 1e-4, (r_gpu, r_orc)
     # the ring moved with the trap: most of the way, less than all of it
     assert 0.0 < r_orc < 1.0
+
+
+def _gpu_run(w, steps, **kw):
+    lb = _gpu()
+    s = lb.Solver.from_workload(w, **kw)
+    s.step(steps)
+    s.sync()
+    got = dict(fields=s.fields(), series=s.series(), X=s.nodes())
+    s.close()
+    return got
+
+
+@pytest.mark.parametrize("model", ["scalar", "tensorial"])
+def test_paper_setup_vs_oracle(model):
+    # the paper's own pulling experiment (App. C, Tables I-IV in lattice units): the 250^2 closed
+    # box, tau = 1.25, the 157-node droplet held by the trap while it ramps up and starts to drag,
+    # the scalar modulus or the K^x of Table IV with the Beris-Edwards field; 300 steps against the
+    # OpenMP build of the oracle
+    from _oracle_child import run_openmp
+    w = W.paper_setup(model, every=10)
+    ref = run_openmp("paper_setup", dict(model=model, every=10), 300, 10)
+    got = _gpu_run(w, 300)
+    if model == "scalar":
+        # the scalar model has no P field (the oracle's P evolves without acting on the rest)
+        for d in (got, ref):
+            d["fields"] = {k: v for k, v in d["fields"].items() if k in SCALAR_FIELDS}
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1)
+
+
+def test_cfg2_full_size_150_steps_vs_oracle():
+    # the 1024^2 workload (one ring of 256 nodes, radius 24, pulled at 30 degrees) over 150 steps,
+    # long enough for the stress around the ring and the flow to build up, in the launch
+    # configuration the bench times; every field <= 1e-5, the restoring force <= 1e-4 over the
+    # 15 readouts, nodes <= 1e-5 cells
+    from _oracle_child import run_openmp
+    w = W.cfg2()
+    ref = run_openmp("cfg2", {}, 150, 10)
+    got = _gpu_run(w, 150)
+    check_fields(got, ref)
+    check_nodes(got, ref, w)
+    check_series(got, ref, 1, cells=1024 * 1024)
+    assert np.abs(ref["series"][-1, 6:8]).max() > 2 * np.abs(ref["series"][1, 6:8]).max()
+
+
+def test_precision_form_4096_restoring_force_within_1pct_of_fp32():
+    # the 4096^2 precision workload (16 rings of 128 nodes at seeded positions and pull angles)
+    # in FP16/BF16 storage against the FP32 state on the same GPU, 1000 steps: the restoring
+    # force of every ring over its 100 readouts within 1 % (relative L2), the fields within 3 %
+    w = W.cfg3()
+    a = _gpu_run(w, 1000)
+    lb = _gpu()
+    b = _gpu_run(w, 1000, precision=lb.LB_FP16_BF16)
+    fa, fb = a["series"][:, 6:], b["series"][:, 6:]
+    cols = [c for r in range(16) for c in (4 * r, 4 * r + 1)]
+    e = rel_l2(fb[:, cols], fa[:, cols])
+    assert e <= 1e-2, e
+    for k in ("ux", "uy", "sxx", "syy", "sxy"):
+        assert rel_l2(b["fields"][k], a["fields"][k]) <= 3e-2, k
 
 
 def test_trap_node_tail_matches_separate_node_kernel_bitwise():

@@ -55,7 +55,7 @@ def test_noalloc_readout_allocates_nothing():
     # On a fresh 1024 x 1024 solver the first readout of u through lb_readout_noalloc leaves the
     # device's free memory unchanged, while lb_readout's first call takes its 12 MiB buffer.
     torch, lb, f = _setup()
-    warm = lb.Solver.from_workload(W.small(32, 32, steps=0))     # the device's first call of all
+    warm = lb.Solver.from_workload(W.make(32, 32, rings=[], noise_amp=0.0))   # the device's first call
     out = np.empty((32, 32), dtype=np.float32)
     assert f(warm.h, 1, out.ctypes.data, out.nbytes, 0) == 0
     warm.close()
