@@ -671,6 +671,48 @@ def measure_learned_curve(args, lb, torch, budgets=(45.0, 180.0, 540.0)):
             "ms_plain": ms_p, "points": points}
 
 
+PROFILE_CASES = ("tile_fp32", "tile_lp", "tile_scalar", "strip_fp32", "strip_lp", "strip_scalar", "sweep_fp32",
+                 "diffuse_fp32", "batch")
+
+
+def run_case(args):
+    """One lattice kernel on its profiling workload for --steps lattice steps (the commands under
+    profiles/ capture these): tile_* and sweep_fp32 on cfg3 at 2048^2 with 4 rings, strip_* on
+    cfg3 at 4096^2 with 16 rings (FP32, FP16/BF16 storage, scalar model), diffuse_fp32 on the
+    2048^2 lattice with D_p = 0.6 in 3 sub-steps, batch: 64 lattices of 256^2 (cfg4 recipe,
+    D_p = 0.05, no sub-steps) in one batch with the 32 x 16 tile shape."""
+    import torch
+    from paper_2209_14889_gb300 import lb, workloads as W
+    torch.cuda.set_device(0)
+    case = args.case
+    if case == "batch":
+        ws = W.cfg4(n_instances=64, sides=(256,))
+        for w in ws:
+            w["Dp"], w["diffusion_substeps"] = 0.05, 0
+        ss = [lb.Solver.from_workload(w) for w in ws]
+        b = lb.Batch(ss)
+        b.set_shape(0)
+        b.step(args.steps)
+        b.sync()
+        print(json.dumps({"case": case, "cells": sum(w["nx"] * w["ny"] for w in ws), "steps": args.steps}))
+        b.close()
+        return
+    side = 4096 if case.startswith("strip") else 2048
+    w = W.cfg3(side=side, n_rings=max(1, 16 * side * side // (4096 * 4096)))
+    if case.endswith("_scalar"):
+        w = dict(w, **W.scalar_physics())
+    if case.startswith("diffuse"):
+        w = dict(w, Dp=0.6, diffusion_substeps=3)
+    prec = lb.LB_FP16_BF16 if case.endswith("_lp") else lb.LB_FP32
+    s = lb.Solver.from_workload(w, precision=prec)
+    s.set_kernel({"tile": lb.LB_KERNEL_TILE, "strip": lb.LB_KERNEL_STRIP, "sweep": lb.LB_KERNEL_SWEEP,
+                  "diffuse": lb.LB_KERNEL_TILE}[case.split("_")[0]])
+    s.step(args.steps)
+    s.sync()
+    print(json.dumps({"case": case, "kernel": s.lattice_kernel, "cells": w["nx"] * w["ny"], "steps": args.steps}))
+    s.close()
+
+
 def run_learned_curve(args):
     import torch
     from paper_2209_14889_gb300 import lb
@@ -749,6 +791,8 @@ def main():
                     help="run the anisotropy study (Return against alpha and theta0) only")
     ap.add_argument("--only-paper", action="store_true",
                     help="run the paper's own setup (Return against D_p and radius) only")
+    ap.add_argument("--case", default=None, choices=PROFILE_CASES,
+                    help="run one lattice kernel's profiling workload for --steps steps (only)")
     ap.add_argument("--learned-curve", action="store_true",
                     help="train the learned form for growing budgets and report each point (only)")
     ap.add_argument("--learned-seconds", type=float, default=45.0,
@@ -769,6 +813,8 @@ def main():
         return run_only_paper(args)
     if args.learned_curve:
         return run_learned_curve(args)
+    if args.case:
+        return run_case(args)
 
     import numpy as np
     import torch

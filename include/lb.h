@@ -295,9 +295,11 @@ void lb_destroy(lb_handle* h);
 /*
  * Batched form.  Many independent lattices (each with its own size, parameters, rings and
  * diffusion sub-steps; Sec. II with the parameters of Tables I-IV varied per instance) advanced
- * together: one persistent cooperative kernel runs all instances' lattice tiles, then their
- * diffusion sub-steps, then their node blocks, with a grid barrier between phases, for a chunk
- * of readout_every steps per launch; the chunk is captured once as a CUDA graph and replayed.
+ * together, a chunk of readout_every steps at a time, the chunk captured once as a CUDA graph and
+ * replayed.  By default every step is three launches per tile-shape group: all instances'
+ * lattice tiles, then their diffusion sub-steps, then their node blocks.  With
+ * lb_batch_set_persistent(b, 1) one persistent cooperative kernel per group runs the whole chunk
+ * instead, with a grid barrier between the phases.
  * Each instance computes exactly what lb_step computes for its handle (fields and nodes bitwise
  * equal; the readout sums of the lattice may differ in the last bits with the tile shape).
  *
@@ -315,10 +317,15 @@ void lb_destroy(lb_handle* h);
  * lb_batch_autotune: time `steps` steps with each shape per distinct lattice size and keep the
  *   fastest; the states are saved and restored, so the simulation does not advance.  cache_path
  *   (or NULL) is a flat JSON object "<gpu name>|<nx>x<ny>": shape, read first and rewritten.
- * lb_batch_set_wait_limit: limit of one barrier wait in ms (default 2000) and an arrival-count
- *   offset that is 0 in normal use; a positive offset makes every barrier wait run out, which
- *   exercises the LB_ETIMEOUT path.
- * lb_batch_grid: CTAs of the persistent launch; lb_batch_uses_graph: 1 if chunks are replayed
+ * lb_batch_set_persistent: 1 = the persistent cooperative kernel, 0 = phase launches (default;
+ *   measured faster on GB300: the tile phase keeps the tile kernel's three CTAs per SM and no
+ *   CTA waits at a grid barrier).  Both compute the same values bit for bit.  LB_EINVAL for
+ *   other values.
+ * lb_batch_set_wait_limit: limit of one barrier wait of the persistent kernel in ms (default
+ *   2000) and an arrival-count offset that is 0 in normal use; a positive offset makes every
+ *   barrier wait run out, which exercises the LB_ETIMEOUT path.
+ * lb_batch_grid: CTAs of the persistent launch of the first group, or the lattice-tile CTAs of
+ *   one step over all groups with phase launches; lb_batch_uses_graph: 1 if chunks are replayed
  *   from a captured graph.
  */
 typedef struct lb_batch lb_batch;
@@ -328,6 +335,7 @@ int lb_batch_sync(lb_batch* b);
 int lb_batch_set_shape(lb_batch* b, int32_t inst, int32_t shape);
 int32_t lb_batch_shape(const lb_batch* b, int32_t inst);
 int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps);
+int lb_batch_set_persistent(lb_batch* b, int32_t enable);
 int lb_batch_set_wait_limit(lb_batch* b, double wait_ms, int32_t extra_arrivals);
 int32_t lb_batch_grid(const lb_batch* b);
 int32_t lb_batch_uses_graph(const lb_batch* b);

@@ -1,7 +1,12 @@
-// lb_batch.cu -- batched sweeps: many independent lattices of uneven sizes advanced by one
-// persistent cooperative launch per chunk of steps, replayed from a captured CUDA graph.
+// lb_batch.cu -- batched sweeps: many independent lattices of uneven sizes advanced together,
+// a chunk of steps per captured CUDA graph.
 //
-// Each step of the persistent kernel has three phases separated by a grid barrier:
+// Default (phase launches): each step is one launch per phase and tile-shape group -- all
+// instances' lattice tiles (k_batch_tiles, the tile kernel's occupancy of three CTAs per SM),
+// their diffusion sub-steps, then their node blocks -- in stream order, so no kernel waits on
+// another inside a launch.  Alternatively (lb_batch_set_persistent) one persistent cooperative
+// kernel per group runs the whole chunk, each step having three phases separated by a grid
+// barrier:
 //   lattice  the fused step of every tile of every instance (tile shape per instance, chosen by
 //            the autotuner among 32x16, 32x8, 64x8, 16x16), the tile code of lb_tile.cuh;
 //   sigma    diffusion sub-steps of the instances whose D_p exceeds the Heun bound;
@@ -179,6 +184,70 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchArgs B, int nsteps)
     if (blockIdx.x == 0 && threadIdx.x == 0) *B.cur = (cur0 + nsteps) & 1;
 }
 
+// ---- phase launches: one CTA per work item, the buffer parity of step s of the chunk read from
+// the device word (so that a replayed graph continues from wherever the last chunk ended) ----
+
+template <int TX, int TY, bool SCALAR>
+__global__ void __launch_bounds__(BT, 3) k_batch_tiles(const BatchArgs B, int s)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int par = (*B.cur + s) & 1;
+    const int item = blockIdx.x;
+    const int i = find_inst(B.tile_begin, B.n_inst, item);
+    const BatchInst& I = B.inst[i];
+    const int local = item - __ldg(B.tile_begin + i);
+    const int by = local / I.tiles_x, bx = local - by * I.tiles_x;
+    // the state was written by an earlier launch: the read-only path is safe
+    tile::tile_step<MODE_STEP, cell::PREC_FP32, TX, TY, false, SCALAR>(I.fa[par], bx, by, local, sm);
+}
+
+// sub-step k of the diffusion of the instances with dsub > k (or, with dsub odd and k == dsub,
+// the copy of the result back into the new state's sigma planes)
+__global__ void __launch_bounds__(BT) k_batch_diffuse(const BatchArgs B, int s, int k)
+{
+    extern __shared__ __align__(16) float sm[];
+    const int par = (*B.cur + s) & 1;
+    const int item = blockIdx.x;
+    const int i = find_inst(B.dif_begin, B.n_inst, item);
+    const BatchInst& I = B.inst[i];
+    const int local = item - __ldg(B.dif_begin + i);
+    const int by = local / I.dif_tx, bx = local - by * I.dif_tx;
+    float* sn = I.sig[par ^ 1];
+    float* so = I.sig[par];
+    const long long NP = I.fa[0].plane;
+    if (k < I.dsub) {
+        const bool even = (k & 1) == 0;
+        dif::diffuse_tile(even ? sn : so, even ? so : sn, NP, I.fa[0].nx, I.fa[0].ny, I.dsub_D, bx, by, sm);
+    } else if (k == I.dsub && (I.dsub & 1)) {
+        for (int q = threadIdx.x; q < dif::DX * dif::DY; q += blockDim.x) {
+            const int ly = q / dif::DX, lx = q - ly * dif::DX;
+            const int gx = bx * dif::DX + lx, gy = by * dif::DY + ly;
+            if (gx < I.fa[0].nx && gy < I.fa[0].ny) {
+                const long long g = (long long)gy * I.fa[0].nx + gx;
+                for (int c = 0; c < 3; ++c) sn[c * NP + g] = so[c * NP + g];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NODE_THREADS) k_batch_nodes(const BatchArgs B, int s)
+{
+    __shared__ node::NodeSmem S;
+    const int par = (*B.cur + s) & 1;
+    const int item = blockIdx.x;
+    const int i = find_inst(B.node_begin, B.n_inst, item);
+    NodeArgs na = B.inst[i].na;
+    na.X = B.inst[i].xb[par];
+    na.X_out = B.inst[i].xb[par ^ 1];
+    node::node_block(na, item - __ldg(B.node_begin + i), S);
+}
+
+// the buffer parity after a chunk of n steps
+__global__ void k_batch_parity(int* cur, int n)
+{
+    if (threadIdx.x == 0) *cur = (*cur + n) & 1;
+}
+
 }  // namespace
 }  // namespace vlb
 
@@ -199,6 +268,10 @@ struct lb_batch {
     int n_group[N_SHAPES] = {};
     int max_dsub[N_SHAPES] = {};
     int grid[N_SHAPES] = {};                // CTAs of each shape's persistent launch
+    int n_tiles[N_SHAPES] = {};             // work items of each group (phase launches)
+    int n_nodes[N_SHAPES] = {};
+    int n_dif[N_SHAPES] = {};
+    bool persistent = false;                // one persistent kernel per chunk (else phase launches)
     int* d_cur = nullptr;                   // buffer parity, one word per group
     unsigned* d_bar = nullptr;              // barrier words, two per group
     int* d_err = nullptr;
@@ -274,6 +347,9 @@ int build_plan(lb_batch* b)
             inst.push_back(I);
         }
         b->n_group[sh] = (int)inst.size();
+        b->n_tiles[sh] = tb.back();
+        b->n_nodes[sh] = nb.back();
+        b->n_dif[sh] = db.back();
         if (inst.empty()) continue;
         const int g = (int)inst.size();
         BCK(b, cudaMemcpy(b->d_inst[sh], inst.data(), sizeof(BatchInst) * g, cudaMemcpyHostToDevice));
@@ -320,9 +396,63 @@ cudaError_t launch_shape(const lb_batch* b, int sh, int nsteps)
                      : cudaLaunchKernelEx(&cfg, k_batch<TX, TY, false>, a, nsteps);
 }
 
-// one persistent launch per non-empty shape group, one after another on the batch stream
+template <int TX, int TY>
+cudaError_t launch_tiles(const lb_batch* b, int sh, int s)
+{
+    static unsigned long long attr_done = 0;     // per device
+    auto kern = b->scalar ? k_batch_tiles<TX, TY, true> : k_batch_tiles<TX, TY, false>;
+    const size_t smem = tile::TileGeo<TX, TY>::SMEM_BYTES;
+    if (!done_on_device(attr_done)) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_tiles<TX, TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_tiles<TX, TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            attr_done = 0;
+            return e;
+        }
+    }
+    kern<<<b->n_tiles[sh], BT, smem, b->stream>>>(batch_args(b, sh), s);
+    return cudaGetLastError();
+}
+
+// Phase launches of `nsteps` steps: per step the lattice tiles of every group, then the
+// diffusion sub-steps, then the node blocks; at the end the device parity words advance.
+cudaError_t launch_phases(const lb_batch* b, int nsteps)
+{
+    cudaError_t e = cudaSuccess;
+    const size_t dsm = sizeof(float) * dif::SMEM;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+        if (b->n_group[0] && e == cudaSuccess) e = launch_tiles<32, 16>(b, 0, s);
+        if (b->n_group[1] && e == cudaSuccess) e = launch_tiles<32, 8>(b, 1, s);
+        if (b->n_group[2] && e == cudaSuccess) e = launch_tiles<64, 8>(b, 2, s);
+        if (b->n_group[3] && e == cudaSuccess) e = launch_tiles<16, 16>(b, 3, s);
+        for (int sh = 0; sh < N_SHAPES && e == cudaSuccess; ++sh) {
+            if (!b->n_group[sh] || !b->n_dif[sh]) continue;
+            for (int k = 0; k <= b->max_dsub[sh] && e == cudaSuccess; ++k) {
+                k_batch_diffuse<<<b->n_dif[sh], BT, dsm, b->stream>>>(batch_args(b, sh), s, k);
+                e = cudaGetLastError();
+            }
+        }
+        for (int sh = 0; sh < N_SHAPES && e == cudaSuccess; ++sh) {
+            if (!b->n_group[sh] || !b->n_nodes[sh]) continue;
+            k_batch_nodes<<<b->n_nodes[sh], NODE_THREADS, 0, b->stream>>>(batch_args(b, sh), s);
+            e = cudaGetLastError();
+        }
+    }
+    for (int sh = 0; sh < N_SHAPES && e == cudaSuccess; ++sh) {
+        if (!b->n_group[sh]) continue;
+        k_batch_parity<<<1, 32, 0, b->stream>>>(b->d_cur + sh, nsteps);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// one persistent launch per non-empty shape group, one after another on the batch stream (or
+// the phase launches)
 cudaError_t launch_batch(const lb_batch* b, int nsteps)
 {
+    if (!b->persistent) return launch_phases(b, nsteps);
     cudaError_t e = cudaSuccess;
     if (b->n_group[0] && e == cudaSuccess) e = launch_shape<32, 16>(b, 0, nsteps);
     if (b->n_group[1] && e == cudaSuccess) e = launch_shape<32, 8>(b, 1, nsteps);
@@ -502,7 +632,24 @@ int lb_batch_sync(lb_batch* b)
     return LB_OK;
 }
 
-int32_t lb_batch_grid(const lb_batch* b) { return b ? b->grid[0] : 0; }
+int32_t lb_batch_grid(const lb_batch* b)
+{
+    if (!b) return 0;
+    if (b->persistent) return b->grid[0];
+    int n = 0;
+    for (int sh = 0; sh < N_SHAPES; ++sh) n += b->n_group[sh] ? b->n_tiles[sh] : 0;
+    return n;
+}
+
+int lb_batch_set_persistent(lb_batch* b, int32_t enable)
+{
+    if (!b) return LB_EINVAL;
+    if (enable != 0 && enable != 1) return bfail(b, LB_EINVAL, "enable must be 0 or 1");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->persistent = enable != 0;
+    drop_graph(b);
+    return LB_OK;
+}
 
 int32_t lb_batch_uses_graph(const lb_batch* b) { return b && b->graph ? 1 : 0; }
 

@@ -109,6 +109,7 @@ def lib():
             "lb_batch_set_shape": (ctypes.c_int, [_B, i32, i32]),
             "lb_batch_shape": (i32, [_B, i32]),
             "lb_batch_autotune": (ctypes.c_int, [_B, ctypes.c_char_p, i32]),
+            "lb_batch_set_persistent": (ctypes.c_int, [_B, i32]),
             "lb_batch_set_wait_limit": (ctypes.c_int, [_B, ctypes.c_double, i32]),
             "lb_batch_grid": (i32, [_B]),
             "lb_batch_uses_graph": (i32, [_B]),
@@ -402,6 +403,10 @@ class Batch:
     def autotune(self, cache_path=None, steps: int = 5):
         self._check(lib().lb_batch_autotune(self.b, None if cache_path is None else
                                             os.fsencode(cache_path), int(steps)))
+
+    def set_persistent(self, enable: bool):
+        """One persistent cooperative kernel per chunk (True) or phase launches (False, default)."""
+        self._check(lib().lb_batch_set_persistent(self.b, 1 if enable else 0))
 
     def set_wait_limit(self, wait_ms: float, extra_arrivals: int = 0):
         self._check(lib().lb_batch_set_wait_limit(self.b, float(wait_ms), int(extra_arrivals)))

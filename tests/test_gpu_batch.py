@@ -79,14 +79,16 @@ def _assert_bitwise(got, ref, series_exact_cols=True):
     np.testing.assert_allclose(gs[:, 1:6], rs[:, 1:6], rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("persistent", [False, True], ids=["phase_launches", "persistent"])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3])
-def test_batch_matches_single_handles_bitwise(shape):
+def test_batch_matches_single_handles_bitwise(shape, persistent):
     lb = _gpu()
     ws = _mixed()
     steps = 37                                  # 3 graph chunks of 10 + 7 direct steps
     ref = _reference(lb, ws, steps)
     ss = _solvers(lb, ws)
     b = lb.Batch(ss)
+    b.set_persistent(persistent)
     b.set_shape(shape)
     assert all(b.shape(i) == shape for i in range(len(ws)))
     b.step(steps)
@@ -110,7 +112,10 @@ def test_batch_mixed_shapes_graph_and_resume():
     b.step(20)
     b.sync()
     assert b.uses_graph
-    assert b.grid >= 152
+    # phase launches: one CTA per lattice tile of every instance (tile shape i % 4)
+    dims = {0: (32, 16), 1: (32, 8), 2: (64, 8), 3: (16, 16)}
+    tiles = sum(-(-w["nx"] // dims[i % 4][0]) * -(-w["ny"] // dims[i % 4][1]) for i, w in enumerate(ws))
+    assert b.grid == tiles
     b.step(25)                                  # continues from the device-side parity
     b.sync()
     for s, r in zip(ss, ref):
@@ -217,6 +222,7 @@ def test_barrier_wait_runs_out_with_timeout_status():
     ws = _mixed(seed=41)[:2]
     ss = _solvers(lb, ws)
     b = lb.Batch(ss)
+    b.set_persistent(True)                      # the grid barrier is the persistent kernel's
     b.set_wait_limit(200.0, extra_arrivals=1)
     b.step(1)
     with pytest.raises(lb.LBError) as e:
