@@ -484,7 +484,8 @@ def measure_batched(args, lb, W, torch):
     tune_s = time.perf_counter() - t0
     shapes = {}
     for i, w in enumerate(ws):
-        shapes["%dx%d" % (w["nx"], w["ny"])] = "%dx%d" % lb.TILE_SHAPES[b.shape(i)]
+        sh = lb.TILE_SHAPES[b.shape(i)]
+        shapes["%dx%d" % (w["nx"], w["ny"])] = sh if isinstance(sh, str) else "%dx%d" % sh
     chunk = 10
     steps = max(3, min(args.steps, 10))
     b.step(2 * chunk)

@@ -313,9 +313,11 @@ void lb_destroy(lb_handle* h);
  *   order).  lb_batch_sync: wait, then report LB_ETIMEOUT if a grid barrier gave up (the
  *   states are then undefined) or the first instance error of lb_sync.
  * lb_batch_set_shape: tile shape of instance inst (-1: all): 0 = 32x16, 1 = 32x8, 2 = 64x8,
- *   3 = 16x16 cells.  lb_batch_shape returns it (-1 for a bad index).
- * lb_batch_autotune: time `steps` steps with each shape per distinct lattice size and keep the
- *   fastest; the states are saved and restored, so the simulation does not advance.  cache_path
+ *   3 = 16x16 cells, 4 = the warp-strip kernel (LB_KERNEL_STRIP's step; periodic instances with
+ *   nx >= 64 even and ny >= 32, phase launches only, else LB_EINVAL).  lb_batch_shape returns
+ *   it (-1 for a bad index).
+ * lb_batch_autotune: time `steps` steps with each shape that applies per distinct lattice size
+ *   and keep the fastest; the states are saved and restored, so the simulation does not advance.  cache_path
  *   (or NULL) is a flat JSON object "<gpu name>|<nx>x<ny>": shape, read first and rewritten.
  * lb_batch_set_persistent: 1 = the persistent cooperative kernel, 0 = phase launches (default;
  *   measured faster on GB300: the tile phase keeps the tile kernel's three CTAs per SM and no

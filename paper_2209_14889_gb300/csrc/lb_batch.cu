@@ -26,13 +26,19 @@
 #include "lb_diffuse.cuh"
 #include "lb_handle.h"
 #include "lb_node.cuh"
+#include "lb_strip.cuh"
 #include "lb_tile.cuh"
 
 namespace vlb {
 namespace {
 
 constexpr int BT = 256;     // threads per CTA
-constexpr int N_SHAPES = 4;
+// tile shapes 0..3 (32x16, 32x8, 64x8, 16x16 cells per CTA), and shape 4: the warp-strip kernel
+// (phase launches only; a CTA = SWARPS strips of SOWN columns x STRIP_H rows)
+constexpr int N_SHAPES = 5;
+constexpr int N_TILE_SHAPES = 4;
+constexpr int SHAPE_STRIP = 4;
+constexpr int STRIP_H = 64;
 __host__ __device__ constexpr int shape_tx(int s) { return s == 0 ? 32 : (s == 1 ? 32 : (s == 2 ? 64 : 16)); }
 __host__ __device__ constexpr int shape_ty(int s) { return s == 0 ? 16 : (s == 1 ? 8 : (s == 2 ? 8 : 16)); }
 
@@ -201,6 +207,22 @@ __global__ void __launch_bounds__(BT, 3) k_batch_tiles(const BatchArgs B, int s)
     tile::tile_step<MODE_STEP, cell::PREC_FP32, TX, TY, false, SCALAR>(I.fa[par], bx, by, local, sm);
 }
 
+// the warp-strip step of every instance of the strip group: CTA `local` of an instance covers
+// strip columns (local % tiles_x) * SWARPS .. and rows chunk local / tiles_x; the step index comes
+// from the instance's control block (advanced by its node blocks of the step before)
+template <bool SCALAR>
+__global__ void __launch_bounds__(SNT, 3) k_batch_strips(const BatchArgs B, int s)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int par = (*B.cur + s) & 1;
+    const int item = blockIdx.x;
+    const int i = find_inst(B.tile_begin, B.n_inst, item);
+    const BatchInst& I = B.inst[i];
+    const int local = item - __ldg(B.tile_begin + i);
+    const int cy = local / I.tiles_x, cx = local - cy * I.tiles_x;
+    strip_body<cell::PREC_FP32, SCALAR>(I.fa[par], I.fa[par].ctl->t, STRIP_H, cx, cy, local, smem);
+}
+
 // sub-step k of the diffusion of the instances with dsub > k (or, with dsub odd and k == dsub,
 // the copy of the result back into the new state's sigma planes)
 __global__ void __launch_bounds__(BT) k_batch_diffuse(const BatchArgs B, int s, int k)
@@ -286,6 +308,9 @@ struct lb_batch {
 
 namespace {
 
+// the strip shape applies to this instance (the warp-strip kernel's conditions)
+bool strip_ok(const lb_handle* h) { return strip_eligible(h->p.nx, h->p.ny, h->p.walls_x || h->p.walls_y); }
+
 int bfail(lb_batch* b, int code, const std::string& msg)
 {
     if (b) b->err = msg;
@@ -332,8 +357,13 @@ int build_plan(lb_batch* b)
             I.xb[h->cur] = h->X;
             I.xb[h->cur ^ 1] = h->X_alt;
             I.shape = sh;
-            I.tiles_x = (h->p.nx + shape_tx(sh) - 1) / shape_tx(sh);
-            I.tiles_y = (h->p.ny + shape_ty(sh) - 1) / shape_ty(sh);
+            if (sh == SHAPE_STRIP) {
+                I.tiles_x = ((h->p.nx + SOWN - 1) / SOWN + SWARPS - 1) / SWARPS;
+                I.tiles_y = (h->p.ny + STRIP_H - 1) / STRIP_H;
+            } else {
+                I.tiles_x = (h->p.nx + shape_tx(sh) - 1) / shape_tx(sh);
+                I.tiles_y = (h->p.ny + shape_ty(sh) - 1) / shape_ty(sh);
+            }
             I.na.n_partials = I.tiles_x * I.tiles_y;
             for (int p = 0; p < 2; ++p) I.sig[p] = static_cast<float*>(h->state[p]) + (size_t)PL_SXX * h->plane;
             I.dsub = h->p.diffusion_substeps;
@@ -416,6 +446,24 @@ cudaError_t launch_tiles(const lb_batch* b, int sh, int s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_strips(const lb_batch* b, int s)
+{
+    static unsigned long long attr_done = 0;     // per device
+    if (!done_on_device(attr_done)) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_strips<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)STRIP_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_strips<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STRIP_SMEM);
+        if (e != cudaSuccess) {
+            attr_done = 0;
+            return e;
+        }
+    }
+    auto kern = b->scalar ? k_batch_strips<true> : k_batch_strips<false>;
+    kern<<<b->n_tiles[SHAPE_STRIP], SNT, STRIP_SMEM, b->stream>>>(batch_args(b, SHAPE_STRIP), s);
+    return cudaGetLastError();
+}
+
 // Phase launches of `nsteps` steps: per step the lattice tiles of every group, then the
 // diffusion sub-steps, then the node blocks; at the end the device parity words advance.
 cudaError_t launch_phases(const lb_batch* b, int nsteps)
@@ -427,6 +475,7 @@ cudaError_t launch_phases(const lb_batch* b, int nsteps)
         if (b->n_group[1] && e == cudaSuccess) e = launch_tiles<32, 8>(b, 1, s);
         if (b->n_group[2] && e == cudaSuccess) e = launch_tiles<64, 8>(b, 2, s);
         if (b->n_group[3] && e == cudaSuccess) e = launch_tiles<16, 16>(b, 3, s);
+        if (b->n_group[SHAPE_STRIP] && e == cudaSuccess) e = launch_strips(b, s);
         for (int sh = 0; sh < N_SHAPES && e == cudaSuccess; ++sh) {
             if (!b->n_group[sh] || !b->n_dif[sh]) continue;
             for (int k = 0; k <= b->max_dsub[sh] && e == cudaSuccess; ++k) {
@@ -593,6 +642,13 @@ int lb_batch_set_shape(lb_batch* b, int32_t inst, int32_t shape)
     if (!b) return LB_EINVAL;
     if (inst < -1 || inst >= (int)b->h.size() || shape < 0 || shape >= N_SHAPES)
         return bfail(b, LB_EINVAL, "bad instance or shape");
+    if (shape == SHAPE_STRIP) {
+        if (b->persistent) return bfail(b, LB_EINVAL, "the strip shape runs with phase launches only");
+        for (int i = 0; i < (int)b->h.size(); ++i)
+            if ((inst < 0 || i == inst) && !strip_ok(b->h[i]))
+                return bfail(b, LB_EINVAL, "instance " + std::to_string(i) + " cannot take the strip shape "
+                             "(periodic, nx >= 64 even, ny >= 32)");
+    }
     BCK(b, cudaStreamSynchronize(b->stream));
     if (inst < 0) std::fill(b->shape.begin(), b->shape.end(), shape);
     else b->shape[inst] = shape;
@@ -646,6 +702,9 @@ int lb_batch_set_persistent(lb_batch* b, int32_t enable)
     if (!b) return LB_EINVAL;
     if (enable != 0 && enable != 1) return bfail(b, LB_EINVAL, "enable must be 0 or 1");
     BCK(b, cudaStreamSynchronize(b->stream));
+    if (enable)
+        for (int sh : b->shape)
+            if (sh == SHAPE_STRIP) return bfail(b, LB_EINVAL, "an instance has the strip shape (phase launches only)");
     b->persistent = enable != 0;
     drop_graph(b);
     return LB_OK;
@@ -752,6 +811,7 @@ int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps)
         float best = 3.0e38f;
         int best_s = 0;
         for (int sh = 0; sh < N_SHAPES && rc == LB_OK; ++sh) {
+            if (sh == SHAPE_STRIP && (b->persistent || !strip_ok(b->h[kv.second[0]]))) continue;
             for (int i : kv.second) b->shape[i] = sh;
             if ((rc = build_plan(b)) != LB_OK) break;
             cudaError_t e = launch_batch(b, 1);     // warm-up

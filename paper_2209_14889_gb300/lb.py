@@ -355,7 +355,7 @@ class Solver:
         return lib().lb_launches_per_step(self.h)
 
 
-TILE_SHAPES = {0: (32, 16), 1: (32, 8), 2: (64, 8), 3: (16, 16)}
+TILE_SHAPES = {0: (32, 16), 1: (32, 8), 2: (64, 8), 3: (16, 16), 4: "strip"}
 
 
 class Batch:

@@ -101,6 +101,34 @@ def test_batch_matches_single_handles_bitwise(shape, persistent):
         s.close()
 
 
+def test_batch_strip_shape_matches_single_handles_bitwise():
+    # the warp-strip step as a batch shape (the instances it applies to; the others keep tiles):
+    # fields and nodes bitwise equal to the single handles; the shape is refused where it does
+    # not apply and in the persistent mode
+    lb = _gpu()
+    ws = _mixed(seed=13)
+    steps = 37
+    ref = _reference(lb, ws, steps)
+    ss = _solvers(lb, ws)
+    b = lb.Batch(ss)
+    ok = [w["nx"] >= 64 and w["nx"] % 2 == 0 and w["ny"] >= 32 for w in ws]
+    assert any(ok) and not all(ok)
+    with pytest.raises(lb.LBError):
+        b.set_shape(4)                          # some instances are too small
+    for i, good in enumerate(ok):
+        b.set_shape(4 if good else 0, inst=i)
+    with pytest.raises(lb.LBError):
+        b.set_persistent(True)
+    b.step(steps)
+    b.sync()
+    for s, r in zip(ss, ref):
+        assert s.t == steps
+        _assert_bitwise(_state(s), r)
+    b.close()
+    for s in ss:
+        s.close()
+
+
 def test_batch_mixed_shapes_graph_and_resume():
     lb = _gpu()
     ws = _mixed(seed=21)
