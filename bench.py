@@ -73,15 +73,42 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = ["lb_fused.cu", "lb_tile.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h", "lb_node.cuh"]
+STRIP_SOURCES = ["lb_strip.cu", "lb_strip.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h"]
 
 
-def kernel_source_sha1():
-    """SHA-1 over the sources of the fused lattice kernel (the counters in profiles/ are valid
-    only for the source they were taken on)."""
+def kernel_source_sha1(sources=KERNEL_SOURCES):
+    """SHA-1 over the sources of a lattice kernel (the counters in profiles/ are valid only for
+    the source they were taken on)."""
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_2209_14889_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+def profile_values(name, sources):
+    """key: value lines of a committed ncu summary, or {} when the kernel's sources changed
+    since its counters were taken."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return {}
+    info = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            info[k.strip()] = v.strip()
+    return info if info.get("kernel_source_sha1") == kernel_source_sha1(sources) else {}
+
+
+# Instruction issue of a GB300: 152 SMs x 4 schedulers x one warp instruction per cycle at the SM
+# clock (the nominal unit counts; the clock is the median sampled under load, else the maximum).
+def issue_roofline(warp_inst_per_launch, launch_s, sm_mhz):
+    if not warp_inst_per_launch or not launch_s:
+        return None
+    peak = 152 * 4 * sm_mhz * 1e6
+    achieved = warp_inst_per_launch / launch_s
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "T warp-instr/s",
+            "frac": achieved / peak, "warp_instructions_per_launch": warp_inst_per_launch,
+            "peak_from": "152 SMs x 4 schedulers x 1 warp instruction/cycle x %.0f MHz" % sm_mhz}
 
 
 def ncu_traffic():
@@ -247,8 +274,11 @@ def measure_forms(args, lb, W, torch):
         s.timing(False)
         fused_s = kt["fused_ms"] * 1e-3 / max(kt["fused_launches"], 1)
         gbs = s.bytes_per_cell * cells / fused_s / 1e9
+        prof = profile_values("strip_step_4096x4096_counters.txt", STRIP_SOURCES)
+        inst = float(prof["warp_inst_per_launch_" + name]) if ("warp_inst_per_launch_" + name) in prof else None
         out[name] = {"value": cells * LB_STEPS_PER_STEP * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
                      "kernel": s.lattice_kernel,
+                     "issue_roofline": issue_roofline(inst, fused_s, args.sm_mhz) if s.lattice_kernel == "strip" else None,
                      "bytes_per_cell_step": s.bytes_per_cell, "fused_mean_us": fused_s * 1e6,
                      "node_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1),
                      "roofline_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "steps": steps}
@@ -480,7 +510,7 @@ def measure_batched(args, lb, W, torch):
     b = lb.Batch(ss)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    b.autotune(args.tune_cache, steps=3)
+    b.autotune(args.tune_cache, steps=20)
     tune_s = time.perf_counter() - t0
     shapes = {}
     for i, w in enumerate(ws):
@@ -884,8 +914,14 @@ def main():
     bytes_launch = s.bytes_per_cell * cells
     achieved = bytes_launch / fused_avg_s / 1e9
     traffic = ncu_traffic() if args.kernel in ("auto", "tile") and args.side == 1024 else None
+    csum = clk.summary()
+    args.sm_mhz = csum.get("sm_mhz") or csum.get("sm_max_mhz") or 2070.0
+    prof = profile_values("fused_step_1024x1024.txt", KERNEL_SOURCES) if args.kernel in ("auto", "tile") \
+        and args.side == 1024 else {}
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "issue": issue_roofline(float(prof["warp_inst_per_launch"]) if "warp_inst_per_launch" in prof else None,
+                                    fused_avg_s, args.sm_mhz),
             "kernel": KERNEL_NAMES[args.kernel], "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bytes_launch,
             "mean_launch_us": fused_avg_s * 1e6,

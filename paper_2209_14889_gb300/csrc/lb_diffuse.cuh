@@ -32,10 +32,21 @@ __device__ __forceinline__ void diffuse_tile(const float* src, float* dst, long 
     float* sA = sm;               // sigma on the halo-2 region [3][D2]
     float* sB = sm + 3 * D2;      // predictor on the halo-1 region [3][D1]
     const int x0 = bx * DX, y0 = by * DY;
+    // a staged index lies within one period of the lattice when the lattice is at least a tile and
+    // its halo wide: one conditional add or subtract wraps it; smaller lattices take the modulo
+    const bool near = nx >= D2W && ny >= D2H;
     for (int i = threadIdx.x; i < D2; i += blockDim.x) {
         const int ly = i / D2W, lx = i - ly * D2W;
-        const long long g = (long long)wrapd(y0 - 2 + ly, ny) * nx + wrapd(x0 - 2 + lx, nx);
-        for (int c = 0; c < 3; ++c) sA[c * D2 + i] = __ldcg(src + c * NP + g);   // written by the previous sub-step
+        int x = x0 - 2 + lx, y = y0 - 2 + ly;
+        if (near) {
+            x += x < 0 ? nx : (x >= nx ? -nx : 0);
+            y += y < 0 ? ny : (y >= ny ? -ny : 0);
+        } else {
+            x = wrapd(x, nx);
+            y = wrapd(y, ny);
+        }
+        const float* p = src + (long long)y * nx + x;
+        for (int c = 0; c < 3; ++c) sA[c * D2 + i] = __ldcg(p + c * NP);   // written by the previous sub-step
     }
     __syncthreads();
     for (int i = threadIdx.x; i < D1; i += blockDim.x) {
@@ -52,12 +63,13 @@ __device__ __forceinline__ void diffuse_tile(const float* src, float* dst, long 
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
         const int j = (ly + 2) * D2W + lx + 2, k = (ly + 1) * D1W + lx + 1;
+        float* q = dst + (long long)gy * nx + gx;
         for (int c = 0; c < 3; ++c) {
             const float* a = sA + c * D2;
             const float* b = sB + c * D1;
             const float l0 = a[j + 1] + a[j - 1] + a[j + D2W] + a[j - D2W] - 4.f * a[j];
             const float l1 = b[k + 1] + b[k - 1] + b[k + D1W] + b[k - D1W] - 4.f * b[k];
-            dst[c * NP + (long long)gy * nx + gx] = a[j] + 0.5f * D * (l0 + l1);
+            q[c * NP] = a[j] + 0.5f * D * (l0 + l1);
         }
     }
     __syncthreads();
