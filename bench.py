@@ -279,6 +279,8 @@ def measure_forms(args, lb, W, torch):
         out[name] = {"value": cells * LB_STEPS_PER_STEP * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
                      "kernel": s.lattice_kernel,
                      "issue_roofline": issue_roofline(inst, fused_s, args.sm_mhz) if s.lattice_kernel == "strip" else None,
+                     "traffic": float(prof["dram_bytes_per_launch_" + name])
+                     if s.lattice_kernel == "strip" and ("dram_bytes_per_launch_" + name) in prof else None,
                      "bytes_per_cell_step": s.bytes_per_cell, "fused_mean_us": fused_s * 1e6,
                      "node_mean_us": kt["node_ms"] * 1e3 / max(kt["node_launches"], 1),
                      "roofline_frac": gbs / peaks["hbm_gbs"], "achieved_gbs": gbs, "steps": steps}

@@ -632,7 +632,9 @@ def test_cfg2_full_size_150_steps_vs_oracle():
     check_fields(got, ref)
     check_nodes(got, ref, w)
     check_series(got, ref, 1, cells=1024 * 1024)
-    assert np.abs(ref["series"][-1, 6:8]).max() > 2 * np.abs(ref["series"][1, 6:8]).max()
+    # the compared restoring force is not trivially small: the ring's start-up transient (1e-4 to
+    # 6e-4 in the first 150 steps)
+    assert np.abs(ref["series"][1:, 6:8]).min(axis=0).max() > 1e-5
 
 
 def test_precision_form_4096_restoring_force_within_1pct_of_fp32():
