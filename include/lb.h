@@ -316,7 +316,8 @@ void lb_destroy(lb_handle* h);
  *   3 = 16x16 cells, 4 = the warp-strip kernel (LB_KERNEL_STRIP's step; periodic instances with
  *   nx >= 64 even and ny >= 32, phase launches only, else LB_EINVAL).  lb_batch_shape returns
  *   it (-1 for a bad index).
- * lb_batch_autotune: time `steps` steps with each shape that applies per distinct lattice size
+ * lb_batch_autotune: time `steps` steps with each shape that applies, first for the whole batch
+ *   (one shape for all untuned sizes), then per distinct lattice size from the best of those,
  *   and keep the fastest; the states are saved and restored, so the simulation does not advance.  cache_path
  *   (or NULL) is a flat JSON object "<gpu name>|<nx>x<ny>": shape, read first and rewritten.
  * lb_batch_set_persistent: 1 = the persistent cooperative kernel, 0 = phase launches (default;

@@ -802,30 +802,64 @@ int lb_batch_autotune(lb_batch* b, const char* cache_path, int32_t steps)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = LB_OK;
+    // time `steps` batch steps with the current shapes (after one warm-up step); < 0 on error
+    auto time_plan = [&]() -> float {
+        if ((rc = build_plan(b)) != LB_OK) return -1.f;
+        cudaError_t e = launch_batch(b, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = launch_batch(b, steps);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = bfail(b, LB_ECUDA, std::string("autotune launch: ") + cudaGetErrorString(e));
+            return -1.f;
+        }
+        return ms;
+    };
+    auto allowed = [&](int sh, int i) { return sh != SHAPE_STRIP || (!b->persistent && strip_ok(b->h[i])); };
+    // First one shape for every untuned instance (one launch per phase for the whole batch: a
+    // shape can pay only when most of the batch takes it), then each size class on its own from
+    // there, the other classes fixed.
+    if (need_tune) {
+        float best = 3.0e38f;
+        int best_s = 0;
+        for (int sh = 0; sh < N_SHAPES && rc == LB_OK; ++sh) {
+            bool ok = true;
+            for (auto& kv : classes)
+                if (!cache.count(kv.first))
+                    for (int i : kv.second) ok = ok && allowed(sh, i);
+            if (!ok) continue;
+            for (auto& kv : classes) {
+                auto hit = cache.find(kv.first);
+                for (int i : kv.second) b->shape[i] = hit != cache.end() ? hit->second : sh;
+            }
+            const float ms = time_plan();
+            if (ms >= 0.f && ms < best) {
+                best = ms;
+                best_s = sh;
+            }
+        }
+        for (auto& kv : classes)
+            if (!cache.count(kv.first))
+                for (int i : kv.second) b->shape[i] = best_s;
+    }
     for (auto& kv : classes) {
+        if (rc != LB_OK) break;
         auto hit = cache.find(kv.first);
         if (hit != cache.end()) {
             for (int i : kv.second) b->shape[i] = hit->second;
             continue;
         }
-        float best = 3.0e38f;
-        int best_s = 0;
+        const int start = b->shape[kv.second[0]];
+        float best = time_plan();
+        int best_s = start;
         for (int sh = 0; sh < N_SHAPES && rc == LB_OK; ++sh) {
-            if (sh == SHAPE_STRIP && (b->persistent || !strip_ok(b->h[kv.second[0]]))) continue;
+            if (sh == start || !allowed(sh, kv.second[0])) continue;
             for (int i : kv.second) b->shape[i] = sh;
-            if ((rc = build_plan(b)) != LB_OK) break;
-            cudaError_t e = launch_batch(b, 1);     // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            if (e == cudaSuccess) e = launch_batch(b, steps);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                rc = bfail(b, LB_ECUDA, std::string("autotune launch: ") + cudaGetErrorString(e));
-                break;
-            }
-            if (ms < best) {
+            const float ms = time_plan();
+            if (ms >= 0.f && ms < best) {
                 best = ms;
                 best_s = sh;
             }
