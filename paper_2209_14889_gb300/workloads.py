@@ -199,3 +199,36 @@ def paper_setup(model: str = "scalar", seed: int = 1, every: int = 100, **si_ove
     physics.update(tau=lu["tau"], eta_p=lu["eta_p"], Dp=lu["Dp"], walls_x=1, walls_y=1)
     return make(lu["nx"], lu["ny"], rings=rings, seed=seed, noise_amp=0.0, steps=lu["n_steps"], every=every,
                 **physics)
+
+
+# ---------------------------------------------------------------------------------------
+# Three-dimensional workloads (the D3Q19 form of Sec. IV's first extension)
+# ---------------------------------------------------------------------------------------
+
+# Recipe: D3Q19 BGK, tau = 0.8, rho0 = 1, periodic in x, y and z, fluid at rest; K^x = G0 (2, 1,
+# 1, 1, 1/2) for (K1111, K1122, K2222, K1212, K2233), G0 = 1e-3 (the two-dimensional ratios, with
+# K2233 inside the interval (0, K2222) where the transversely isotropic K^x is positive
+# definite); eta_p and D_p given directly; the Beris-Edwards parameters of the two-dimensional
+# recipe; P = P_eq d + noise with the director d along x and noise uniform in [-0.05, 0.05] per
+# component; sigma = 0.
+DEFAULT_PHYSICS_3D = dict(tau=0.8, rho0=1.0, K=(2e-3, 1e-3, 1e-3, 1e-3, 5e-4), eta_p=0.05, Dp=0.05,
+                          alpha=-0.9, beta=1.0, xi=1.1, Gamma=1.0, kappa=0.001, P_cap=0.99, ericksen=1,
+                          director=(1.0, 0.0, 0.0), n_quad=24, fext=None)
+
+
+def make3d(nx: int, ny: int, nz: int, seed: int = 1, noise_amp: float = 0.05, steps: int = 100,
+           every: int = 10, **physics) -> dict:
+    """A three-dimensional workload: physics + seeded orientation noise [3, nz, ny, nx]."""
+    w = dict(DEFAULT_PHYSICS_3D)
+    w.update(physics)
+    w.update(nx=nx, ny=ny, nz=nz, seed=seed, steps=steps, every=every, dim=3)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w["noise"] = rng.uniform(-noise_amp, noise_amp, size=(3, nz, ny, nx)) if noise_amp > 0 else None
+    w["noise_amp"] = noise_amp
+    return w
+
+
+def cube3d(seed: int = 7) -> dict:
+    """The measured three-dimensional workload: a 256^3 periodic box of the default physics
+    (2 x 28 planes x 67 M cells x 4 B = 3.8 GB of state)."""
+    return make3d(256, 256, 256, seed=seed, steps=100, every=10)
