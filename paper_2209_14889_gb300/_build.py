@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 SOURCES = ["lb_api.cu", "lb_fused.cu", "lb_strip.cu", "lb_sweep.cu", "lb_nodes.cu", "lb_lut.cu", "lb_diffuse.cu",
-           "lb_batch.cu", "lb_unet.cu", "lb_learned.cu", "lb_ckpt.cu"]
+           "lb_batch.cu", "lb_unet.cu", "lb_learned.cu", "lb_ckpt.cu", "lb3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic contraction of a product and a sum into one FMA.  The one-cell
 # kernels fuse exactly where the source calls fmaf, so the same device code rounds identically
@@ -32,7 +32,7 @@ def _deps():
     return [os.path.join(CSRC, s) for s in SOURCES] + [
         os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_handle.h"), os.path.join(CSRC, "lb_cell.cuh"),
         os.path.join(CSRC, "lb_tile.cuh"), os.path.join(CSRC, "lb_node.cuh"), os.path.join(CSRC, "lb_diffuse.cuh"), os.path.join(CSRC, "lb_vec.cuh"),
-        os.path.join(ROOT, "include", "lb.h"),
+        os.path.join(ROOT, "include", "lb.h"), os.path.join(ROOT, "include", "lb3d.h"),
         os.path.abspath(__file__)]
 
 

@@ -114,3 +114,69 @@ def test_batch_entry_points_validate_without_gpu():
     assert L.lb_batch_set_wait_limit(None, 1.0, 0) == lb.LB_EINVAL
     assert L.lb_batch_grid(None) == 0
     L.lb_batch_destroy(None)
+
+
+# ---- the three-dimensional entry points (include/lb3d.h) --------------------------------------
+
+def _declared3d():
+    src = open(os.path.join(ROOT, "include", "lb3d.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb3d_\w+)\s*\(", src)))
+
+
+def test_every_3d_symbol_is_exported_and_bound(libvlb):
+    from paper_2209_14889_gb300 import lb3d
+    names = _declared3d()
+    assert len(names) >= 12
+    assert not [n for n in names if not hasattr(libvlb, n)]
+    L = lb3d.lib()
+    for n in names:
+        assert getattr(L, n).argtypes is not None, n
+
+
+def _params3d(**kw):
+    from paper_2209_14889_gb300 import lb3d
+    base = dict(nx=8, ny=8, nz=8, readout_every=10, tau=0.8, rho0=1.0, K1111=2e-3, K1122=1e-3,
+                K2222=1e-3, K1212=1e-3, K2233=5e-4, eta_p=0.05, Dp=0.05, alpha=-0.9, beta=1.0, xi=1.1,
+                Gamma=1.0, kappa=1e-3, P_cap=0.99, ericksen=1, max_samples=16)
+    base.update(kw)
+    return lb3d.lb3d_params(**base)
+
+
+def test_3d_struct_layout_and_validation_without_gpu():
+    # lb3d_params: 4 int32, 15 doubles, 3 doubles of f_ext, 3 of P_ref, 2 int32
+    from paper_2209_14889_gb300 import lb, lb3d
+    assert ctypes.sizeof(lb3d.lb3d_params) == 16 + 15 * 8 + 24 + 24 + 8
+    L = lb3d.lib()
+    for bad, code in [(dict(nx=2), lb.LB_EINVAL), (dict(tau=0.5), lb.LB_EINVAL), (dict(eta_p=0.0), lb.LB_EINVAL),
+                      (dict(P_cap=1.0), lb.LB_EINVAL), (dict(readout_every=0), lb.LB_EINVAL),
+                      (dict(Dp=0.2), lb.LB_EUNSTABLE), (dict(alpha=-1.5), lb.LB_EUNSTABLE),
+                      (dict(kappa=0.2), lb.LB_EUNSTABLE)]:
+        h = ctypes.c_void_p()
+        assert L.lb3d_create(ctypes.byref(_params3d(**bad)), ctypes.byref(h)) == code, bad
+        assert not h.value
+
+
+def test_3d_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2209_14889_gb300 import lb, lb3d
+    h = ctypes.c_void_p()
+    rc = lb3d.lib().lb3d_create(ctypes.byref(_params3d()), ctypes.byref(h))
+    assert rc in (lb.LB_ECUDA, lb.LB_ENOMEM) and not h.value
+
+
+def test_3d_moment_table_matches_oracle_quadrature():
+    # the host table the kernels interpolate (series / recursion of the Fisher moments) against
+    # the oracle's numerical sphere quadrature, to FP32 rounding
+    import numpy as np
+    import oracle.o3d as O3
+    from paper_2209_14889_gb300 import lb3d
+    for cap in (0.9, 0.99):
+        t = lb3d.moment_table(cap)
+        assert t.shape == (8193, 2)
+        for i in (0, 1, 7, 100, 4095, 7200, 8191, 8192):
+            m = O3.orientation_moments(O3.k_of_P(cap * i / 8192), 48)
+            assert abs(t[i, 0] - m[2]) < 3e-8 and abs(t[i, 1] - m[4]) < 3e-8, (cap, i)
+        assert np.all(np.diff(t[:, 0]) >= 0) and np.all(np.diff(t[:, 1]) >= 0)
