@@ -705,7 +705,7 @@ def measure_learned_curve(args, lb, torch, budgets=(45.0, 180.0, 540.0)):
 
 
 PROFILE_CASES = ("tile_fp32", "tile_lp", "tile_scalar", "strip_fp32", "strip_lp", "strip_scalar", "sweep_fp32",
-                 "diffuse_fp32", "batch")
+                 "diffuse_fp32", "batch", "cube3d_128", "cube3d_256")
 
 
 def run_case(args):
@@ -713,11 +713,22 @@ def run_case(args):
     profiles/ capture these): tile_* and sweep_fp32 on cfg3 at 2048^2 with 4 rings, strip_* on
     cfg3 at 4096^2 with 16 rings (FP32, FP16/BF16 storage, scalar model), diffuse_fp32 on the
     2048^2 lattice with D_p = 0.6 in 3 sub-steps, batch: 64 lattices of 256^2 (cfg4 recipe,
-    D_p = 0.05, no sub-steps) in one batch with the 32 x 16 tile shape."""
+    D_p = 0.05, no sub-steps) in one batch with the 32 x 16 tile shape, cube3d_N: the
+    three-dimensional step on an N^3 periodic box of the default three-dimensional physics."""
     import torch
     from paper_2209_14889_gb300 import lb, workloads as W
     torch.cuda.set_device(0)
     case = args.case
+    if case.startswith("cube3d"):
+        from paper_2209_14889_gb300 import lb3d
+        n = int(case.split("_")[1])
+        w = W.make3d(n, n, n, seed=7)
+        s3 = lb3d.Solver3D.from_workload(w)
+        s3.step(args.steps)
+        s3.sync()
+        print(json.dumps({"case": case, "cells": n ** 3, "steps": args.steps}))
+        s3.close()
+        return
     if case == "batch":
         ws = W.cfg4(n_instances=64, sides=(256,))
         for w in ws:

@@ -85,6 +85,7 @@ __device__ __forceinline__ bool cell_of(const Args3& a, Cell& q)
     if (q.x >= a.nx || q.y >= a.ny || q.z >= a.nz) return false;
     const int nx = a.nx, nxy = a.nx * a.ny;
     q.c = q.z * nxy + q.y * nx + q.x;
+    // neighbour offsets compose: the +x neighbour of the +y neighbour is c + (xp - c) + (yp - c)
     q.xp = q.c + (q.x + 1 == nx ? 1 - nx : 1);
     q.xm = q.c + (q.x == 0 ? nx - 1 : -1);
     q.yp = q.c + (q.y + 1 == a.ny ? nx - nxy : nx);
@@ -177,10 +178,26 @@ __device__ __forceinline__ void apply_c(const Stiff& S, const float* X, float* o
 }
 
 // ---- right-hand sides of Eq. StiffCons (Jaumann derivative) and Eq. BE -----------------------
-// y: sigma (6) and dP = P - P_ref (3); yv[k][7]: stencil of component k; uc: u at the cell; G:
-// G[i][j] = d_i u_j; h: molecular field at the cell
-__device__ __forceinline__ void rhs9(const Args3& a, const float (*yv)[7], const float* uc, const float (*G)[3],
-                                     const float* h, float* r)
+// y = (sigma (6), dP = P - P_ref (3)) at the cell, reduced from each component's stencil as it is
+// loaded: the value, the advection u.grad (central differences) and the 7-point Laplacian
+struct Y9 {
+    float c[9], adv[9], lap[9];
+};
+
+__device__ __forceinline__ void load_y9(const float* base, long long NP, const Cell& q, const float* uc, Y9& y)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        float v[7];
+        stencil(base + k * NP, q, v);
+        y.c[k] = v[0];
+        y.adv[k] = uc[0] * dif(v, 0) + uc[1] * dif(v, 1) + uc[2] * dif(v, 2);
+        y.lap[k] = lap7(v);
+    }
+}
+
+// uc: u at the cell; G[i][j] = d_i u_j; h: molecular field at the cell
+__device__ __forceinline__ void rhs9(const Args3& a, const Y9& y, const float (*G)[3], const float* h, float* r)
 {
     float Psi[3][3], Om[3][3], s[3][3];
 #pragma unroll
@@ -189,37 +206,32 @@ __device__ __forceinline__ void rhs9(const Args3& a, const float (*yv)[7], const
         for (int j = 0; j < 3; ++j) {
             Psi[i][j] = 0.5f * (G[i][j] + G[j][i]);
             Om[i][j] = 0.5f * (G[i][j] - G[j][i]);
-            s[i][j] = yv[sym6(i, j)][0];
+            s[i][j] = y.c[sym6(i, j)];
         }
-    const float px = a.prx + yv[6][0], py = a.pry + yv[7][0], pz = a.prz + yv[8][0];
-    const Stiff S = stiffness(a, px, py, pz);
+    const float P[3] = {a.prx + y.c[6], a.pry + y.c[7], a.prz + y.c[8]};
+    const Stiff S = stiffness(a, P[0], P[1], P[2]);
     const float psi6[6] = {Psi[0][0], Psi[1][1], Psi[2][2], Psi[1][2], Psi[0][2], Psi[0][1]};
-    const float sig6[6] = {s[0][0], s[1][1], s[2][2], s[1][2], s[0][2], s[0][1]};
     float Cpsi[6], Csig[6];
     apply_c(S, psi6, Cpsi);
-    apply_c(S, sig6, Csig);
+    apply_c(S, y.c, Csig);
     const int I[6] = {0, 1, 2, 1, 0, 0}, J[6] = {0, 1, 2, 2, 2, 1};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         const int i = I[c], j = J[c];
-        const float adv = uc[0] * dif(yv[c], 0) + uc[1] * dif(yv[c], 1) + uc[2] * dif(yv[c], 2);
         float Jc = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Jc += Om[i][k] * s[k][j] - s[i][k] * Om[k][j];
-        r[c] = -adv - Jc + Cpsi[c] - a.inv_eta * Csig[c] + a.Dp * lap7(yv[c]);
+        r[c] = -y.adv[c] - Jc + Cpsi[c] - a.inv_eta * Csig[c] + a.Dp * y.lap[c];
     }
-    const float P[3] = {px, py, pz};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const float* v = yv[6 + i];
-        const float adv = uc[0] * dif(v, 0) + uc[1] * dif(v, 1) + uc[2] * dif(v, 2);
         float rot = 0.f, str = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             rot += Om[i][k] * P[k];
             str += Psi[i][k] * P[k];
         }
-        r[6 + i] = -adv - rot + a.xi * str - a.Gamma * h[i];
+        r[6 + i] = -y.adv[6 + i] - rot + a.xi * str - a.Gamma * h[i];
     }
 }
 
@@ -338,24 +350,28 @@ __global__ void __launch_bounds__(NT) k3_collide(const Args3 a, int mode)
         a.u[q.c] = ux;
         a.u[a.NP + q.c] = uy;
         a.u[2 * a.NP + q.c] = uz;
-        const float uu = ux * ux + uy * uy + uz * uz;
-        const int nxy = a.nx * a.ny;
+        // BGK with the Guo source: d* = d - (d - d_eq)/tau + (1 - 1/(2 tau)) w [3 (c - u) + 9 (c.u) c].F,
+        // d_eq = w (drho + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)); pushed to x + c_n (periodic: the
+        // neighbour offsets of the cell, combined per direction)
+        const float rq = 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+        const float uF3 = 3.f * (ux * F[0] + uy * F[1] + uz * F[2]);
+        const int ox[2] = {q.xp - q.c, q.xm - q.c}, oy[2] = {q.yp - q.c, q.ym - q.c}, oz[2] = {q.zp - q.c, q.zm - q.c};
+        const float keep = 1.f - a.tau_inv;
 #pragma unroll
         for (int n = 0; n < NQ; ++n) {
-            const float cx = (float)CX[n], cy = (float)CY[n], cz = (float)CZ[n];
-            const float cu = cx * ux + cy * uy + cz * uz;
+            float cu = 0.f, cF = 0.f;
+            if (CX[n]) { cu += CX[n] > 0 ? ux : -ux; cF += CX[n] > 0 ? F[0] : -F[0]; }
+            if (CY[n]) { cu += CY[n] > 0 ? uy : -uy; cF += CY[n] > 0 ? F[1] : -F[1]; }
+            if (CZ[n]) { cu += CZ[n] > 0 ? uz : -uz; cF += CZ[n] > 0 ? F[2] : -F[2]; }
             const float w = wq(n);
-            const float deq = w * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
-            const float Sg = a.guo * w *
-                ((3.f * (cx - ux) + 9.f * cu * cx) * F[0] + (3.f * (cy - uy) + 9.f * cu * cy) * F[1] +
-                 (3.f * (cz - uz) + 9.f * cu * cz) * F[2]);
-            const float out = d[n] - (d[n] - deq) * a.tau_inv + Sg;
-            // push to x + c_n (periodic)
-            int xd = q.x + CX[n], yd = q.y + CY[n], zd = q.z + CZ[n];
-            xd = xd < 0 ? xd + a.nx : (xd >= a.nx ? xd - a.nx : xd);
-            yd = yd < 0 ? yd + a.ny : (yd >= a.ny ? yd - a.ny : yd);
-            zd = zd < 0 ? zd + a.nz : (zd >= a.nz ? zd - a.nz : zd);
-            a.dst[(long long)n * a.NP + zd * nxy + yd * a.nx + xd] = out;
+            const float deq = w * (drho + rho * cu * (3.f + 4.5f * cu) - rq);
+            const float Sg = (a.guo * w) * (3.f * cF - uF3 + 9.f * cu * cF);
+            const float out = keep * d[n] + a.tau_inv * deq + Sg;
+            int dstc = q.c;
+            if (CX[n]) dstc += ox[CX[n] > 0 ? 0 : 1];
+            if (CY[n]) dstc += oy[CY[n] > 0 ? 0 : 1];
+            if (CZ[n]) dstc += oz[CZ[n] > 0 ? 0 : 1];
+            a.dst[(long long)n * a.NP + dstc] = out;
         }
         if (a.readout) {
             acc[0] = (double)drho;
@@ -406,18 +422,17 @@ __global__ void __launch_bounds__(NT) k3_predict(const Args3 a)
     if (!cell_of(a, q)) return;
     float uc[3], G[3][3];
     flow(a, q, uc, G);
-    float yv[9][7];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) stencil(a.src + (long long)(PL_S + k) * a.NP, q, yv[k]);
+    Y9 y;
+    load_y9(a.src + (long long)PL_S * a.NP, a.NP, q, uc, y);
     float h[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) h[i] = __ldg(a.hm + i * a.NP + q.c);
     float r[9];
-    rhs9(a, yv, uc, G, h, r);
+    rhs9(a, y, G, h, r);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         a.r0[k * a.NP + q.c] = r[k];
-        a.ys[k * a.NP + q.c] = yv[k][0] + r[k];
+        a.ys[k * a.NP + q.c] = y.c[k] + r[k];
     }
 }
 
@@ -427,17 +442,16 @@ __global__ void __launch_bounds__(NT) k3_correct(const Args3 a)
     if (!cell_of(a, q)) return;
     float uc[3], G[3][3];
     flow(a, q, uc, G);
-    float yv[9][7];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) stencil(a.ys + k * a.NP, q, yv[k]);
+    Y9 y;
+    load_y9(a.ys, a.NP, q, uc, y);
     // h(P*): Eq. Ffunctional at the predictor
-    const float A = bulk(a, yv[6][0], yv[7][0], yv[8][0]);
+    const float A = bulk(a, y.c[6], y.c[7], y.c[8]);
     const float Pr[3] = {a.prx, a.pry, a.prz};
     float h[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) h[i] = A * (Pr[i] + yv[6 + i][0]) - a.kappa * lap7(yv[6 + i]);
+    for (int i = 0; i < 3; ++i) h[i] = A * (Pr[i] + y.c[6 + i]) - a.kappa * y.lap[6 + i];
     float r[9];
-    rhs9(a, yv, uc, G, h, r);
+    rhs9(a, y, G, h, r);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const float y0 = __ldg(a.src + (long long)(PL_S + k) * a.NP + q.c);
