@@ -74,6 +74,7 @@ def measured_peaks():
 
 KERNEL_SOURCES = ["lb_fused.cu", "lb_tile.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h", "lb_node.cuh"]
 STRIP_SOURCES = ["lb_strip.cu", "lb_strip.cuh", "lb_cell.cuh", "lb_vec.cuh", "lb_internal.h"]
+LB3D_SOURCES = ["lb3d.cu"]
 
 
 def kernel_source_sha1(sources=KERNEL_SOURCES):
@@ -365,6 +366,46 @@ def _paper_batch(lb, W, torch, overrides, seed0):
         b.close()
         for s_ in ss:
             s_.close()
+
+
+def measure_3d(args, W):
+    """The three-dimensional step (D3Q19, stiffness averaged over the unit sphere; four kernels
+    per step) on the 256^3 periodic box of the default three-dimensional physics (3.8 GB of state,
+    larger than L2, so no flush), timed with CUDA events around every step on the handle's own
+    stream.  Its HBM roofline takes the algorithmic 224 B per cell and step (the 28 FP32 planes
+    read once and written once); traffic is the DRAM bytes per step of the four kernels from the
+    committed ncu counters at 128^3, scaled by the cell count (the kernels stream every plane, so
+    traffic grows with the cells), or null when the source changed since."""
+    from paper_2209_14889_gb300 import lb3d
+    peaks, src = measured_peaks()
+    w = W.cube3d()
+    cells = w["nx"] * w["ny"] * w["nz"]
+    s = lb3d.Solver3D.from_workload(w)
+    s.step(3)
+    s.sync()
+    steps = max(5, min(args.steps, 40))
+    s.timing(True)
+    s.step(steps)
+    s.sync()
+    ms, n = s.kernel_time()
+    s.timing(False)
+    s.sync()
+    bpc = s.bytes_per_cell
+    launches = s.launches_per_step
+    s.close()
+    step_s = ms * 1e-3 / n
+    prof = profile_values("step3d_128x128x128_counters.txt", LB3D_SOURCES)
+    traffic = float(prof["dram_bytes_per_cell_step"]) * cells if "dram_bytes_per_cell_step" in prof else None
+    inst = float(prof["warp_inst_per_cell_step"]) * cells if "warp_inst_per_cell_step" in prof else None
+    gbs = bpc * cells / step_s / 1e9
+    return {"workload": "256x256x256 periodic D3Q19 box, default three-dimensional physics (K^x = 1e-3 (2, 1, "
+                        "1, 1, 1/2), eta_p 0.05, D_p 0.05, P = P_eq x + noise 0.05)",
+            "value": cells / step_s / 1e6, "unit": "MLUPS", "ms_per_step": step_s * 1e3, "steps": n,
+            "launches_per_step": launches,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
+                         "bytes_per_cell_step": bpc},
+            "issue_roofline": issue_roofline(inst, step_s, args.sm_mhz)}
 
 
 def measure_paper_setup(args, lb, W, torch):
@@ -993,6 +1034,8 @@ def main():
             forms["paper_setup"] = measure_paper_setup(args, lb, W, torch)
         except lb.LBError as e:
             forms["paper_setup"] = {"error": str(e)}
+    if forms is not None and not args.no_batched:
+        forms["three_d"] = measure_3d(args, W)
     if forms is not None and args.learned_seconds > 0:
         forms["learned"] = measure_learned(args, lb, torch)
     if rank != 0:

@@ -67,7 +67,7 @@ struct Args3 {
     int readout;                 // k3_collide: sum the readouts of this step
     long long t;
     double* partials;            // [CTAs][7]
-    unsigned* ticket;
+    double* gpartials;           // [groups of NT CTAs][7]
     double* row;                 // readout row of this step (8 values)
     int* err_nonfinite;
 };
@@ -282,6 +282,29 @@ __global__ void __launch_bounds__(NT) k3_molecular(const Args3 a, const float* d
         }
 }
 
+// Fixed-order sums of the readout values v[7] of a CTA into out[7]: FP32 within each warp (a
+// warp's cells are 32 consecutive FP32 values), FP64 across the warps, one thread per value (FP64
+// is a narrow unit on this GPU: seven short chains, not one long one).
+__device__ __forceinline__ void cta_sum7(const float* v, double* out, float* sm)
+{
+    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        float x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sm[wid * 7 + k] = x;
+    }
+    __syncthreads();
+    if (tid < 7) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) s += (double)sm[w * 7 + tid];
+        out[tid] = s;
+    }
+}
+
 // fixed-order FP64 block sum of v[7] (thread 0 returns the totals)
 __device__ __forceinline__ void block_sum7(double* v, double* sm)
 {
@@ -305,13 +328,12 @@ __device__ __forceinline__ void block_sum7(double* v, double* sm)
 }
 
 // mode 0: the step's collision and streaming; mode 1: moments of the current state only
-__global__ void __launch_bounds__(NT) k3_collide(const Args3 a, int mode)
+__global__ void __launch_bounds__(NT, 4) k3_collide(const Args3 a, int mode)
 {
-    __shared__ double sRed[(NT / 32) * 7];
-    __shared__ int sLast;
+    __shared__ float sRedF[(NT / 32) * 7];
     Cell q;
     const bool in = cell_of(a, q);
-    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (in) {
         // F_i = d_j sigma^p_ij + d_j sigma^E_ij + f_ext,i
         float F[3] = {a.fx, a.fy, a.fz};
@@ -374,50 +396,67 @@ __global__ void __launch_bounds__(NT) k3_collide(const Args3 a, int mode)
             a.dst[(long long)n * a.NP + dstc] = out;
         }
         if (a.readout) {
-            acc[0] = (double)drho;
-            acc[1] = (double)jx; acc[2] = (double)jy; acc[3] = (double)jz;
-            acc[4] = (double)F[0]; acc[5] = (double)F[1]; acc[6] = (double)F[2];
+            acc[0] = drho;
+            acc[1] = jx; acc[2] = jy; acc[3] = jz;
+            acc[4] = F[0]; acc[5] = F[1]; acc[6] = F[2];
         }
     }
     if (mode == 1 || !a.readout) return;
-    // readout: per-CTA sums, then the last CTA adds them in CTA order
-    block_sum7(acc, sRed);
-    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    // readout: the CTA's sums; the groups of NT CTAs are added by the next kernel and the groups by
+    // the one after (kernel boundaries order the writes: no fence or atomic in this kernel)
+    const unsigned cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    cta_sum7(acc, a.partials + (long long)cta * 7, sRedF);
+}
+
+// Readout, second level (in k3_predict): CTA g < groups adds the sums of CTAs g NT .. g NT + NT - 1
+// of k3_collide in a fixed tree.
+__device__ __forceinline__ void readout_groups(const Args3& a, double* sm)
+{
     const unsigned n_ctas = gridDim.x * gridDim.y * gridDim.z;
     const unsigned cta = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    if (tid == 0) {
-        for (int k = 0; k < 7; ++k) a.partials[(long long)cta * 7 + k] = acc[k];
-        __threadfence();
-        sLast = atomicAdd(a.ticket, 1u) == n_ctas - 1u;
-    }
-    __syncthreads();
-    if (!sLast) return;
-    __threadfence();
-    // each thread sums a fixed contiguous range of CTAs, then the block adds the threads in order
+    const unsigned n_grp = (n_ctas + NT - 1) / NT;
+    if (!a.readout || cta >= n_grp) return;
+    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    const unsigned g0 = cta * NT;
     double s[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const unsigned per = (n_ctas + NT - 1) / NT;
-    const unsigned b0 = tid * per, b1 = min(n_ctas, b0 + per);
-    for (unsigned b = b0; b < b1; ++b) {
-        const volatile double* p = a.partials + (long long)b * 7;
-        for (int k = 0; k < 7; ++k) s[k] += p[k];
+    if (g0 + tid < n_ctas) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s[k] = a.partials[(long long)(g0 + tid) * 7 + k];
     }
-    __shared__ double sAll[NT * 7];
-    for (int k = 0; k < 7; ++k) sAll[tid * 7 + k] = s[k];
-    __syncthreads();
+    block_sum7(s, sm);
+    if (tid == 0)
+        for (int k = 0; k < 7; ++k) a.gpartials[(long long)cta * 7 + k] = s[k];
+}
+
+// Readout, last level (in k3_correct, CTA 0): the group sums, each thread a fixed contiguous range,
+// then the fixed tree; the row (t, mass, momentum, force) of the step.
+__device__ __forceinline__ void readout_total(const Args3& a, double* sm)
+{
+    if (!a.readout || blockIdx.x + blockIdx.y + blockIdx.z != 0) return;
+    const unsigned n_ctas = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned n_grp = (n_ctas + NT - 1) / NT;
+    const int tid = threadIdx.x + BX * (threadIdx.y + BY * threadIdx.z);
+    const unsigned per = (n_grp + NT - 1) / NT;
+    const unsigned b0 = min(n_grp, tid * per), b1 = min(n_grp, b0 + per);
+    double s[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (unsigned b = b0; b < b1; ++b) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s[k] += a.gpartials[(long long)b * 7 + k];
+    }
+    block_sum7(s, sm);
     if (tid == 0) {
         a.row[0] = (double)a.t;
         for (int k = 0; k < 7; ++k) {
-            double v = 0.0;
-            for (int t2 = 0; t2 < NT; ++t2) v += sAll[t2 * 7 + k];
-            a.row[1 + k] = v;
-            if (!isfinite(v)) atomicExch(a.err_nonfinite, 1);
+            a.row[1 + k] = s[k];
+            if (!isfinite(s[k])) atomicExch(a.err_nonfinite, 1);
         }
-        *a.ticket = 0u;
     }
 }
 
 __global__ void __launch_bounds__(NT) k3_predict(const Args3 a)
 {
+    __shared__ double sRed[(NT / 32) * 7];
+    readout_groups(a, sRed);
     Cell q;
     if (!cell_of(a, q)) return;
     float uc[3], G[3][3];
@@ -438,6 +477,8 @@ __global__ void __launch_bounds__(NT) k3_predict(const Args3 a)
 
 __global__ void __launch_bounds__(NT) k3_correct(const Args3 a)
 {
+    __shared__ double sRed[(NT / 32) * 7];
+    readout_total(a, sRed);
     Cell q;
     if (!cell_of(a, q)) return;
     float uc[3], G[3][3];
@@ -568,7 +609,7 @@ struct lb3d_handle {
     float* mom = nullptr;
     float4* lut = nullptr;
     double* partials = nullptr;
-    unsigned* ticket = nullptr;
+    double* gpartials = nullptr;
     double* series = nullptr;
     int* err = nullptr;
     long long t = 0;
@@ -640,7 +681,7 @@ v3::Args3 args_of(lb3d_handle* h)
     a.A0 = (float)(p.alpha + p.beta * (p.P_ref[0] * p.P_ref[0] + p.P_ref[1] * p.P_ref[1] + p.P_ref[2] * p.P_ref[2]));
     a.ericksen = p.ericksen;
     a.partials = h->partials;
-    a.ticket = h->ticket;
+    a.gpartials = h->gpartials;
     a.err_nonfinite = h->err;
     a.t = h->t;
     return a;
@@ -700,15 +741,15 @@ int lb3d_create(const lb3d_params* p, lb3d_handle** out)
     if (e == cudaSuccess) e = cudaMalloc(&h->r0, 9 * pb);
     if (e == cudaSuccess) e = cudaMalloc(&h->mom, 4 * pb);
     if (e == cudaSuccess) e = cudaMalloc(&h->lut, sizeof(float4) * 2 * (v3::LUT_N + 1));
+    const size_t n_grp = (n_ctas + v3::NT - 1) / v3::NT;
     if (e == cudaSuccess) e = cudaMalloc(&h->partials, sizeof(double) * 7 * n_ctas);
-    if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->gpartials, sizeof(double) * 7 * n_grp);
     if (e == cudaSuccess) e = cudaMalloc(&h->series, sizeof(double) * 8 * (size_t)p->max_samples);
     if (e == cudaSuccess) e = cudaMalloc(&h->err, sizeof(int));
     if (e != cudaSuccess) return bail(e == cudaErrorMemoryAllocation ? LB_ENOMEM : LB_ECUDA);
     std::vector<float> lut;
     v3::coefficient_table(*p, lut);
     e = cudaMemcpy(h->lut, lut.data(), sizeof(float) * lut.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
     if (e != cudaSuccess) return bail(LB_ECUDA);
     *out = h;
@@ -721,7 +762,7 @@ void lb3d_destroy(lb3d_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     dfree(h->state[0]); dfree(h->state[1]);
     dfree(h->hm); dfree(h->sE); dfree(h->u); dfree(h->ys); dfree(h->r0); dfree(h->mom);
-    dfree(h->lut); dfree(h->partials); dfree(h->ticket); dfree(h->series); dfree(h->err);
+    dfree(h->lut); dfree(h->partials); dfree(h->gpartials); dfree(h->series); dfree(h->err);
     for (auto e : h->ev) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -750,7 +791,6 @@ int lb3d_init_fields(lb3d_handle* h, const double* P_init)
     }
     CK3(h, cudaMemset(h->state[1], 0, v3::NPL * pb));
     CK3(h, cudaMemset(h->err, 0, sizeof(int)));
-    CK3(h, cudaMemset(h->ticket, 0, sizeof(unsigned)));
     h->cur = 0;
     h->t = 0;
     h->rows = 0;
