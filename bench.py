@@ -398,6 +398,16 @@ def measure_3d(args, W):
     traffic = float(prof["dram_bytes_per_cell_step"]) * cells if "dram_bytes_per_cell_step" in prof else None
     inst = float(prof["warp_inst_per_cell_step"]) * cells if "warp_inst_per_cell_step" in prof else None
     gbs = bpc * cells / step_s / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the three-dimensional oracle as it stands, one host core, one step of a 32^3 box
+        import oracle.o3d as O3
+        sim = O3.Sim3.from_workload(W.make3d(32, 32, 32, seed=7))
+        t0 = time.perf_counter()
+        sim.step(1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 32 ** 3 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": "1 step of a 32^3 box of the same physics (%.2f s)" % dt}
     return {"workload": "256x256x256 periodic D3Q19 box, default three-dimensional physics (K^x = 1e-3 (2, 1, "
                         "1, 1, 1/2), eta_p 0.05, D_p 0.05, P = P_eq x + noise 0.05)",
             "value": cells / step_s / 1e6, "unit": "MLUPS", "ms_per_step": step_s * 1e3, "steps": n,
@@ -405,7 +415,7 @@ def measure_3d(args, W):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
                          "bytes_per_cell_step": bpc},
-            "issue_roofline": issue_roofline(inst, step_s, args.sm_mhz)}
+            "issue_roofline": issue_roofline(inst, step_s, args.sm_mhz), "cpu_baseline": cpu}
 
 
 def measure_paper_setup(args, lb, W, torch):

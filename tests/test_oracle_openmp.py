@@ -56,3 +56,30 @@ def test_openmp_build_is_bitwise_the_serial_oracle(tmp_path):
     assert set(got.files) == set(ref)
     for k, v in ref.items():
         assert np.array_equal(got[k], v), k
+
+
+_CHILD3D = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle.o3d as O3
+from paper_2209_14889_gb300 import workloads as W
+assert O3._OPENMP
+s = O3.Sim3.from_workload(W.make3d(10, 8, 6, seed=4, fext=(1e-5, 0.0, -2e-5)))
+s.step(8, every=2)
+np.savez(sys.argv[2], h=s.h, sigma=s.sigma, P=s.P, series=np.array(s.series))
+"""
+
+
+def test_openmp_build_of_the_3d_oracle_is_bitwise_the_serial_one(tmp_path):
+    import oracle.o3d as O3
+    assert not O3._OPENMP
+    path = str(tmp_path / "omp3d.npz")
+    env = dict(os.environ, VLB_ORACLE_OPENMP="1", OMP_NUM_THREADS="4")
+    subprocess.check_call([sys.executable, "-c", _CHILD3D, ROOT, path], env=env, cwd=ROOT)
+    got = np.load(path)
+    s = O3.Sim3.from_workload(W.make3d(10, 8, 6, seed=4, fext=(1e-5, 0.0, -2e-5)))
+    s.step(8, every=2)
+    for k, v in (("h", s.h), ("sigma", s.sigma), ("P", s.P), ("series", np.array(s.series))):
+        assert np.array_equal(got[k], v), k
+
