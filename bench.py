@@ -374,7 +374,7 @@ def measure_3d(args, W):
     larger than L2, so no flush), timed with CUDA events around every step on the handle's own
     stream.  Its HBM roofline takes the algorithmic 224 B per cell and step (the 28 FP32 planes
     read once and written once); traffic is the DRAM bytes per step of the four kernels from the
-    committed ncu counters at 128^3, scaled by the cell count (the kernels stream every plane, so
+    committed ncu counters at 192^3, scaled by the cell count (the kernels stream every plane, so
     traffic grows with the cells), or null when the source changed since."""
     from paper_2209_14889_gb300 import lb3d
     peaks, src = measured_peaks()
@@ -394,7 +394,7 @@ def measure_3d(args, W):
     launches = s.launches_per_step
     s.close()
     step_s = ms * 1e-3 / n
-    prof = profile_values("step3d_128x128x128_counters.txt", LB3D_SOURCES)
+    prof = profile_values("step3d_192x192x192_counters.txt", LB3D_SOURCES)
     traffic = float(prof["dram_bytes_per_cell_step"]) * cells if "dram_bytes_per_cell_step" in prof else None
     inst = float(prof["warp_inst_per_cell_step"]) * cells if "warp_inst_per_cell_step" in prof else None
     gbs = bpc * cells / step_s / 1e9
@@ -756,7 +756,7 @@ def measure_learned_curve(args, lb, torch, budgets=(45.0, 180.0, 540.0)):
 
 
 PROFILE_CASES = ("tile_fp32", "tile_lp", "tile_scalar", "strip_fp32", "strip_lp", "strip_scalar", "sweep_fp32",
-                 "diffuse_fp32", "batch", "cube3d_128", "cube3d_256")
+                 "diffuse_fp32", "batch", "cube3d_128", "cube3d_192", "cube3d_256")
 
 
 def run_case(args):

@@ -100,7 +100,8 @@ int lb3d_series(lb3d_handle* h, double* dst, int32_t max_rows, int32_t* rows_wri
  * the summed device time (ms) of the steps since timing was enabled and their number. */
 int lb3d_timing(lb3d_handle* h, int32_t enable);
 int lb3d_kernel_time(lb3d_handle* h, double* ms, int64_t* steps);
-/* Kernels launched per step (4: molecular field, collision, predictor, corrector). */
+/* Kernels launched per step: 4 (Ericksen stress, collision, predictor, corrector), 3 without the
+ * Ericksen force. */
 int32_t lb3d_launches_per_step(const lb3d_handle* h);
 
 /* The orientation moments behind the kernels' table: (<mu^2>, <mu^4>) of the Fisher density at

@@ -4,11 +4,13 @@
 //
 // Kernels of one step (one thread per cell, CTAs of 32 x 4 x 2 cells, x fastest so that a warp
 // reads 128 contiguous bytes of a plane; neighbour values come through L1/L2):
-//   k3_molecular  h = (alpha + beta |P|^2) P - kappa lap P and sigma^E (Sec. II C 1) of the state
+//   k3_molecular  sigma^E (Sec. II C 1) of the state, from h = (alpha + beta |P|^2) P - kappa lap P
+//                 (launched with the Ericksen force only)
 //   k3_collide    F = div sigma^p + div sigma^E + f_ext, moments with the Guo half force, BGK
 //                 collision with the Guo source pushed to the neighbours (Eq. LB, Eq. BGK); u;
 //                 on readout steps the FP64 sums (mass, momentum, force) in a fixed order
-//   k3_predict    RHS(y) of Eq. StiffCons and Eq. BE at y = (sigma^p, P), u(t) frozen; y* = y + RHS
+//   k3_predict    RHS(y) of Eq. StiffCons and Eq. BE at y = (sigma^p, P) (h from the P stencils it
+//                 loads), u(t) frozen; y* = y + RHS
 //   k3_correct    RHS(y*) (h* from P*), y' = y + (RHS(y) + RHS(y*)) / 2 into the next state
 // The stiffness C(P) = int g(n) K(n) dOmega is applied in its transversely isotropic form about
 // P^: with the orientation moments m2 = <mu^2>, m4 = <mu^4> of the Fisher density (their
@@ -50,7 +52,6 @@ __device__ __forceinline__ float wq(int n) { return n == 0 ? 1.f / 3.f : (n < 7 
 struct Args3 {
     const float* src;            // state at t (NPL planes)
     float* dst;                  // state at t + 1
-    float* hm;                   // molecular field of the state at t [3]
     float* sE;                   // Ericksen stress [9] (i * 3 + j)
     float* u;                    // u(t) [3]
     float* ys;                   // predictor y* [9]
@@ -261,11 +262,7 @@ __global__ void __launch_bounds__(NT) k3_molecular(const Args3 a, const float* d
     const float P[3] = {a.prx + v[0][0], a.pry + v[1][0], a.prz + v[2][0]};
     float h[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        h[i] = A * P[i] - a.kappa * lap7(v[i]);
-        a.hm[i * a.NP + q.c] = h[i];
-    }
-    if (!a.ericksen) return;
+    for (int i = 0; i < 3; ++i) h[i] = A * P[i] - a.kappa * lap7(v[i]);
     float gP[3][3];                 // gP[i][k] = d_i P_k
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -463,9 +460,12 @@ __global__ void __launch_bounds__(NT) k3_predict(const Args3 a)
     flow(a, q, uc, G);
     Y9 y;
     load_y9(a.src + (long long)PL_S * a.NP, a.NP, q, uc, y);
+    // h(P): Eq. Ffunctional from the folded dP stencils
+    const float A = bulk(a, y.c[6], y.c[7], y.c[8]);
+    const float Pr[3] = {a.prx, a.pry, a.prz};
     float h[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) h[i] = __ldg(a.hm + i * a.NP + q.c);
+    for (int i = 0; i < 3; ++i) h[i] = A * (Pr[i] + y.c[6 + i]) - a.kappa * y.lap[6 + i];
     float r[9];
     rhs9(a, y, G, h, r);
 #pragma unroll
@@ -601,7 +601,6 @@ struct lb3d_handle {
     long long NP = 0;
     float* state[2] = {nullptr, nullptr};
     int cur = 0;
-    float* hm = nullptr;
     float* sE = nullptr;
     float* u = nullptr;
     float* ys = nullptr;
@@ -663,7 +662,7 @@ v3::Args3 args_of(lb3d_handle* h)
     v3::Args3 a = {};
     a.src = h->state[h->cur];
     a.dst = h->state[h->cur ^ 1];
-    a.hm = h->hm; a.sE = h->sE; a.u = h->u; a.ys = h->ys; a.r0 = h->r0; a.mom = h->mom;
+    a.sE = h->sE; a.u = h->u; a.ys = h->ys; a.r0 = h->r0; a.mom = h->mom;
     a.lut = h->lut;
     a.NP = h->NP;
     a.nx = p.nx; a.ny = p.ny; a.nz = p.nz;
@@ -698,9 +697,11 @@ int launch_check(lb3d_handle* h, const char* what)
 int launch_front(lb3d_handle* h, v3::Args3& a, int mode)
 {
     const dim3 g = grid_of(h), b(v3::BX, v3::BY, v3::BZ);
-    v3::k3_molecular<<<g, b, 0, h->stream>>>(a, a.src + (long long)v3::PL_P * h->NP);
-    int rc = launch_check(h, "k3_molecular");
-    if (rc) return rc;
+    if (h->p.ericksen) {
+        v3::k3_molecular<<<g, b, 0, h->stream>>>(a, a.src + (long long)v3::PL_P * h->NP);
+        int rc = launch_check(h, "k3_molecular");
+        if (rc) return rc;
+    }
     v3::k3_collide<<<g, b, 0, h->stream>>>(a, mode);
     return launch_check(h, "k3_collide");
 }
@@ -734,7 +735,6 @@ int lb3d_create(const lb3d_params* p, lb3d_handle** out)
     const dim3 g = grid_of(h);
     const size_t n_ctas = (size_t)g.x * g.y * g.z;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&h->state[b], v3::NPL * pb);
-    if (e == cudaSuccess) e = cudaMalloc(&h->hm, 3 * pb);
     if (e == cudaSuccess && p->ericksen) e = cudaMalloc(&h->sE, 9 * pb);
     if (e == cudaSuccess) e = cudaMalloc(&h->u, 3 * pb);
     if (e == cudaSuccess) e = cudaMalloc(&h->ys, 9 * pb);
@@ -761,7 +761,7 @@ void lb3d_destroy(lb3d_handle* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     dfree(h->state[0]); dfree(h->state[1]);
-    dfree(h->hm); dfree(h->sE); dfree(h->u); dfree(h->ys); dfree(h->r0); dfree(h->mom);
+    dfree(h->sE); dfree(h->u); dfree(h->ys); dfree(h->r0); dfree(h->mom);
     dfree(h->lut); dfree(h->partials); dfree(h->gpartials); dfree(h->series); dfree(h->err);
     for (auto e : h->ev) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -926,7 +926,7 @@ int lb3d_kernel_time(lb3d_handle* h, double* ms, int64_t* steps)
     return LB_OK;
 }
 
-int32_t lb3d_launches_per_step(const lb3d_handle* h) { return h ? 4 : 0; }
+int32_t lb3d_launches_per_step(const lb3d_handle* h) { return h ? (h->p.ericksen ? 4 : 3) : 0; }
 
 int32_t lb3d_moment_table(double P_cap, float* dst, int32_t max_entries)
 {

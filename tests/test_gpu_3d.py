@@ -52,7 +52,7 @@ def test_3d_step_vs_oracle(case):
     got = s.fields()
     pops = s.populations()
     ser = s.series()
-    assert s.t == steps and s.launches_per_step == 4
+    assert s.t == steps and s.launches_per_step == (4 if w["ericksen"] else 3)
     s.close()
     sim = O3.Sim3.from_workload(w)
     sim.step(steps, every=w["every"])
@@ -138,3 +138,56 @@ def test_3d_full_size_sampled_patches_vs_oracle():
         hp = np.stack([_patch(nxt_pop[n], c, r)[core] for n in range(19)]).astype(np.float64)
         hp += wq[:, None, None, None] * w["rho0"]
         assert np.abs(hp - sim.h[(slice(None),) + core]).max() <= 2e-6, c
+
+
+def test_3d_entry_points_device_readout_series_wrap_timing_and_zero_P():
+    # lb3d_readout into device memory equals the host copy; the series keeps the last
+    # max_samples rows in order; timing counts every step; P_init = NULL starts from P = 0
+    lb3d = _gpu()
+    import torch
+    w = W.make3d(20, 12, 8, seed=21, every=2)
+    p = lb3d.params_from_workload(w, max_samples=3)
+    s = lb3d.Solver3D(p)
+    Pref = lb3d.reference_polarization(w)
+    P = np.broadcast_to(Pref[:, None, None, None], (3, 8, 12, 20)).copy() + w["noise"]
+    s.init_fields(P)
+    s.timing(True)
+    s.step(11)
+    ms, n = s.kernel_time()
+    assert n == 11 and ms > 0
+    s.timing(False)
+    ser = s.series()
+    assert ser.shape == (3, 8) and list(ser[:, 0]) == [6.0, 8.0, 10.0]
+    for name in ("ux", "Pz", "sxy"):
+        dev = torch.empty(8 * 12 * 20, dtype=torch.float32, device="cuda")
+        s.readout_device(name, dev.data_ptr(), dev.numel())
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy().reshape(8, 12, 20), s.readout(name)), name
+    # a restart without P: fluid at rest with P = 0 stays at rest (every force and source is zero)
+    s.init_fields(None)
+    s.step(5)
+    s.sync()
+    f = s.fields()
+    for k in ("drho", "ux", "uy", "uz", "sxx", "sxy", "Px", "Py", "Pz"):
+        assert np.abs(f[k]).max() == 0.0, k
+    assert s.t == 5
+    s.close()
+
+
+def test_3d_nonfinite_state_is_reported_and_cleared():
+    # a NaN in the initial P reaches the readout sums of step 0: lb3d_sync reports
+    # LB_ENONFINITE once and clears the flag (nothing on the device faults: the table lookup
+    # clamps a NaN |P|)
+    lb3d = _gpu()
+    from paper_2209_14889_gb300 import lb
+    w = W.make3d(16, 8, 8, seed=22)
+    s = lb3d.Solver3D(lb3d.params_from_workload(w))
+    P = np.broadcast_to(lb3d.reference_polarization(w)[:, None, None, None], (3, 8, 8, 16)).copy()
+    P[1, 4, 3, 7] = np.nan
+    s.init_fields(P)
+    s.step(2)
+    with pytest.raises(lb3d.LB3DError) as e:
+        s.sync()
+    assert e.value.code == lb.LB_ENONFINITE
+    s.sync()                     # cleared
+    s.close()
