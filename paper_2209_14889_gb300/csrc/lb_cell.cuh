@@ -282,6 +282,19 @@ __device__ __forceinline__ void moments(const Phys& ph, const T* d, T Fx, T Fy, 
     uy = vfma(0.5f, Fy, jy) * inv;
 }
 
+// Readout values of one cell from its shifted populations: the mass excess and the bare momentum
+// as FP32 sums in a fixed order (the momentum as moments forms it); every lattice kernel
+// accumulates these and the cell's force in FP64, so the sums differ between kernels only in
+// the order of the FP64 additions (FP64 is a narrow unit on this GPU: five additions per cell).
+__device__ __forceinline__ void cell_readout(const float* d, float& dsum, float& jx, float& jy)
+{
+    dsum = 0.f;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) dsum += d[n];
+    jx = ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
+    jy = ((d[2] - d[4]) + (d[5] - d[8])) + (d[6] - d[7]);
+}
+
 // BGK collision with the Guo source (Eq. LB, Eq. BGK): the changes D_n = d*_n - d_n of one cell,
 // D_n = omega (d^eq_n - d_n) + (1 - 1/2tau) S_n with
 //   d^eq_n = w_n (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)),

@@ -369,17 +369,11 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
                         for (int n = 0; n < 9; ++n) gdl[n] = gd[n];
                         st_pops<PREC>(dst, NP, gdl, out, (unsigned long long)t, gC);
                         if (readout) {
-                            float dsum = 0.f;
-                            double jxs = 0.0, jys = 0.0;
-#pragma unroll
-                            for (int n = 0; n < 9; ++n) {
-                                dsum += d[n];
-                                jxs += (double)((float)S_CX[n] * d[n]);
-                                jys += (double)((float)S_CY[n] * d[n]);
-                            }
+                            float dsum, jx, jy;
+                            cell_readout(d, dsum, jx, jy);
                             acc[0] += (double)dsum;
-                            acc[1] += jxs;
-                            acc[2] += jys;
+                            acc[1] += (double)jx;
+                            acc[2] += (double)jy;
                             acc[3] += (double)Fx;
                             acc[4] += (double)Fy;
                         }

@@ -412,17 +412,11 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
                         dst[n * NP + (long long)yy * nx + xx] = dn[n] + D[n];
                     }
                     if (readout) {
-                        float dsum = 0.f;
-                        double jxs = 0.0, jys = 0.0;
-#pragma unroll
-                        for (int n = 0; n < 9; ++n) {
-                            dsum += dn[n];
-                            jxs += (double)((float)c_cx[n] * dn[n]);
-                            jys += (double)((float)c_cy[n] * dn[n]);
-                        }
+                        float dsum, jx, jy;
+                        cell::cell_readout(dn, dsum, jx, jy);
                         acc[0] += (double)dsum;
-                        acc[1] += jxs;
-                        acc[2] += jys;
+                        acc[1] += (double)jx;
+                        acc[2] += (double)jy;
                         acc[3] += (double)Fx;
                         acc[4] += (double)Fy;
                     }

@@ -565,17 +565,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 st_pops<PREC>(dst, NP, gd, out, (unsigned long long)t, g);
             }
             if (readout) {
-                float dsum = 0.f;
-                double jxs = 0.0, jys = 0.0;
-#pragma unroll
-                for (int n = 0; n < 9; ++n) {
-                    dsum += d[n];
-                    jxs += (double)((float)C_CX[n] * d[n]);
-                    jys += (double)((float)C_CY[n] * d[n]);
-                }
+                float dsum, jx, jy;
+                cell_readout(d, dsum, jx, jy);
                 acc[0] += (double)dsum;
-                acc[1] += jxs;
-                acc[2] += jys;
+                acc[1] += (double)jx;
+                acc[2] += (double)jy;
                 acc[3] += (double)Fx;
                 acc[4] += (double)Fy;
             }
@@ -830,18 +824,14 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (k == 1 && !has1) break;
-                    float dsum = 0.f;
-                    double jxs = 0.0, jys = 0.0;
+                    float dk[9];
 #pragma unroll
-                    for (int n = 0; n < 9; ++n) {
-                        const float v = lane(d[n], k);
-                        dsum += v;
-                        jxs += (double)((float)C_CX[n] * v);
-                        jys += (double)((float)C_CY[n] * v);
-                    }
+                    for (int n = 0; n < 9; ++n) dk[n] = lane(d[n], k);
+                    float dsum, jx, jy;
+                    cell_readout(dk, dsum, jx, jy);
                     acc[0] += (double)dsum;
-                    acc[1] += jxs;
-                    acc[2] += jys;
+                    acc[1] += (double)jx;
+                    acc[2] += (double)jy;
                     acc[3] += (double)lane(Fx, k);
                     acc[4] += (double)lane(Fy, k);
                 }
