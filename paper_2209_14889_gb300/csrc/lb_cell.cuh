@@ -282,10 +282,69 @@ __device__ __forceinline__ void moments(const Phys& ph, const T* d, T Fx, T Fy, 
     uy = vfma(0.5f, Fy, jy) * inv;
 }
 
+// Readout sums in double-float: a sum is kept as hi + lo, two FP32 numbers (about 48 significant
+// bits), accumulated with the error-free two-sum (Knuth): s = a + b, e = (a - (s - b')) + (b - b')
+// with b' = s - a is exactly a + b - s.  These sources are built without FMA contraction, so every
+// operation rounds as written.  FP64 is a narrow unit on this GPU (the per-cell FP64 accumulation
+// and FP64 warp shuffles of the readout made a readout step 40 % slower than a plain one at
+// 1024^2); here the cells and the warp trees run on FP32 lanes and only a CTA's five totals are
+// formed in FP64.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add(DF& x, float v)
+{
+    const float s = x.hi + v;
+    const float bp = s - x.hi;
+    const float e = (x.hi - (s - bp)) + (v - bp);
+    x.hi = s;
+    x.lo += e;
+}
+
+__device__ __forceinline__ DF df_merge(DF x, DF y)
+{
+    const float s = x.hi + y.hi;
+    const float bp = s - x.hi;
+    const float e = (x.hi - (s - bp)) + (y.hi - bp);
+    const float l = (x.lo + y.lo) + e;
+    const float h = s + l;
+    return DF{h, l - (h - s)};
+}
+
+// Fixed-order sum over the CTA (NW warps, 1-D thread index) of K double-float values per thread:
+// a shuffle tree within each warp, then the warps in order by thread k < K, which returns the
+// total of value k in FP64 (other threads return 0).  red: 2 K NW floats of shared memory.
+template <int K, int NW>
+__device__ __forceinline__ double df_cta_sum(const DF* v, float* red)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        DF x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const DF y{__shfl_down_sync(0xffffffffu, x.hi, o), __shfl_down_sync(0xffffffffu, x.lo, o)};
+            x = df_merge(x, y);
+        }
+        if (lane == 0) {
+            red[2 * (k * NW + wid)] = x.hi;
+            red[2 * (k * NW + wid) + 1] = x.lo;
+        }
+    }
+    __syncthreads();
+    double out = 0.0;
+    if (tid < K) {
+        DF s{red[2 * (tid * NW)], red[2 * (tid * NW) + 1]};
+        for (int w = 1; w < NW; ++w) s = df_merge(s, DF{red[2 * (tid * NW + w)], red[2 * (tid * NW + w) + 1]});
+        out = (double)s.hi + (double)s.lo;
+    }
+    return out;
+}
+
 // Readout values of one cell from its shifted populations: the mass excess and the bare momentum
 // as FP32 sums in a fixed order (the momentum as moments forms it); every lattice kernel
-// accumulates these and the cell's force in FP64, so the sums differ between kernels only in
-// the order of the FP64 additions (FP64 is a narrow unit on this GPU: five additions per cell).
+// accumulates these and the cell's force in double-float (above).
 __device__ __forceinline__ void cell_readout(const float* d, float& dsum, float& jx, float& jy)
 {
     dsum = 0.f;

@@ -161,9 +161,12 @@ __device__ __forceinline__ void lattice_readout(const NodeArgs& a, long long t, 
     double* row = a.series + (long long)((t / a.every) % a.series_cap) * a.row_len;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     double v4 = 0.0;
+    // the partials of other CTAs, read through L2 (after the caller's fence), several in flight
+#pragma unroll 4
     for (int k = tid; k < a.n_partials; k += blockDim.x) {
-        const volatile double* p = a.partials + (long long)k * 5;
-        v[0] += p[0]; v[1] += p[1]; v[2] += p[2]; v[3] += p[3]; v4 += p[4];
+        const double* p = a.partials + (long long)k * 5;
+        v[0] += __ldcg(p); v[1] += __ldcg(p + 1); v[2] += __ldcg(p + 2); v[3] += __ldcg(p + 3);
+        v4 += __ldcg(p + 4);
     }
     double w1[1] = {v4};
     cta_reduce<4, double>(v, dred, false);

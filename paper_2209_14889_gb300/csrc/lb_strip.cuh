@@ -218,7 +218,7 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
     const unsigned stages_s = (unsigned)__cvta_generic_to_shared(stages);
     float* fib = smem + wid * WARP_FLOATS + NST * STAGE_WORDS;
     float* tmp = fib + FIB_FLOATS;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    DF acc[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 
     // the state at t was written two launches back; the ring records, node forces and boxes by
     // the node kernel just before this one
@@ -371,11 +371,11 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
                         if (readout) {
                             float dsum, jx, jy;
                             cell_readout(d, dsum, jx, jy);
-                            acc[0] += (double)dsum;
-                            acc[1] += (double)jx;
-                            acc[2] += (double)jy;
-                            acc[3] += (double)Fx;
-                            acc[4] += (double)Fy;
+                            df_add(acc[0], dsum);
+                            df_add(acc[1], jx);
+                            df_add(acc[2], jy);
+                            df_add(acc[3], Fx);
+                            df_add(acc[4], Fy);
                         }
                         // u (and f^p on readout steps, as the tile kernel forms it) on the work
                         // box of every ring whose box holds this cell
@@ -490,21 +490,9 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
     }
 
     if (readout) {
-        // fixed-order reduction of the CTA's FP64 readout sums into its partial slot
-        double* red = reinterpret_cast<double*>(smem + OFF_RED);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            double v = acc[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-            if (lane == 0) red[q * SWARPS + wid] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 5) {
-            double v = 0.0;
-            for (int w = 0; w < SWARPS; ++w) v += red[threadIdx.x * SWARPS + w];
-            a.partials[part * 5 + threadIdx.x] = v;
-        }
+        // fixed-order reduction of the CTA's double-float readout sums into its FP64 partial slot
+        const double v = df_cta_sum<5, SWARPS>(acc, smem + OFF_RED);
+        if (threadIdx.x < 5) a.partials[part * 5 + threadIdx.x] = v;
     }
 }
 

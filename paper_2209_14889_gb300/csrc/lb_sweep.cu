@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
 
     const int c_cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int c_cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    DF acc[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     bool timed_out = false;
 
     for (int k = 0; k < K; ++k) {
@@ -414,11 +414,11 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
                     if (readout) {
                         float dsum, jx, jy;
                         cell::cell_readout(dn, dsum, jx, jy);
-                        acc[0] += (double)dsum;
-                        acc[1] += (double)jx;
-                        acc[2] += (double)jy;
-                        acc[3] += (double)Fx;
-                        acc[4] += (double)Fy;
+                        cell::df_add(acc[0], dsum);
+                        cell::df_add(acc[1], jx);
+                        cell::df_add(acc[2], jy);
+                        cell::df_add(acc[3], Fx);
+                        cell::df_add(acc[4], Fy);
                     }
                 }
                 {
@@ -481,19 +481,8 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
     }
     if (readout) {
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            double v = acc[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sRed[q * (NT / 32) + wid] = v;
-        }
-        __syncthreads();
-        if (tid < 5) {
-            double v = 0.0;
-            for (int w = 0; w < NT / 32; ++w) v += sRed[tid * (NT / 32) + w];
-            a.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5 + tid] = v;
-        }
+        const double v = cell::df_cta_sum<5, NT / 32>(acc, reinterpret_cast<float*>(sRed));
+        if (tid < 5) a.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5 + tid] = v;
     }
 }
 

@@ -372,23 +372,11 @@ __device__ __forceinline__ void box_write(const FusedArgs& a, unsigned mask, lon
         box_write_ring<R3, R3W>(a, __ffs(mask) - 1, t, gx, gy, ux, uy, readout, sS, j3);
 }
 
-// fixed-order block reduction of the FP64 readout sums of the tile into its partial slot
-__device__ __forceinline__ void readout_reduce(const FusedArgs& a, const double* acc, double* sRed, int tile_index)
+// fixed-order reduction of the tile's double-float readout sums into its FP64 partial slot
+__device__ __forceinline__ void readout_reduce(const FusedArgs& a, const DF* acc, double* sRed, int tile_index)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        double v = acc[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sRed[c * (NT / 32) + wid] = v;
-    }
-    __syncthreads();
-    if (tid < 5) {
-        double v = 0.0;
-        for (int w = 0; w < NT / 32; ++w) v += sRed[tid * (NT / 32) + w];
-        a.partials[(long long)tile_index * 5 + tid] = v;
-    }
+    const double v = df_cta_sum<5, NT / 32>(acc, reinterpret_cast<float*>(sRed));
+    if (threadIdx.x < 5) a.partials[(long long)tile_index * 5 + threadIdx.x] = v;
 }
 
 // the moments of the owned cells to the moments_out planes (MODE_MOMENTS)
@@ -504,7 +492,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     // x + c_n (Eq. LB, Eq. BGK, Guo source; exactly conservative FP32 increments).
     const long long t = step_index(a);
     const bool readout = (t % a.every) == 0;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    DF acc[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     void* dst = a.dst;
     for (int k = tid; k < R2; k += NT) {
         int lx, ly;
@@ -567,11 +555,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             if (readout) {
                 float dsum, jx, jy;
                 cell_readout(d, dsum, jx, jy);
-                acc[0] += (double)dsum;
-                acc[1] += (double)jx;
-                acc[2] += (double)jy;
-                acc[3] += (double)Fx;
-                acc[4] += (double)Fy;
+                df_add(acc[0], dsum);
+                df_add(acc[1], jx);
+                df_add(acc[2], jy);
+                df_add(acc[3], Fx);
+                df_add(acc[4], Fy);
             }
         }
     }
@@ -745,7 +733,7 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
     // is owned or not as a whole) -------------------------------------------------------------
     const long long t = step_index(a);
     const bool readout = (t % a.every) == 0;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    DF acc[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     void* dst = a.dst;
     for (int q = tid; q < R2 / 2; q += NT) {
         const int ly = q / (R2W / 2), lx = 2 * (q - ly * (R2W / 2));
@@ -829,11 +817,11 @@ __device__ __forceinline__ void tile_step2(const FusedArgs& a, int bx, int by, i
                     for (int n = 0; n < 9; ++n) dk[n] = lane(d[n], k);
                     float dsum, jx, jy;
                     cell_readout(dk, dsum, jx, jy);
-                    acc[0] += (double)dsum;
-                    acc[1] += (double)jx;
-                    acc[2] += (double)jy;
-                    acc[3] += (double)lane(Fx, k);
-                    acc[4] += (double)lane(Fy, k);
+                    df_add(acc[0], dsum);
+                    df_add(acc[1], jx);
+                    df_add(acc[2], jy);
+                    df_add(acc[3], lane(Fx, k));
+                    df_add(acc[4], lane(Fy, k));
                 }
             }
         }
