@@ -14,8 +14,9 @@ roofline  fused lattice kernel (the node step runs in its tail; --separate-nodes
           own kernel instead): algorithmic bytes (112 B/cell: 14 FP32 fields read + written)
           x cells / mean launch duration (CUDA events around each launch in a second pass over
           the same steps), against the measured HBM copy bandwidth.
-e2e       the same metric through the C ABI with host buffers: per step the whole state is
-          uploaded from pinned host memory, ten steps run, and the readout row is copied back.
+e2e       the same metric through the C ABI with host buffers: per step the whole stored state is
+          uploaded from pinned host memory in one copy (lb_write_state), ten steps run, and the
+          newest readout row is copied back (lb_series_latest).
 cpu_baseline         the FP64 oracle on one host core, one LB step of the 1024 x 1024 workload;
 cpu_baseline_openmp  the same oracle source with OpenMP on all host cores (bitwise the same).
 forms     the 4096^2 sixteen-ring workload in FP32, in the FP16/BF16 storage form and with the
@@ -1003,27 +1004,25 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # end to end through the C ABI with host buffers
-    host = {}
-    names = ["pop%d" % n for n in range(9)] + ["sxx", "syy", "sxy", "Px", "Py"]
-    for nm in names:
-        host[nm] = s.readout(nm, device=False)
-    pinned = {nm: torch.from_numpy(host[nm]).pin_memory() for nm in names}
+    # end to end through the C ABI with host buffers: every bench step uploads the whole stored
+    # state from pinned host memory in one copy (lb_write_state), runs the 10 LB steps and reads
+    # the newest readout row back (lb_series_latest)
+    nbytes = s.state_bytes
+    pinned = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    s.read_state(pinned)
     e2e_steps = max(3, min(args.steps, 10))
     barrier()
     t0 = time.perf_counter()
     d2h = 0
     for _ in range(e2e_steps):
-        for nm in names:
-            s.write_field(nm, pinned[nm])
+        s.write_state(pinned)
         s.step(LB_STEPS_PER_STEP)
-        row = s.series()[-1:]
+        row = s.series_latest(1)
         d2h = row.nbytes
     barrier()
     e2e_dt = time.perf_counter() - t0
-    h2d = sum(pinned[nm].numel() * 4 for nm in names)
     e2e = {"value": cells * LB_STEPS_PER_STEP * e2e_steps * world / e2e_dt / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(d2h),
+           "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(d2h),
            "steps": e2e_steps}
 
     rc = lb.lib().lb_sync(s.h)

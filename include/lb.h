@@ -200,6 +200,27 @@ int lb_write_field(lb_handle* h, int32_t field, const void* src, size_t bytes, i
  */
 int lb_series(lb_handle* h, double* dst, int32_t max_rows, int32_t* rows_written);
 int32_t lb_series_row_len(const lb_handle* h);
+/* The most recent n rows of the same series (oldest first), copying only those rows; host FP64
+ * [n][row length]; *rows_written gets the number copied (fewer while fewer are recorded).
+ * Synchronises the stream. */
+int lb_series_latest(lb_handle* h, double* dst, int32_t n, int32_t* rows_written);
+
+/*
+ * Bulk transfer of the stored state (the paper has no counterpart; it exists so that a caller
+ * can move a whole state between host and device in one copy).  The layout is the stored one:
+ * N_PLANES planes of nx*ny values in the handle's storage form (LB_FP32: FP32; LB_FP16_BF16: the
+ * 2-byte encodings above), x fastest: the 9 shifted populations h_n - w_n rho0 (scaled as above in
+ * the 2-byte form), sigma^p (xx, yy, xy), P - P_ref (x, y); lb_state_bytes gives the size.
+ * lb_read_state copies the current state into dst and synchronises the stream.  lb_write_state
+ * replaces the current state with src (node positions, forces and work boxes are unchanged, as
+ * with lb_write_field); the copy is enqueued on the handle's stream: host memory that is not
+ * pinned is staged before the call returns, pinned host or device memory must stay unchanged
+ * until the stream has passed the copy (lb_sync).  LB_EINVAL (null pointer or wrong size),
+ * LB_ESTATE (before lb_init_fields).
+ */
+int64_t lb_state_bytes(const lb_handle* h);
+int lb_read_state(lb_handle* h, void* dst, size_t bytes, int32_t dst_is_device);
+int lb_write_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_device);
 
 /*
  * Checkpoint and resume (the paper has no counterpart: its runs are single jobs).  lb_save

@@ -731,6 +731,47 @@ int lb_series(lb_handle* h, double* dst, int32_t max_rows, int32_t* rows_written
     return LB_OK;
 }
 
+int lb_series_latest(lb_handle* h, double* dst, int32_t n, int32_t* rows_written)
+{
+    if (!h || !dst || n < 0) return fail(h, LB_EINVAL, "bad argument");
+    const long long every = h->p.readout_every;
+    const long long recorded = (h->t + every - 1) / every;
+    const int rows = std::min(series_rows(h), n);
+    // the ring-buffer slots of the newest rows, copied one by one (oldest first); ordered on the
+    // stream after the steps that wrote them
+    for (int r = 0; r < rows; ++r) {
+        const long long k = recorded - rows + r;
+        CK(h, cudaMemcpyAsync(dst + (size_t)r * h->row_len, h->series + (size_t)(k % h->series_cap) * h->row_len,
+                              sizeof(double) * h->row_len, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (rows_written) *rows_written = rows;
+    return LB_OK;
+}
+
+int64_t lb_state_bytes(const lb_handle* h) { return h ? (int64_t)N_PLANES * h->plane * h->esz : 0; }
+
+int lb_read_state(lb_handle* h, void* dst, size_t bytes, int32_t dst_is_device)
+{
+    if (!h || !dst) return fail(h, LB_EINVAL, "null argument");
+    if (!h->fields_ready) return fail(h, LB_ESTATE, "lb_init_fields not called");
+    if (bytes != (size_t)lb_state_bytes(h)) return fail(h, LB_EINVAL, "need %lld bytes", (long long)lb_state_bytes(h));
+    CK(h, cudaMemcpyAsync(dst, h->state[h->cur], bytes, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+int lb_write_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_device)
+{
+    if (!h || !src) return fail(h, LB_EINVAL, "null argument");
+    if (!h->fields_ready) return fail(h, LB_ESTATE, "lb_init_fields not called");
+    if (bytes != (size_t)lb_state_bytes(h)) return fail(h, LB_EINVAL, "need %lld bytes", (long long)lb_state_bytes(h));
+    CK(h, cudaMemcpyAsync(h->state[h->cur], src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->stream));
+    return LB_OK;
+}
+
 int lb_restoring_force(lb_handle* h, int32_t ring, double* dst, int32_t max_k, int32_t* k_written)
 {
     if (!h || !dst || ring < 0 || ring >= h->n_rings) return fail(h, LB_EINVAL, "bad argument");

@@ -89,6 +89,10 @@ def lib():
             "lb_write_field": (ctypes.c_int, [_H, i32, vp, sz, i32]),
             "lb_series": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
             "lb_series_row_len": (i32, [_H]),
+            "lb_series_latest": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
+            "lb_state_bytes": (i64, [_H]),
+            "lb_read_state": (ctypes.c_int, [_H, vp, sz, i32]),
+            "lb_write_state": (ctypes.c_int, [_H, vp, sz, i32]),
             "lb_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
             "lb_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
             "lb_restoring_force": (ctypes.c_int, [_H, i32, vp, i32, ctypes.POINTER(i32)]),
@@ -300,6 +304,43 @@ class Solver:
         else:
             a = np.ascontiguousarray(data, dtype=np.float32)
             _check(self.h, lib().lb_write_field(self.h, fid, a.ctypes.data, a.nbytes, 0))
+
+    def series_latest(self, n: int = 1) -> np.ndarray:
+        """The most recent n readout rows (lb_series_latest)."""
+        L = lib()
+        buf = np.zeros((max(n, 1), L.lb_series_row_len(self.h)))
+        k = ctypes.c_int32(0)
+        _check(self.h, L.lb_series_latest(self.h, buf.ctypes.data, int(n), ctypes.byref(k)))
+        return buf[:k.value].copy()
+
+    @property
+    def state_bytes(self) -> int:
+        return lib().lb_state_bytes(self.h)
+
+    def read_state(self, out=None):
+        """The stored state in one copy (lb_read_state): into `out` (a torch tensor on the host or
+        the device, or a numpy array) or a new numpy uint8 array."""
+        n = self.state_bytes
+        if out is None:
+            out = np.zeros(n, dtype=np.uint8)
+        if isinstance(out, np.ndarray):
+            assert out.nbytes == n and out.flags.c_contiguous
+            _check(self.h, lib().lb_read_state(self.h, out.ctypes.data, n, 0))
+        else:
+            assert out.is_contiguous() and out.numel() * out.element_size() == n
+            _check(self.h, lib().lb_read_state(self.h, ctypes.c_void_p(out.data_ptr()), n, 1 if out.is_cuda else 0))
+        return out
+
+    def write_state(self, src):
+        """Replace the stored state in one copy (lb_write_state) from a numpy array or a torch
+        tensor (pinned host or device memory must stay unchanged until the next sync)."""
+        n = self.state_bytes
+        if isinstance(src, np.ndarray):
+            assert src.nbytes == n and src.flags.c_contiguous
+            _check(self.h, lib().lb_write_state(self.h, src.ctypes.data, n, 0))
+        else:
+            assert src.is_contiguous() and src.numel() * src.element_size() == n
+            _check(self.h, lib().lb_write_state(self.h, ctypes.c_void_p(src.data_ptr()), n, 1 if src.is_cuda else 0))
 
     def series(self) -> np.ndarray:
         L = lib()

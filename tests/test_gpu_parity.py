@@ -711,3 +711,41 @@ def test_anisotropy_closed_box_vs_oracle_and_mirror(theta0, alpha):
     assert abs(dref) > 1e-2
     assert abs(ya[-1] - dref) <= 1e-3 * abs(dref) + 5e-6
     assert np.abs(ya + yb).max() <= 1e-3 * abs(dref) + 5e-6
+
+
+def test_bulk_state_transfer_and_latest_series_rows():
+    # lb_read_state / lb_write_state move the stored state in one copy: a second handle given the
+    # first one's state (and the same rings, advanced to the same step) continues bit for bit;
+    # lb_series_latest returns the newest rows of lb_series
+    lb = _gpu()
+    import torch
+    w = W.small(96, 64, steps=0)
+    a = lb.Solver.from_workload(w)
+    a.step(13)
+    a.sync()
+    assert a.state_bytes == 14 * 96 * 64 * 4
+    host = torch.empty(a.state_bytes, dtype=torch.uint8).pin_memory()
+    a.read_state(host)
+    dev = torch.empty(a.state_bytes, dtype=torch.uint8, device="cuda")
+    a.read_state(dev)
+    torch.cuda.synchronize()
+    assert torch.equal(dev.cpu(), host)
+    # the same state written back into the same handle changes nothing
+    a.write_state(host)
+    a.step(7)
+    a.sync()
+    ref = {k: a.readout(k, device=False) for k in ("ux", "sxy", "Py", "pop5")}
+    rows = a.series()
+    assert np.array_equal(a.series_latest(1), rows[-1:])
+    assert np.array_equal(a.series_latest(3), rows[-2:])          # only two rows recorded
+    a.close()
+    b = lb.Solver.from_workload(w)
+    b.step(13)
+    b.sync()
+    b.write_state(torch.zeros(b.state_bytes, dtype=torch.uint8, device="cuda"))   # overwritten next
+    b.write_state(host)
+    b.step(7)
+    b.sync()
+    for k, v in ref.items():
+        assert np.array_equal(b.readout(k, device=False), v), k
+    b.close()
