@@ -32,9 +32,8 @@ def nvcc() -> str:
 
 
 def _deps():
-    return [os.path.join(CSRC, s) for s in SOURCES] + [
-        os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_handle.h"), os.path.join(CSRC, "lb_cell.cuh"),
-        os.path.join(CSRC, "lb_tile.cuh"), os.path.join(CSRC, "lb_node.cuh"), os.path.join(CSRC, "lb_diffuse.cuh"), os.path.join(CSRC, "lb_vec.cuh"),
+    headers = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
+    return [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, f) for f in headers] + [
         os.path.join(ROOT, "include", "lb.h"), os.path.join(ROOT, "include", "lb3d.h"),
         os.path.abspath(__file__)]
 

@@ -312,13 +312,14 @@ __device__ __forceinline__ DF df_merge(DF x, DF y)
     return DF{h, l - (h - s)};
 }
 
-// Fixed-order sum over the CTA (NW warps, 1-D thread index) of K double-float values per thread:
-// a shuffle tree within each warp, then the warps in order by thread k < K, which returns the
-// total of value k in FP64 (other threads return 0).  red: 2 K NW floats of shared memory.
-template <int K, int NW>
-__device__ __forceinline__ double df_cta_sum(const DF* v, float* red)
+// Fixed-order sum over the CTA (1-D, whole warps, at most 16 of them) of K double-float values
+// per thread: a shuffle tree within each warp, then the warps in order by thread k < K, which
+// returns the total of value k (other threads return zero).  red: 2 K (warps) floats of shared
+// memory, reusable when the call returns.
+template <int K>
+__device__ __forceinline__ DF df_block_sum(const DF* v, float* red)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         DF x = v[k];
@@ -328,18 +329,28 @@ __device__ __forceinline__ double df_cta_sum(const DF* v, float* red)
             x = df_merge(x, y);
         }
         if (lane == 0) {
-            red[2 * (k * NW + wid)] = x.hi;
-            red[2 * (k * NW + wid) + 1] = x.lo;
+            red[2 * (k * nw + wid)] = x.hi;
+            red[2 * (k * nw + wid) + 1] = x.lo;
         }
     }
     __syncthreads();
-    double out = 0.0;
+    DF s{0.f, 0.f};
     if (tid < K) {
-        DF s{red[2 * (tid * NW)], red[2 * (tid * NW) + 1]};
-        for (int w = 1; w < NW; ++w) s = df_merge(s, DF{red[2 * (tid * NW + w)], red[2 * (tid * NW + w) + 1]});
-        out = (double)s.hi + (double)s.lo;
+        s = DF{red[2 * (tid * nw)], red[2 * (tid * nw) + 1]};
+        for (int w = 1; w < nw; ++w) s = df_merge(s, DF{red[2 * (tid * nw + w)], red[2 * (tid * nw + w) + 1]});
     }
-    return out;
+    __syncthreads();
+    return s;
+}
+
+// A CTA's readout partial: value k as the double-float pair (hi, lo) at float2 index 5 slot + k of
+// the partials buffer (5 values per CTA); the lattice readout merges them in double-float and
+// forms FP64 only for the five totals.
+__device__ __forceinline__ void store_partial(double* partials, long long slot, const DF* acc, float* red)
+{
+    const DF s = df_block_sum<5>(acc, red);
+    if (threadIdx.x < 5)
+        reinterpret_cast<float2*>(partials)[slot * 5 + threadIdx.x] = make_float2(s.hi, s.lo);
 }
 
 // Readout values of one cell from its shifted populations: the mass excess and the bare momentum

@@ -153,31 +153,31 @@ struct NodeSmem {
 };
 
 // Lattice readout of step t, run by the last CTA to arrive (all its threads): the sums of the
-// per-tile partials in a fixed order into columns 0-5 of the readout row.  dred: 4 * 32 doubles
-// of shared scratch.
+// per-CTA partials (double-float pairs, cell::store_partial) in a fixed order, merged in
+// double-float on FP32 lanes, into columns 0-5 of the readout row; FP64 only for the five totals.
+// dred: 4 * 32 doubles of shared scratch.
 __device__ __forceinline__ void lattice_readout(const NodeArgs& a, long long t, double* dred)
 {
     const int tid = threadIdx.x;
     double* row = a.series + (long long)((t / a.every) % a.series_cap) * a.row_len;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    double v4 = 0.0;
+    cell::DF v[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     // the partials of other CTAs, read through L2 (after the caller's fence), several in flight
+    const float2* P = reinterpret_cast<const float2*>(a.partials);
 #pragma unroll 4
     for (int k = tid; k < a.n_partials; k += blockDim.x) {
-        const double* p = a.partials + (long long)k * 5;
-        v[0] += __ldcg(p); v[1] += __ldcg(p + 1); v[2] += __ldcg(p + 2); v[3] += __ldcg(p + 3);
-        v4 += __ldcg(p + 4);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            const float2 q = __ldcg(P + (long long)k * 5 + c);
+            v[c] = cell::df_merge(v[c], cell::DF{q.x, q.y});
+        }
     }
-    double w1[1] = {v4};
-    cta_reduce<4, double>(v, dred, false);
-    cta_reduce<1, double>(w1, dred, false);
-    if (tid == 0) {
-        row[0] = (double)t;
-        for (int c = 0; c < 4; ++c) row[1 + c] = v[c];
-        row[5] = w1[0];
-        for (int c = 0; c < 5; ++c)
-            if (!isfinite(row[1 + c])) atomicExch(&a.ctl->err_nonfinite, 1);
+    const cell::DF s = cell::df_block_sum<5>(v, reinterpret_cast<float*>(dred));
+    if (tid < 5) {
+        const double val = (double)s.hi + (double)s.lo;
+        row[1 + tid] = val;
+        if (!isfinite(val)) atomicExch(&a.ctl->err_nonfinite, 1);
     }
+    if (tid == 0) row[0] = (double)t;
 }
 
 // One CTA per block of NB nodes of one ring, with a halo of HALO nodes on each side whose

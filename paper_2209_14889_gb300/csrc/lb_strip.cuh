@@ -490,9 +490,8 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
     }
 
     if (readout) {
-        // fixed-order reduction of the CTA's double-float readout sums into its FP64 partial slot
-        const double v = df_cta_sum<5, SWARPS>(acc, smem + OFF_RED);
-        if (threadIdx.x < 5) a.partials[part * 5 + threadIdx.x] = v;
+        // fixed-order reduction of the CTA's double-float readout sums into its partial slot
+        store_partial(a.partials, part, acc, smem + OFF_RED);
     }
 }
 

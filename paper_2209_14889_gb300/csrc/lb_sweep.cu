@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(NT, 2) k_sweep(const FusedArgs a, const int ch
     }
     if (readout) {
         __syncthreads();
-        const double v = cell::df_cta_sum<5, NT / 32>(acc, reinterpret_cast<float*>(sRed));
-        if (tid < 5) a.partials[(long long)(blockIdx.y * gridDim.x + blockIdx.x) * 5 + tid] = v;
+        cell::store_partial(a.partials, (long long)blockIdx.y * gridDim.x + blockIdx.x, acc,
+                            reinterpret_cast<float*>(sRed));
     }
 }
 

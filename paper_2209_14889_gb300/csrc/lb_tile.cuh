@@ -372,11 +372,10 @@ __device__ __forceinline__ void box_write(const FusedArgs& a, unsigned mask, lon
         box_write_ring<R3, R3W>(a, __ffs(mask) - 1, t, gx, gy, ux, uy, readout, sS, j3);
 }
 
-// fixed-order reduction of the tile's double-float readout sums into its FP64 partial slot
+// fixed-order reduction of the tile's double-float readout sums into its partial slot
 __device__ __forceinline__ void readout_reduce(const FusedArgs& a, const DF* acc, double* sRed, int tile_index)
 {
-    const double v = df_cta_sum<5, NT / 32>(acc, reinterpret_cast<float*>(sRed));
-    if (threadIdx.x < 5) a.partials[(long long)tile_index * 5 + threadIdx.x] = v;
+    store_partial(a.partials, tile_index, acc, reinterpret_cast<float*>(sRed));
 }
 
 // the moments of the owned cells to the moments_out planes (MODE_MOMENTS)
