@@ -5,6 +5,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lb_internal.h"
 #include "lb_vec.cuh"
 
@@ -64,6 +66,31 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 using namespace vec;
+
+// One cell per thread (T = float): the per-cell functions below then pair the x and y parts of
+// a vector, two components of a tensor or two lattice directions onto the paired FP32
+// instructions, each lane evaluating the scalar expression (same operations, same order, same
+// fused multiply-adds), so the results are those of the scalar form: on GB300 every normal FP32
+// result agreed bit for bit with the scalar build, and only values in the subnormal range (below
+// 1e-37, in the nearly quiescent corners of a closed box) differed.  Per time step this cuts the
+// FP32 instruction count, and the kernels, which are issue-bound, by 5-7 %.
+template <class T>
+constexpr bool ONE_CELL = std::is_same<T, float>::value;
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// A paired product rounded on its own.  The compiler fuses a paired product with the paired sum
+// or difference that consumes it when every use of the product is such a sum (even under
+// -fmad=false and with the .rn intrinsics; measured on GB300), which rounds the two as one and
+// makes the result depend on the surrounding code.  Written as a paired fused multiply-add with
+// a +0 addend, the product rounds exactly as a plain product (up to the sign of a zero result)
+// and is not fused.  Products that are only multiplied further, used as a factor or addend of a
+// fused multiply-add, or scaled by a power of two (exact) need no such care.
+__device__ __forceinline__ float2 mul_r(float2 a, float2 b) { return __ffma2_rn(a, b, make_float2(0.f, 0.f)); }
+__device__ __forceinline__ float2 mul_r(float a, float2 b)
+{
+    return __ffma2_rn(make_float2(a, a), b, make_float2(0.f, 0.f));
+}
 
 // Stencil values of one component: centre, east (+x), west, north (+y), south; T = float for
 // one cell, float2 for two neighbouring cells (x, x+1).
@@ -131,6 +158,18 @@ __device__ __forceinline__ void st2(float* p, float2 v)
 template <class T>
 __device__ __forceinline__ void molecular(const Phys& ph, const StT<T>& dx, const StT<T>& dy, T& hx, T& hy)
 {
+    if constexpr (ONE_CELL<T>) {
+        // the two components of P as one pair (lanes x, y): the Laplacians and h on paired FP32
+        const float two_pd = fmaf(ph.prx, dx.c, ph.pry * dy.c);
+        const float dd = fmaf(dx.c, dx.c, dy.c * dy.c);
+        const float A = fmaf(ph.beta, fmaf(2.f, two_pd, dd), ph.A0);
+        const float2 c = f2(dx.c, dy.c);
+        const float2 L = vfma(-4.f, c, (f2(dx.e, dy.e) + f2(dx.w, dy.w)) + (f2(dx.n, dy.n) + f2(dx.s, dy.s)));
+        const float2 H = vfma(A, c + f2(ph.prx, ph.pry), (-ph.kappa) * L);
+        hx = H.x;
+        hy = H.y;
+        return;
+    }
     const T two_pd = vfma(ph.prx, dx.c, ph.pry * dy.c);
     const T dd = vfma(dx.c, dx.c, dy.c * dy.c);
     const T A = vfma(ph.beta, vfma(2.f, two_pd, dd), bc<T>(ph.A0));
@@ -151,6 +190,61 @@ __device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, T ux,
                                          T om, const StT<T>& s0, const StT<T>& s1, const StT<T>& s2,
                                          const StT<T>& p0, const StT<T>& p1, T hx, T hy, T* r)
 {
+    if constexpr (ONE_CELL<T>) {
+        // pairs: (sigma_xx, sigma_yy) stencils, (P_x, P_y) stencils, (u_x, u_y), (Psi_xx, Psi_yy),
+        // the first two rows of C~ v, the right-hand sides (r0, r1) and (r3, r4)
+        const float2 V01 = vfma(-ph.inv_eta, f2(s0.c, s1.c), f2(pxx, pyy));   // (v0, v1)
+        const float v2 = fmaf(-ph.inv_eta, s2.c, pxy);
+        // Jaumann rotation: (-J0, J0) with J0 = 2 w sxy (the negation is exact), J2 = w (syy - sxx)
+        const float2 nJ = f2(-2.f, 2.f) * (om * s2.c);
+        const float J2 = om * (s1.c - s0.c);
+        const float2 uh = 0.5f * f2(ux, uy);
+        const float D = ph.Dp;
+        const float2 E01 = f2(s0.e, s1.e), W01 = f2(s0.w, s1.w), N01 = f2(s0.n, s1.n), S01 = f2(s0.s, s1.s);
+        const float2 nadv01 = vfma(uh.x, W01 - E01, uh.y * (S01 - N01));
+        const float2 lap01 = vfma(-4.f, f2(s0.c, s1.c), (E01 + W01) + (N01 + S01));
+        const float nadv2 = fmaf(uh.x, s2.w - s2.e, uh.y * (s2.s - s2.n));
+        const float lap2 = fmaf(-4.f, s2.c, (s2.e + s2.w) + (s2.n + s2.s));
+        if (SCALAR) {
+            const float2 r01 = vfma(D, lap01, (mul_r(ph.kS8, V01) + nJ) + nadv01);
+            r[0] = r01.x;
+            r[1] = r01.y;
+            r[2] = fmaf(D, lap2, ((ph.kS8 * v2) - J2) + nadv2);
+            return;
+        }
+        const float2 P = f2(p0.c, p1.c) + f2(ph.prx, ph.pry);
+        const float2 PP = mul_r(P, P);
+        float a2, a4;
+        lut_eval(lut, ph, PP.x + PP.y, a2, a4);
+        const float c2q = PP.x - PP.y, s2q = 2.f * (P.x * P.y);
+        const float2 R2 = a2 * f2(c2q, s2q);                                              // (r2c2, r2s2)
+        const float2 R4 = a4 * f2((c2q - s2q) * (c2q + s2q), 2.f * (c2q * s2q));          // (r4c4, r4s4)
+        const float hds = (0.5f * ph.dK) * R2.y;
+        const float2 X = mul_r(f2(0.125f * ph.kX, 0.25f * ph.kX), R4);                     // (xc, xs)
+        const float C11 = fmaf(0.5f * ph.dK, R2.x, ph.kS8) + X.x;
+        const float C12 = ph.kC12 - X.x;
+        const float C13 = X.y + hds;
+        const float C22 = fmaf(-ph.dK, R2.x, C11);
+        const float C23 = hds - X.y;
+        const float C33 = fmaf(-2.f, X.x, ph.kC33);
+        const float2 C3 = f2(C13, C23);
+        const float2 Cv01 = vfma(f2(C11, C12), V01.x, vfma(f2(C12, C22), V01.y, C3 * v2));
+        const float2 hC3 = 0.5f * C3;
+        const float Cv2 = fmaf(hC3.x, V01.x, fmaf(hC3.y, V01.y, C33 * v2));
+        const float2 r01 = vfma(D, lap01, (Cv01 + nJ) + nadv01);
+        r[0] = r01.x;
+        r[1] = r01.y;
+        r[2] = fmaf(D, lap2, (Cv2 - J2) + nadv2);
+        // Eq. BE
+        const float xp0 = fmaf(pxx, P.x, pxy * P.y), xp1 = fmaf(pxy, P.x, pyy * P.y);
+        const float2 Ep = f2(p0.e, p1.e), Wp = f2(p0.w, p1.w), Np = f2(p0.n, p1.n), Sp = f2(p0.s, p1.s);
+        const float2 nadvp = vfma(uh.x, Wp - Ep, uh.y * (Sp - Np));
+        const float2 r34 = vfma(-ph.Gamma, f2(hx, hy),
+                                vfma(ph.xi, f2(xp0, xp1), f2(nadvp.x - om * P.y, fmaf(om, P.x, nadvp.y))));
+        r[3] = r34.x;
+        r[4] = r34.y;
+        return;
+    }
     // C psi - C s / eta_p = C (psi - s / eta_p)
     const T v0 = vfma(-ph.inv_eta, s0.c, pxx);
     const T v1 = vfma(-ph.inv_eta, s1.c, pyy);
@@ -206,6 +300,15 @@ __device__ __forceinline__ void rhs_cell(const Phys& ph, const float* lut, T ux,
 template <class T>
 __device__ __forceinline__ void vgrad(const StT<T>& ux, const StT<T>& uy, T& pxx, T& pyy, T& pxy, T& om)
 {
+    if constexpr (ONE_CELL<T>) {
+        const float2 A = 0.5f * (f2(ux.e, uy.n) - f2(ux.w, uy.s));   // (d_x u_x, d_y u_y)
+        const float2 B = 0.5f * (f2(uy.e, ux.n) - f2(uy.w, ux.s));   // (d_x u_y, d_y u_x)
+        pxx = A.x;
+        pyy = A.y;
+        pxy = 0.5f * (B.x + B.y);
+        om = 0.5f * (B.x - B.y);
+        return;
+    }
     const T dxux = 0.5f * (ux.e - ux.w);
     const T dyux = 0.5f * (ux.n - ux.s);
     const T dxuy = 0.5f * (uy.e - uy.w);
@@ -238,6 +341,33 @@ __device__ __forceinline__ bool meets(int a, int aw, int b, int bw, int n)
 template <class T>
 __device__ __forceinline__ void ericksen(const Phys& ph, const StT<T>& px, const StT<T>& py, T& hx, T& hy, T* E)
 {
+    if constexpr (ONE_CELL<T>) {
+        // pairs along the stencil: (east, north) and (west, south) of each component, which give
+        // the gradients of P_x and P_y as (d_x, d_y) pairs; the Laplacians add the two lanes
+        const float two_pd = fmaf(ph.prx, px.c, ph.pry * py.c);
+        const float dd = fmaf(px.c, px.c, py.c * py.c);
+        const float A = fmaf(ph.beta, fmaf(2.f, two_pd, dd), ph.A0);
+        const float2 X1 = f2(px.e, px.n), X2 = f2(px.w, px.s), Y1 = f2(py.e, py.n), Y2 = f2(py.w, py.s);
+        const float2 SX = X1 + X2, SY = Y1 + Y2;          // (e + w, n + s) of each component
+        const float2 L = f2(fmaf(-4.f, px.c, SX.x + SX.y), fmaf(-4.f, py.c, SY.x + SY.y));
+        const float2 P = f2(px.c, py.c) + f2(ph.prx, ph.pry);
+        const float2 H = vfma(A, P, (-ph.kappa) * L);
+        hx = H.x;
+        hy = H.y;
+        const float2 GX = 0.5f * (X1 - X2);               // (d_x P_x, d_y P_x)
+        const float2 GY = 0.5f * (Y1 - Y2);               // (d_x P_y, d_y P_y)
+        const float Pxhy = P.x * H.y, hxPy = H.x * P.y;
+        const float anti = Pxhy - hxPy;
+        const float sym = Pxhy + hxPy;
+        const float cross = ph.kappa * fmaf(GX.x, GX.y, GY.x * GY.y);
+        const float xs = (0.5f * ph.xi) * sym;
+        const float2 E03 = vfma(ph.xi, P * H, (-ph.kappa) * vfma(GX, GX, GY * GY));
+        E[0] = E03.x;
+        E[1] = fmaf(-0.5f, anti, xs) - cross;
+        E[2] = fmaf(0.5f, anti, xs) - cross;
+        E[3] = E03.y;
+        return;
+    }
     molecular(ph, px, py, hx, hy);
     const T Px = px.c + ph.prx, Py = py.c + ph.pry;
     const T gxPx = 0.5f * (px.e - px.w), gyPx = 0.5f * (px.n - px.s);
@@ -257,6 +387,12 @@ __device__ __forceinline__ void ericksen(const Phys& ph, const StT<T>& px, const
 template <class T>
 __device__ __forceinline__ void div_sigma(const StT<T>& sxx, const StT<T>& syy, const StT<T>& sxy, T& fx, T& fy)
 {
+    if constexpr (ONE_CELL<T>) {
+        const float2 F = 0.5f * ((f2(sxx.e, sxy.e) - f2(sxx.w, sxy.w)) + (f2(sxy.n, syy.n) - f2(sxy.s, syy.s)));
+        fx = F.x;
+        fy = F.y;
+        return;
+    }
     fx = 0.5f * ((sxx.e - sxx.w) + (sxy.n - sxy.s));
     fy = 0.5f * ((sxy.e - sxy.w) + (syy.n - syy.s));
 }
@@ -266,6 +402,12 @@ template <class T>
 __device__ __forceinline__ void div_ericksen(const StT<T>& exx, const StT<T>& exy, const StT<T>& eyx,
                                              const StT<T>& eyy, T& fx, T& fy)
 {
+    if constexpr (ONE_CELL<T>) {
+        const float2 F = 0.5f * ((f2(exx.e, eyx.e) - f2(exx.w, eyx.w)) + (f2(exy.n, eyy.n) - f2(exy.s, eyy.s)));
+        fx = F.x;
+        fy = F.y;
+        return;
+    }
     fx = 0.5f * ((exx.e - exx.w) + (exy.n - exy.s));
     fy = 0.5f * ((eyx.e - eyx.w) + (eyy.n - eyy.s));
 }
@@ -274,12 +416,66 @@ __device__ __forceinline__ void div_ericksen(const StT<T>& exx, const StT<T>& ex
 template <class T>
 __device__ __forceinline__ void moments(const Phys& ph, const T* d, T Fx, T Fy, T& drho, T& ux, T& uy)
 {
+    if constexpr (ONE_CELL<T>) {
+        // (j_x, j_y) and u as pairs; populations pair as (1, 2), (3, 4), (5, 6), (7, 8)
+        drho = (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]))) + d[8];
+        const float2 J = ((f2(d[1], d[2]) - f2(d[3], d[4])) + f2(d[5] - d[6], d[5] - d[8])) +
+                         f2(d[8] - d[7], d[6] - d[7]);
+        const float inv = __frcp_rn(drho + ph.rho0);
+        const float2 U = mul_r(inv, vfma(0.5f, f2(Fx, Fy), J));
+        ux = U.x;
+        uy = U.y;
+        return;
+    }
     drho = (((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7]))) + d[8];
     const T jx = ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
     const T jy = ((d[2] - d[4]) + (d[5] - d[8])) + (d[6] - d[7]);
     const T inv = vrcp(drho + ph.rho0);
     ux = vfma(0.5f, Fx, jx) * inv;
     uy = vfma(0.5f, Fy, jy) * inv;
+}
+
+// Post-collision populations out_n = d_n + D_n, the (1, 2), (3, 4), (5, 6), (7, 8) sums paired.
+__device__ __forceinline__ void add_pops(const float* d, const float* D, float* out)
+{
+    out[0] = d[0] + D[0];
+#pragma unroll
+    for (int n = 1; n < 9; n += 2) {
+        const float2 o = f2(d[n], d[n + 1]) + f2(D[n], D[n + 1]);
+        out[n] = o.x;
+        out[n + 1] = o.y;
+    }
+}
+
+// Heun corrector of the five fields y' = y + (R + r) / 2 (components 0, 1 and 3, 4 paired);
+// NC = 3 for the scalar model (sigma only).
+template <int NC>
+__device__ __forceinline__ void heun(const float* R, const float* r, const float* y, float* out)
+{
+    const float2 a = vfma(0.5f, f2(R[0], R[1]) + f2(r[0], r[1]), f2(y[0], y[1]));
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = fmaf(0.5f, R[2] + r[2], y[2]);
+    if (NC == 5) {
+        const float2 b = vfma(0.5f, f2(R[3], R[4]) + f2(r[3], r[4]), f2(y[3], y[4]));
+        out[3] = b.x;
+        out[4] = b.y;
+    }
+}
+
+// Heun predictor y* = y + r of the five fields (NC as for heun)
+template <int NC>
+__device__ __forceinline__ void predict(const float* y, const float* r, float* out)
+{
+    const float2 a = f2(y[0], y[1]) + f2(r[0], r[1]);
+    out[0] = a.x;
+    out[1] = a.y;
+    out[2] = y[2] + r[2];
+    if (NC == 5) {
+        const float2 b = f2(y[3], y[4]) + f2(r[3], r[4]);
+        out[3] = b.x;
+        out[4] = b.y;
+    }
 }
 
 // Readout sums in double-float: a sum is kept as hi + lo, two FP32 numbers (about 48 significant
@@ -379,6 +575,35 @@ __device__ __forceinline__ void collide(const Phys& ph, const T* d, T drho, T ux
 {
     const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
     const float om = ph.omega, g = ph.guo;
+    if constexpr (ONE_CELL<T>) {
+        // the opposite pairs (1, 3) and (2, 4) share w1 and run as the lanes of one paired
+        // evaluation, likewise (5, 7) and (6, 8) with w5: D_12 = (D1, D2), D_34 = (D3, D4), ...
+        const float nrho = (-ph.rho0) - drho;
+        const float uu = 1.5f * fmaf(ux, ux, uy * uy);
+        const float nuF3 = -3.f * fmaf(ux, Fx, uy * Fy);
+        const float base = fmaf(nrho, uu, drho);
+        const float rho3 = -3.f * nrho, rho45 = -4.5f * nrho;
+        D[0] = fmaf(om, w0 * base - d[0], (g * w0) * nuF3);
+        auto quad = [&](float w, float2 cu, float2 cF, float2 dn, float2 dm, float2& Dn, float2& Dm) {
+            const float2 ev = mul_r(w, vfma(rho45 * cu, cu, base));
+            const float2 od = mul_r(w, rho3 * cu);
+            const float2 Sev = mul_r(w, vfma(9.f * cu, cF, nuF3));
+            const float2 Sod = mul_r(3.f * w, cF);
+            Dn = vfma(om, (ev + od) - dn, g * (Sev + Sod));
+            Dm = vfma(om, (ev - od) - dm, g * (Sev - Sod));
+        };
+        float2 D12, D34, D56, D78;
+        quad(w1, f2(ux, uy), f2(Fx, Fy), f2(d[1], d[2]), f2(d[3], d[4]), D12, D34);
+        quad(w5, f2(ux + uy, uy - ux), f2(Fx + Fy, Fy - Fx), f2(d[5], d[6]), f2(d[7], d[8]), D56, D78);
+        const float2 e = (((D12 - D34) + f2(D56.x - D56.y, D56.x - D78.y)) + f2(D78.y - D78.x, D56.y - D78.x)) -
+                         f2(Fx, Fy);                      // (ex, ey)
+        D12 = vfma(-0.5f, e, D12);
+        D34 = vfma(0.5f, e, D34);
+        D[1] = D12.x; D[2] = D12.y; D[3] = D34.x; D[4] = D34.y;
+        D[5] = D56.x; D[6] = D56.y; D[7] = D78.x; D[8] = D78.y;
+        D[0] = D[0] - ((((D[1] + D[2]) + (D[3] + D[4])) + ((D[5] + D[6]) + (D[7] + D[8]))) + D[0]);
+        return;
+    }
     const T nrho = (-ph.rho0) - drho;                   // -rho
     const T uu = 1.5f * vfma(ux, ux, uy * uy);
     const T nuF3 = -3.f * vfma(ux, Fx, uy * Fy);        // -3 u.F

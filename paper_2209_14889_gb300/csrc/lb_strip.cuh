@@ -362,8 +362,8 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
                             const int yy = S_CY[n] > 0 ? gyp : (S_CY[n] < 0 ? gym : gy);
                             const int xx = S_CX[n] > 0 ? gxp : (S_CX[n] < 0 ? gxm : gx);
                             gd[n] = yy * nx + xx;
-                            out[n] = d[n] + D[n];
                         }
+                        add_pops(d, D, out);
                         long long gdl[9];
 #pragma unroll
                         for (int n = 0; n < 9; ++n) gdl[n] = gd[n];
@@ -416,13 +416,11 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
                 const St p1 = SCALAR ? St{} : st5(P1[1], P1[2], P1[0]);
                 rhs_cell<float, SCALAR>(ph, lut, U0[2], U1[2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
                                         SCALAR ? 0.f : H0[0], SCALAR ? 0.f : H1[0], Rn);
-                Y[0][2] = s0.c + Rn[0];
-                Y[1][2] = s1.c + Rn[1];
-                Y[2][2] = s2.c + Rn[2];
-                if (!SCALAR) {
-                    Y[3][2] = p0.c + Rn[3];
-                    Y[4][2] = p1.c + Rn[4];
-                }
+                const float yc[5] = {s0.c, s1.c, s2.c, p0.c, p1.c};
+                float ys[5];
+                predict<SCALAR ? 3 : 5>(yc, Rn, ys);
+#pragma unroll
+                for (int c = 0; c < (SCALAR ? 3 : 5); ++c) Y[c][2] = ys[c];
             }
 
             // ---- E: corrector at row e ----------------------------------------------------------
@@ -442,14 +440,16 @@ __device__ __forceinline__ void strip_body(const FusedArgs& a, long long t, int 
                     const int g = e * nx + gx;            // e inside [yc, yc + Hc)
                     if (SCALAR) {
                         float* dd = reinterpret_cast<float*>(dst);
-                        dd[PL_SXX * NP + g] = vfma(0.5f, R[0] + r[0], S0[0]);
-                        dd[PL_SYY * NP + g] = vfma(0.5f, R[1] + r[1], S1[0]);
-                        dd[PL_SXY * NP + g] = vfma(0.5f, R[2] + r[2], S2[0]);
+                        const float y0s[3] = {S0[0], S1[0], S2[0]};
+                        float ynew[3];
+                        heun<3>(R, r, y0s, ynew);
+                        dd[PL_SXX * NP + g] = ynew[0];
+                        dd[PL_SYY * NP + g] = ynew[1];
+                        dd[PL_SXY * NP + g] = ynew[2];
                     } else {
                         const float y0s[5] = {S0[0], S1[0], S2[0], P0[0], P1[0]};
                         float ynew[5];
-#pragma unroll
-                        for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, R[c] + r[c], y0s[c]);
+                        heun<5>(R, r, y0s, ynew);
                         st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
                     }
                 }

@@ -497,19 +497,18 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         int lx, ly;
         region_cell<TX, TY, 2>(k, lx, ly);
         const int i = ly * R2W + lx;
-        float Fx, Fy;
+        float2 F;
         div_sigma(st_at(m.sS, R3W, lx + 1, ly + 1), st_at(m.sS + R3, R3W, lx + 1, ly + 1),
-                  st_at(m.sS + 2 * R3, R3W, lx + 1, ly + 1), Fx, Fy);
+                  st_at(m.sS + 2 * R3, R3W, lx + 1, ly + 1), F.x, F.y);
         if (ph.ericksen) {
-            float ex, ey;
+            float2 E;
             div_ericksen(st_at(m.sE, R3W, lx + 1, ly + 1), st_at(m.sE + R3, R3W, lx + 1, ly + 1),
                          st_at(m.sE + 2 * R3, R3W, lx + 1, ly + 1), st_at(m.sE + 3 * R3, R3W, lx + 1, ly + 1),
-                         ex, ey);
-            Fx += ex;
-            Fy += ey;
+                         E.x, E.y);
+            F = F + E;
         }
-        Fx += m.sFib[i];
-        Fy += m.sFib[R2 + i];
+        F = F + f2(m.sFib[i], m.sFib[R2 + i]);
+        const float Fx = F.x, Fy = F.y;
         const long long g = (long long)m.sYi[ly + 2] * nx + m.sXi[lx + 2];
         float d[9];
 #pragma unroll
@@ -530,10 +529,8 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             long long gd[9];
             float out[9];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) {
-                gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
-                out[n] = d[n] + D[n];
-            }
+            for (int n = 0; n < 9; ++n) gd[n] = (long long)m.sYi[ly + 2 + C_CY[n]] * nx + m.sXi[lx + 2 + C_CX[n]];
+            add_pops(d, D, out);
             const int gy = y0 + ly - 2, gxo = x0 + lx - 2;
             if (PREC == PREC_FP32 && wall &&
                 ((a.walls_y && (gy == 0 || gy == ny - 1)) || (a.walls_x && (gxo == 0 || gxo == nx - 1)))) {
@@ -592,12 +589,12 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         rhs_cell<float, SCALAR>(ph, sL, m.sM[R2 + j2], m.sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
                                 SCALAR ? 0.f : m.sH[j3], SCALAR ? 0.f : m.sH[R3 + j3], r);
         // y* (the sigma^E buffer is dead: C has finished)
-        m.sY[i] = s0.c + r[0];
-        m.sY[R1 + i] = s1.c + r[1];
-        m.sY[2 * R1 + i] = s2.c + r[2];
-        if (!SCALAR) {
-            m.sY[3 * R1 + i] = p0.c + r[3];
-            m.sY[4 * R1 + i] = p1.c + r[4];
+        {
+            const float yc[5] = {s0.c, s1.c, s2.c, p0.c, p1.c};
+            float ys[5];
+            predict<SCALAR ? 3 : 5>(yc, r, ys);
+#pragma unroll
+            for (int c = 0; c < (SCALAR ? 3 : 5); ++c) m.sY[c * R1 + i] = ys[c];
         }
         if (k < R0) {       // an owned cell: k = (ly - 1) TX + (lx - 1)
 #pragma unroll
@@ -638,14 +635,18 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
             if (SCALAR) {
                 // sigma only: the scalar model has no P field (its planes keep their values)
                 float* d = reinterpret_cast<float*>(dst);
-                d[PL_SXX * NP + g] = vfma(0.5f, m.sR[i] + r[0], m.sS[j3]);
-                d[PL_SYY * NP + g] = vfma(0.5f, m.sR[R0 + i] + r[1], m.sS[R3 + j3]);
-                d[PL_SXY * NP + g] = vfma(0.5f, m.sR[2 * R0 + i] + r[2], m.sS[2 * R3 + j3]);
+                const float Rs[3] = {m.sR[i], m.sR[R0 + i], m.sR[2 * R0 + i]};
+                const float y0s[3] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3]};
+                float ynew[3];
+                heun<3>(Rs, r, y0s, ynew);
+                d[PL_SXX * NP + g] = ynew[0];
+                d[PL_SYY * NP + g] = ynew[1];
+                d[PL_SXY * NP + g] = ynew[2];
             } else {
                 const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], m.sP[j4], m.sP[R4 + j4]};
+                const float Rs[5] = {m.sR[i], m.sR[R0 + i], m.sR[2 * R0 + i], m.sR[3 * R0 + i], m.sR[4 * R0 + i]};
                 float ynew[5];
-#pragma unroll
-                for (int c = 0; c < 5; ++c) ynew[c] = vfma(0.5f, m.sR[c * R0 + i] + r[c], y0s[c]);
+                heun<5>(Rs, r, y0s, ynew);
                 st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
             }
         }
