@@ -301,12 +301,12 @@ template <class T>
 __device__ __forceinline__ void vgrad(const StT<T>& ux, const StT<T>& uy, T& pxx, T& pyy, T& pxy, T& om)
 {
     if constexpr (ONE_CELL<T>) {
-        const float2 A = 0.5f * (f2(ux.e, uy.n) - f2(ux.w, uy.s));   // (d_x u_x, d_y u_y)
-        const float2 B = 0.5f * (f2(uy.e, ux.n) - f2(uy.w, ux.s));   // (d_x u_y, d_y u_x)
+        const float2 A = 0.5f * (f2(ux.e, uy.e) - f2(ux.w, uy.w));   // (d_x u_x, d_x u_y)
+        const float2 B = 0.5f * (f2(ux.n, uy.n) - f2(ux.s, uy.s));   // (d_y u_x, d_y u_y)
         pxx = A.x;
-        pyy = A.y;
-        pxy = 0.5f * (B.x + B.y);
-        om = 0.5f * (B.x - B.y);
+        pyy = B.y;
+        pxy = 0.5f * (A.y + B.x);
+        om = 0.5f * (A.y - B.x);
         return;
     }
     const T dxux = 0.5f * (ux.e - ux.w);
@@ -342,26 +342,27 @@ template <class T>
 __device__ __forceinline__ void ericksen(const Phys& ph, const StT<T>& px, const StT<T>& py, T& hx, T& hy, T* E)
 {
     if constexpr (ONE_CELL<T>) {
-        // pairs along the stencil: (east, north) and (west, south) of each component, which give
-        // the gradients of P_x and P_y as (d_x, d_y) pairs; the Laplacians add the two lanes
+        // (P_x, P_y) pairs at every stencil point: the Laplacians and h as in molecular, the
+        // gradients as (d P_x, d P_y) pairs along x and along y
         const float two_pd = fmaf(ph.prx, px.c, ph.pry * py.c);
         const float dd = fmaf(px.c, px.c, py.c * py.c);
         const float A = fmaf(ph.beta, fmaf(2.f, two_pd, dd), ph.A0);
-        const float2 X1 = f2(px.e, px.n), X2 = f2(px.w, px.s), Y1 = f2(py.e, py.n), Y2 = f2(py.w, py.s);
-        const float2 SX = X1 + X2, SY = Y1 + Y2;          // (e + w, n + s) of each component
-        const float2 L = f2(fmaf(-4.f, px.c, SX.x + SX.y), fmaf(-4.f, py.c, SY.x + SY.y));
-        const float2 P = f2(px.c, py.c) + f2(ph.prx, ph.pry);
+        const float2 c = f2(px.c, py.c), Ee = f2(px.e, py.e), Ww = f2(px.w, py.w), Nn = f2(px.n, py.n),
+                     Ss = f2(px.s, py.s);
+        const float2 L = vfma(-4.f, c, (Ee + Ww) + (Nn + Ss));
+        const float2 P = c + f2(ph.prx, ph.pry);
         const float2 H = vfma(A, P, (-ph.kappa) * L);
         hx = H.x;
         hy = H.y;
-        const float2 GX = 0.5f * (X1 - X2);               // (d_x P_x, d_y P_x)
-        const float2 GY = 0.5f * (Y1 - Y2);               // (d_x P_y, d_y P_y)
+        const float2 GX = 0.5f * (Ee - Ww);               // (d_x P_x, d_x P_y)
+        const float2 GY = 0.5f * (Nn - Ss);               // (d_y P_x, d_y P_y)
         const float Pxhy = P.x * H.y, hxPy = H.x * P.y;
         const float anti = Pxhy - hxPy;
         const float sym = Pxhy + hxPy;
-        const float cross = ph.kappa * fmaf(GX.x, GX.y, GY.x * GY.y);
+        const float cross = ph.kappa * fmaf(GX.x, GY.x, GX.y * GY.y);
         const float xs = (0.5f * ph.xi) * sym;
-        const float2 E03 = vfma(ph.xi, P * H, (-ph.kappa) * vfma(GX, GX, GY * GY));
+        const float2 g2 = f2(fmaf(GX.x, GX.x, GX.y * GX.y), fmaf(GY.x, GY.x, GY.y * GY.y));
+        const float2 E03 = vfma(ph.xi, P * H, (-ph.kappa) * g2);
         E[0] = E03.x;
         E[1] = fmaf(-0.5f, anti, xs) - cross;
         E[2] = fmaf(0.5f, anti, xs) - cross;

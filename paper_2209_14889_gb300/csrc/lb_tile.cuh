@@ -115,11 +115,12 @@ __device__ __forceinline__ int mirror_row(int y, int ny)
     return y < 0 ? 0 : (y >= ny ? ny - 1 : y);   // rows this far out are never read
 }
 
-// Cells of a staged region (origin (xr, yr), W x H, nplanes planes of stride PS) that lie beyond
-// a wall take the value of their mirror image, times sgn for each wall crossed, where the image
-// is in the region (images are inside the walls, so no cell is both read and written).
+// Cells of a staged region (origin (xr, yr), W x H, nplanes planes of stride PS; value c of the
+// region's cell q at f[c PS + q CS]) that lie beyond a wall take the value of their mirror image,
+// times sgn for each wall crossed, where the image is in the region (images are inside the
+// walls, so no cell is both read and written).  CS = 2, PS = 1: an interleaved pair plane.
 __device__ __forceinline__ void mirror_ghosts(float* f, int PS, int nplanes, int W, int H, int xr, int yr,
-                                              const FusedArgs& a, float sgn)
+                                              const FusedArgs& a, float sgn, int CS = 1)
 {
     for (int q = threadIdx.x; q < W * H; q += NT) {
         const int ly = q / W, lx = q - ly * W;
@@ -129,7 +130,7 @@ __device__ __forceinline__ void mirror_ghosts(float* f, int PS, int nplanes, int
         const int mx = (ox ? mirror_row(x, a.nx) : x) - xr, my = (oy ? mirror_row(y, a.ny) : y) - yr;
         if (mx < 0 || mx >= W || my < 0 || my >= H) continue;
         const float s = (ox ? sgn : 1.f) * (oy ? sgn : 1.f);
-        for (int c = 0; c < nplanes; ++c) f[c * PS + ly * W + lx] = s * f[c * PS + my * W + mx];
+        for (int c = 0; c < nplanes; ++c) f[c * PS + (ly * W + lx) * CS] = s * f[c * PS + (my * W + mx) * CS];
     }
 }
 
@@ -137,7 +138,8 @@ __device__ __forceinline__ void mirror_ghosts(float* f, int PS, int nplanes, int
 // With nx even every staged row starts at an even column (x0 - 4, wrapped), so the rows are read
 // as aligned pairs that never straddle the periodic seam; each thread issues all its loads
 // before its shared-memory stores.  Odd nx takes single-value loads.
-template <int PREC, bool COH, int TX, int TY, bool SCALAR = false>
+// PI: P staged as interleaved (dP_x, dP_y) pairs (the one-cell step), else as two planes.
+template <int PREC, bool COH, int TX, int TY, bool SCALAR = false, bool PI = false>
 __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
 {
     using G = TileGeo<TX, TY>;
@@ -182,8 +184,13 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
         for (int k = 0; k < KP; ++k) {
             const int q = tid + k * NT;
             if (!SCALAR && q < NPP) {
-                st2<true>(m.sP + 2 * q, vp[k][0]);
-                st2<true>(m.sP + R4 + 2 * q, vp[k][1]);
+                if (PI) {
+                    *reinterpret_cast<float4*>(m.sP + 4 * q) =
+                        make_float4(vp[k][0].x, vp[k][1].x, vp[k][0].y, vp[k][1].y);
+                } else {
+                    st2<true>(m.sP + 2 * q, vp[k][0]);
+                    st2<true>(m.sP + R4 + 2 * q, vp[k][1]);
+                }
             }
         }
 #pragma unroll
@@ -203,8 +210,13 @@ __device__ __forceinline__ void stage(const FusedArgs& a, const TileMem<TX, TY>&
         for (int i = tid; i < (SCALAR ? 0 : R4); i += NT) {
             const int ly = i / R4W, lx = i - ly * R4W;
             const long long g = (long long)m.sYi[ly] * nx + m.sXi[lx];
-            m.sP[i] = ld_fld<PREC, COH>(src, NP, PL_PX, g);
-            m.sP[R4 + i] = ld_fld<PREC, COH>(src, NP, PL_PY, g);
+            const float px = ld_fld<PREC, COH>(src, NP, PL_PX, g), py = ld_fld<PREC, COH>(src, NP, PL_PY, g);
+            if (PI) {
+                reinterpret_cast<float2*>(m.sP)[i] = make_float2(px, py);
+            } else {
+                m.sP[i] = px;
+                m.sP[R4 + i] = py;
+            }
         }
         for (int i = tid; i < R3; i += NT) {
             const int ly = i / R3W, lx = i - ly * R3W;
@@ -379,7 +391,8 @@ __device__ __forceinline__ void readout_reduce(const FusedArgs& a, const DF* acc
 }
 
 // the moments of the owned cells to the moments_out planes (MODE_MOMENTS)
-template <int TX, int TY>
+// IL: u staged as interleaved (u_x, u_y) pairs and drho after them (the one-cell step)
+template <int TX, int TY, bool IL = false>
 __device__ __forceinline__ void moments_out(const FusedArgs& a, const TileMem<TX, TY>& m, int x0, int y0)
 {
     using G = TileGeo<TX, TY>;
@@ -390,9 +403,16 @@ __device__ __forceinline__ void moments_out(const FusedArgs& a, const TileMem<TX
         if (gx >= a.nx || gy >= a.ny) continue;
         const int j = (ly + 2) * G::R2W + lx + 2;
         const long long g = (long long)gy * a.nx + gx;
-        a.moments_out[g] = m.sM[j];
-        a.moments_out[NP + g] = m.sM[G::R2 + j];
-        a.moments_out[2 * NP + g] = m.sM[2 * G::R2 + j];
+        if (IL) {
+            const float2 u = reinterpret_cast<const float2*>(m.sM)[j];
+            a.moments_out[g] = m.sM[2 * G::R2 + j];
+            a.moments_out[NP + g] = u.x;
+            a.moments_out[2 * NP + g] = u.y;
+        } else {
+            a.moments_out[g] = m.sM[j];
+            a.moments_out[NP + g] = m.sM[G::R2 + j];
+            a.moments_out[2 * NP + g] = m.sM[2 * G::R2 + j];
+        }
         if (a.forces_out) {
             a.forces_out[g] = m.sFib[j];
             a.forces_out[NP + g] = m.sFib[G::R2 + j];
@@ -433,9 +453,20 @@ __device__ constexpr int C_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int C_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 __device__ constexpr int C_OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};   // c_opp(n) = -c_n
 
+// Stencils of a shared-memory plane of interleaved pairs (a, b): one 8-byte load per stencil point.
+__device__ __forceinline__ void st_pair(const float2* base, int W, int lx, int ly, St& a, St& b)
+{
+    const float2* p = base + ly * W + lx;
+    const float2 c = p[0], e = p[1], w = p[-1], n = p[W], s = p[-W];
+    a = St{c.x, e.x, w.x, n.x, s.x};
+    b = St{c.y, e.y, w.y, n.y, s.y};
+}
+
 // One TX x TY tile (tile coordinates bx, by) of the step, one cell per thread and iteration;
-// sm: TileGeo<TX, TY>::SMEM_BYTES of shared memory.  Used by the sweep comparison and kept as the
-// reference form of the paired step below.
+// sm: TileGeo<TX, TY>::SMEM_BYTES of shared memory.  The two components of P, h, u, the
+// predictor of sigma_xx, sigma_yy and of P, and of the right-hand sides live as interleaved
+// pairs in the regions TileGeo gives their planes (same sizes), so that a stencil point is one
+// 8-byte load that feeds the paired arithmetic of lb_cell.cuh directly.
 template <int MODE, int PREC, int TX, int TY, bool COH = false, bool SCALAR = false>
 __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, int tile_index, float* sm)
 {
@@ -446,6 +477,19 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     constexpr int R1W = G::R1W, R1 = G::R1;
     constexpr int R0 = G::R0;
     const TileMem<TX, TY> m(sm);
+    static_assert(R4 % 2 == 0 && R3 % 2 == 0 && R2 % 2 == 0 && R1 % 2 == 0 && R0 % 2 == 0 &&
+                  G::OFF_H % 2 == 0 && G::OFF_M % 2 == 0 && G::OFF_R % 2 == 0 && G::OFF_E % 2 == 0,
+                  "pair planes need 8-byte alignment");
+    const float2* sP2 = reinterpret_cast<const float2*>(m.sP);   // (dP_x, dP_y)        [R4]
+    float2* sH2 = reinterpret_cast<float2*>(m.sH);               // (h_x, h_y)          [R3]
+    float2* sU2 = reinterpret_cast<float2*>(m.sM);               // (u_x, u_y)          [R2]
+    float* sRho = m.sM + 2 * R2;                                 // drho (moments mode) [R2]
+    float2* sY01 = reinterpret_cast<float2*>(m.sY);              // y* of (s_xx, s_yy)  [R1]
+    float2* sY34 = sY01 + R1;                                    // y* of (dP_x, dP_y)  [R1]
+    float* sY2 = m.sY + 4 * R1;                                  // y* of s_xy          [R1]
+    float2* sR01 = reinterpret_cast<float2*>(m.sR);              // RHS(y): (r0, r1)    [R0]
+    float2* sR34 = sR01 + R0;                                    //         (r3, r4)    [R0]
+    float* sR2 = m.sR + 4 * R0;                                  //          r2         [R0]
     const float* sL = reinterpret_cast<const float*>(a.lut);   // C~ table (global, L1)
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -454,7 +498,7 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     const Phys& ph = a.ph;
     const void* src = a.src;
 
-    stage<PREC, COH, TX, TY, SCALAR>(a, m, x0, y0);
+    stage<PREC, COH, TX, TY, SCALAR, true>(a, m, x0, y0);
     // a tile whose staged cells reach beyond a wall (uniform over the CTA)
     const bool wall = (a.walls_y && (y0 - 4 < 0 || y0 + TY + 4 > ny)) || (a.walls_x && (x0 - 4 < 0 || x0 + TX + 4 > nx));
 
@@ -463,12 +507,11 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         int lx, ly;
         region_cell<TX, TY, 3>(k, lx, ly);
         const int i = ly * R3W + lx;
-        const St px = st_at(m.sP, R4W, lx + 1, ly + 1);         // dP stencils
-        const St py = st_at(m.sP + R4, R4W, lx + 1, ly + 1);
+        St px, py;
+        st_pair(sP2, R4W, lx + 1, ly + 1, px, py);               // dP stencils
         float hx, hy, E[4];
         ericksen(ph, px, py, hx, hy, E);
-        m.sH[i] = hx;
-        m.sH[R3 + i] = hy;
+        sH2[i] = f2(hx, hy);
         if (ph.ericksen) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) m.sE[c * R3 + i] = E[c];
@@ -515,10 +558,9 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         for (int n = 0; n < 9; ++n) d[n] = ld_pop<PREC, COH>(src, NP, n, g);
         float drho, ux, uy;
         moments(ph, d, Fx, Fy, drho, ux, uy);
-        m.sM[R2 + i] = ux;
-        m.sM[2 * R2 + i] = uy;
+        sU2[i] = f2(ux, uy);
         if (MODE == MODE_MOMENTS) {
-            m.sM[i] = drho;
+            sRho[i] = drho;
             m.sFib[i] = Fx;              // the total force replaces f_IB (read above, this cell only)
             m.sFib[R2 + i] = Fy;
         }
@@ -562,12 +604,12 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
     __syncthreads();
 
     if (MODE == MODE_MOMENTS) {
-        moments_out(a, m, x0, y0);
+        moments_out<TX, TY, true>(a, m, x0, y0);
         return;
     }
     if (wall) {
         // u beyond a wall: the negated image (zero velocity at the wall)
-        mirror_ghosts(m.sM + R2, R2, 2, R2W, G::R2H, x0 - 2, y0 - 2, a, -1.f);
+        mirror_ghosts(m.sM, 1, 2, R2W, G::R2H, x0 - 2, y0 - 2, a, -1.f, 2);
         __syncthreads();
     }
 
@@ -576,35 +618,42 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         int lx, ly;
         region_cell<TX, TY, 1>(k, lx, ly);
         const int i = ly * R1W + lx;
-        const int j2 = (ly + 1) * R2W + lx + 1;
         float pxx, pyy, pxy, om;
-        vgrad(m.sM + R2, m.sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
+        St su, sv;
+        st_pair(sU2, R2W, lx + 1, ly + 1, su, sv);
+        vgrad(su, sv, pxx, pyy, pxy, om);
         const St s0 = st_at(m.sS, R3W, lx + 2, ly + 2);
         const St s1 = st_at(m.sS + R3, R3W, lx + 2, ly + 2);
         const St s2 = st_at(m.sS + 2 * R3, R3W, lx + 2, ly + 2);
-        const St p0 = SCALAR ? St{} : st_at(m.sP, R4W, lx + 3, ly + 3);
-        const St p1 = SCALAR ? St{} : st_at(m.sP + R4, R4W, lx + 3, ly + 3);
-        const int j3 = (ly + 2) * R3W + lx + 2;
+        St p0{}, p1{};
+        float2 h{0.f, 0.f};
+        if (!SCALAR) {
+            st_pair(sP2, R4W, lx + 3, ly + 3, p0, p1);
+            h = sH2[(ly + 2) * R3W + lx + 2];
+        }
         float r[5];
-        rhs_cell<float, SCALAR>(ph, sL, m.sM[R2 + j2], m.sM[2 * R2 + j2], pxx, pyy, pxy, om, s0, s1, s2, p0, p1,
-                                SCALAR ? 0.f : m.sH[j3], SCALAR ? 0.f : m.sH[R3 + j3], r);
+        rhs_cell<float, SCALAR>(ph, sL, su.c, sv.c, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, h.x, h.y, r);
         // y* (the sigma^E buffer is dead: C has finished)
         {
             const float yc[5] = {s0.c, s1.c, s2.c, p0.c, p1.c};
             float ys[5];
             predict<SCALAR ? 3 : 5>(yc, r, ys);
-#pragma unroll
-            for (int c = 0; c < (SCALAR ? 3 : 5); ++c) m.sY[c * R1 + i] = ys[c];
+            sY01[i] = f2(ys[0], ys[1]);
+            sY2[i] = ys[2];
+            if (!SCALAR) sY34[i] = f2(ys[3], ys[4]);
         }
         if (k < R0) {       // an owned cell: k = (ly - 1) TX + (lx - 1)
-#pragma unroll
-            for (int c = 0; c < (SCALAR ? 3 : 5); ++c) m.sR[c * R0 + k] = r[c];
+            sR01[k] = f2(r[0], r[1]);
+            sR2[k] = r[2];
+            if (!SCALAR) sR34[k] = f2(r[3], r[4]);
         }
     }
     __syncthreads();
     if (wall) {
         // the predictor beyond a wall: the image (zero gradient of sigma and P)
-        mirror_ghosts(m.sY, R1, SCALAR ? 3 : 5, R1W, G::R1H, x0 - 1, y0 - 1, a, 1.f);
+        mirror_ghosts(m.sY, 1, 2, R1W, G::R1H, x0 - 1, y0 - 1, a, 1.f, 2);
+        mirror_ghosts(sY2, R1, 1, R1W, G::R1H, x0 - 1, y0 - 1, a, 1.f);
+        if (!SCALAR) mirror_ghosts(m.sY + 2 * R1, 1, 2, R1W, G::R1H, x0 - 1, y0 - 1, a, 1.f, 2);
         __syncthreads();
     }
 
@@ -615,27 +664,28 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
         const long long g = (long long)gy * nx + gx;
-        const int j2 = (ly + 2) * R2W + lx + 2;
-        const float ux = m.sM[R2 + j2], uy = m.sM[2 * R2 + j2];
+        St su, sv;
+        st_pair(sU2, R2W, lx + 2, ly + 2, su, sv);
+        const float ux = su.c, uy = sv.c;
         // corrector with the frozen u
         {
             float pxx, pyy, pxy, om;
-            vgrad(m.sM + R2, m.sM + 2 * R2, R2W, j2, pxx, pyy, pxy, om);
-            const St s0 = st_at(m.sY, R1W, lx + 1, ly + 1);
-            const St s1 = st_at(m.sY + R1, R1W, lx + 1, ly + 1);
-            const St s2 = st_at(m.sY + 2 * R1, R1W, lx + 1, ly + 1);
-            const St p0 = SCALAR ? St{} : st_at(m.sY + 3 * R1, R1W, lx + 1, ly + 1);
-            const St p1 = SCALAR ? St{} : st_at(m.sY + 4 * R1, R1W, lx + 1, ly + 1);
+            vgrad(su, sv, pxx, pyy, pxy, om);
+            St s0, s1, p0{}, p1{};
+            st_pair(sY01, R1W, lx + 1, ly + 1, s0, s1);
+            const St s2 = st_at(sY2, R1W, lx + 1, ly + 1);
+            if (!SCALAR) st_pair(sY34, R1W, lx + 1, ly + 1, p0, p1);
             float hx = 0.f, hy = 0.f;
             if (!SCALAR) molecular(ph, p0, p1, hx, hy);
             float r[5];
             rhs_cell<float, SCALAR>(ph, sL, ux, uy, pxx, pyy, pxy, om, s0, s1, s2, p0, p1, hx, hy, r);
             const int j3 = (ly + 3) * R3W + lx + 3;
             const int j4 = (ly + 4) * R4W + lx + 4;
+            const float2 R01 = sR01[i];
             if (SCALAR) {
                 // sigma only: the scalar model has no P field (its planes keep their values)
                 float* d = reinterpret_cast<float*>(dst);
-                const float Rs[3] = {m.sR[i], m.sR[R0 + i], m.sR[2 * R0 + i]};
+                const float Rs[3] = {R01.x, R01.y, sR2[i]};
                 const float y0s[3] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3]};
                 float ynew[3];
                 heun<3>(Rs, r, y0s, ynew);
@@ -643,8 +693,9 @@ __device__ __forceinline__ void tile_step(const FusedArgs& a, int bx, int by, in
                 d[PL_SYY * NP + g] = ynew[1];
                 d[PL_SXY * NP + g] = ynew[2];
             } else {
-                const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], m.sP[j4], m.sP[R4 + j4]};
-                const float Rs[5] = {m.sR[i], m.sR[R0 + i], m.sR[2 * R0 + i], m.sR[3 * R0 + i], m.sR[4 * R0 + i]};
+                const float2 P0 = sP2[j4], R34 = sR34[i];
+                const float y0s[5] = {m.sS[j3], m.sS[R3 + j3], m.sS[2 * R3 + j3], P0.x, P0.y};
+                const float Rs[5] = {R01.x, R01.y, sR2[i], R34.x, R34.y};
                 float ynew[5];
                 heun<5>(Rs, r, y0s, ynew);
                 st_flds<PREC>(dst, NP, g, ynew, (unsigned long long)t);
