@@ -223,6 +223,23 @@ int lb_read_state(lb_handle* h, void* dst, size_t bytes, int32_t dst_is_device);
 int lb_write_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_device);
 
 /*
+ * lb_write_state in two halves, so that the upload of the next state overlaps the steps running
+ * on the current one (the paper has no counterpart; this serves callers that feed a new state
+ * every few steps).  lb_stage_state enqueues the copy of a whole stored state (layout and size as
+ * for lb_write_state) into a staging buffer of the handle on a copy stream of its own and returns;
+ * lb_commit_state makes the handle's stream wait for that upload and copy the staged state over
+ * the current one (a device-to-device copy on the handle's stream), in stream order with the steps
+ * before and after it.  The staging buffer (one state) and the copy stream are created on the
+ * first lb_stage_state.  A second lb_stage_state before a commit replaces the staged state; a
+ * stage after a commit waits on the GPU until that commit's copy has read the buffer.  src must
+ * stay unchanged until the upload is done (pinned host memory overlaps; host memory that is not
+ * pinned is staged before the call returns).  LB_EINVAL (null pointer or wrong size), LB_ESTATE
+ * (before lb_init_fields; lb_commit_state with nothing staged), LB_ENOMEM / LB_ECUDA.
+ */
+int lb_stage_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_device);
+int lb_commit_state(lb_handle* h);
+
+/*
  * Checkpoint and resume (the paper has no counterpart: its runs are single jobs).  lb_save
  * finishes the handle's queued work and writes to the file `path` a raw snapshot of everything
  * a step carries over to the next: both state buffers and which one is current, the step

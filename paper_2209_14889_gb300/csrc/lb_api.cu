@@ -772,6 +772,39 @@ int lb_write_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_d
     return LB_OK;
 }
 
+int lb_stage_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_device)
+{
+    if (!h || !src) return fail(h, LB_EINVAL, "null argument");
+    if (!h->fields_ready) return fail(h, LB_ESTATE, "lb_init_fields not called");
+    if (bytes != (size_t)lb_state_bytes(h)) return fail(h, LB_EINVAL, "need %lld bytes", (long long)lb_state_bytes(h));
+    if (!h->copy_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->ev_staged, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_release, cudaEventDisableTiming));
+    }
+    if (!h->stage_buf) CK(h, cudaMalloc(&h->stage_buf, bytes));
+    // the previous commit's copy out of the staging buffer must be done before it is overwritten
+    if (h->release_pending) CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_release, 0));
+    CK(h, cudaMemcpyAsync(h->stage_buf, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->copy_stream));
+    CK(h, cudaEventRecord(h->ev_staged, h->copy_stream));
+    h->staged = true;
+    return LB_OK;
+}
+
+int lb_commit_state(lb_handle* h)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (!h->staged) return fail(h, LB_ESTATE, "lb_commit_state: no state staged (lb_stage_state)");
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_staged, 0));
+    CK(h, cudaMemcpyAsync(h->state[h->cur], h->stage_buf, (size_t)lb_state_bytes(h), cudaMemcpyDeviceToDevice,
+                          h->stream));
+    CK(h, cudaEventRecord(h->ev_release, h->stream));
+    h->staged = false;
+    h->release_pending = true;
+    return LB_OK;
+}
+
 int lb_restoring_force(lb_handle* h, int32_t ring, double* dst, int32_t max_k, int32_t* k_written)
 {
     if (!h || !dst || ring < 0 || ring >= h->n_rings) return fail(h, LB_EINVAL, "bad argument");
@@ -965,6 +998,13 @@ void lb_destroy(lb_handle* h)
     dfree(h->partials);
     dfree(h->series);
     dfree(h->moments);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    if (h->ev_staged) cudaEventDestroy(h->ev_staged);
+    if (h->ev_release) cudaEventDestroy(h->ev_release);
+    dfree(h->stage_buf);
     for (auto e : h->ev_fused) cudaEventDestroy(e);
     for (auto e : h->ev_nodes) cudaEventDestroy(e);
     delete h;

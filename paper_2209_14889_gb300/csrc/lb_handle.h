@@ -60,6 +60,13 @@ struct lb_handle {
     long long box_floats = 0;
     bool fields_ready = false;
     long long t = 0;
+    // lb_stage_state / lb_commit_state: a staged copy of a whole stored state, uploaded on a copy
+    // stream while the handle's stream computes (allocated on first use)
+    void* stage_buf = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_staged = nullptr;        // the upload into stage_buf is complete
+    cudaEvent_t ev_release = nullptr;       // the handle's stream has read stage_buf
+    bool staged = false, release_pending = false;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_fused, ev_nodes;

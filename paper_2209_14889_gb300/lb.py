@@ -93,6 +93,8 @@ def lib():
             "lb_state_bytes": (i64, [_H]),
             "lb_read_state": (ctypes.c_int, [_H, vp, sz, i32]),
             "lb_write_state": (ctypes.c_int, [_H, vp, sz, i32]),
+            "lb_stage_state": (ctypes.c_int, [_H, vp, sz, i32]),
+            "lb_commit_state": (ctypes.c_int, [_H]),
             "lb_save": (ctypes.c_int, [_H, ctypes.c_char_p]),
             "lb_load": (ctypes.c_int, [_H, ctypes.c_char_p]),
             "lb_restoring_force": (ctypes.c_int, [_H, i32, vp, i32, ctypes.POINTER(i32)]),
@@ -341,6 +343,21 @@ class Solver:
         else:
             assert src.is_contiguous() and src.numel() * src.element_size() == n
             _check(self.h, lib().lb_write_state(self.h, ctypes.c_void_p(src.data_ptr()), n, 1 if src.is_cuda else 0))
+
+    def stage_state(self, src):
+        """Upload a whole stored state into the handle's staging buffer on its copy stream
+        (lb_stage_state), overlapping the steps queued meanwhile; commit_state makes it current."""
+        n = self.state_bytes
+        if isinstance(src, np.ndarray):
+            assert src.nbytes == n and src.flags.c_contiguous
+            _check(self.h, lib().lb_stage_state(self.h, src.ctypes.data, n, 0))
+        else:
+            assert src.is_contiguous() and src.numel() * src.element_size() == n
+            _check(self.h, lib().lb_stage_state(self.h, ctypes.c_void_p(src.data_ptr()), n, 1 if src.is_cuda else 0))
+
+    def commit_state(self):
+        """Make the staged state current, in stream order (lb_commit_state)."""
+        _check(self.h, lib().lb_commit_state(self.h))
 
     def series(self) -> np.ndarray:
         L = lib()

@@ -749,3 +749,47 @@ def test_bulk_state_transfer_and_latest_series_rows():
     for k, v in ref.items():
         assert np.array_equal(b.readout(k, device=False), v), k
     b.close()
+
+
+def test_staged_state_upload_overlaps_and_matches_write_state():
+    # lb_stage_state / lb_commit_state give what lb_write_state gives, in stream order: states
+    # staged while steps run become current only at the commit, a second stage before a commit
+    # replaces the first, and a commit with nothing staged is refused
+    lb = _gpu()
+    import torch
+    w = W.small(96, 64, steps=0)
+    a = lb.Solver.from_workload(w)
+    a.step(13)
+    a.sync()
+    s13 = torch.empty(a.state_bytes, dtype=torch.uint8).pin_memory()
+    a.read_state(s13)
+    a.step(5)
+    a.sync()
+    s18 = torch.empty(a.state_bytes, dtype=torch.uint8).pin_memory()
+    a.read_state(s18)
+    with pytest.raises(lb.LBError):
+        a.commit_state()                                   # nothing staged
+    runs = []
+    for mode in ("write", "stage"):
+        s = lb.Solver.from_workload(w)
+        s.step(13)
+        series = []
+        for k, st in enumerate((s13, s18, s13)):
+            if mode == "write":
+                s.write_state(st)
+            else:
+                if k == 1:
+                    s.stage_state(s13)                     # replaced by the next stage
+                s.stage_state(st)
+                s.commit_state()
+            s.step(6)
+            series.append(s.series_latest(1))
+        s.sync()
+        runs.append(({f: s.readout(f, device=False) for f in ("ux", "sxy", "Py", "pop7")}, s.nodes(), series))
+        s.close()
+    for f in runs[0][0]:
+        assert np.array_equal(runs[0][0][f], runs[1][0][f]), f
+    assert np.array_equal(runs[0][1], runs[1][1])
+    for x, y in zip(runs[0][2], runs[1][2]):
+        assert np.array_equal(x, y)
+    a.close()
