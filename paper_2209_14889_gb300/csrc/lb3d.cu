@@ -211,10 +211,12 @@ __device__ __forceinline__ void rhs9(const Args3& a, const Y9& y, const float (*
         }
     const float P[3] = {a.prx + y.c[6], a.pry + y.c[7], a.prz + y.c[8]};
     const Stiff S = stiffness(a, P[0], P[1], P[2]);
+    // C Psi - C sigma / eta_p = C (Psi - sigma / eta_p): one contraction (C is linear in X)
     const float psi6[6] = {Psi[0][0], Psi[1][1], Psi[2][2], Psi[1][2], Psi[0][2], Psi[0][1]};
-    float Cpsi[6], Csig[6];
-    apply_c(S, psi6, Cpsi);
-    apply_c(S, y.c, Csig);
+    float X6[6], CX6[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) X6[c] = psi6[c] - a.inv_eta * y.c[c];
+    apply_c(S, X6, CX6);
     const int I[6] = {0, 1, 2, 1, 0, 0}, J[6] = {0, 1, 2, 2, 2, 1};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -222,7 +224,7 @@ __device__ __forceinline__ void rhs9(const Args3& a, const Y9& y, const float (*
         float Jc = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) Jc += Om[i][k] * s[k][j] - s[i][k] * Om[k][j];
-        r[c] = -y.adv[c] - Jc + Cpsi[c] - a.inv_eta * Csig[c] + a.Dp * y.lap[c];
+        r[c] = -y.adv[c] - Jc + CX6[c] + a.Dp * y.lap[c];
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -376,21 +378,29 @@ __global__ void __launch_bounds__(NT, 4) k3_collide(const Args3 a, int mode)
         const float uF3 = 3.f * (ux * F[0] + uy * F[1] + uz * F[2]);
         const int ox[2] = {q.xp - q.c, q.xm - q.c}, oy[2] = {q.yp - q.c, q.ym - q.c}, oz[2] = {q.zp - q.c, q.zm - q.c};
         const float keep = 1.f - a.tau_inv;
-#pragma unroll
-        for (int n = 0; n < NQ; ++n) {
-            float cu = 0.f, cF = 0.f;
-            if (CX[n]) { cu += CX[n] > 0 ? ux : -ux; cF += CX[n] > 0 ? F[0] : -F[0]; }
-            if (CY[n]) { cu += CY[n] > 0 ? uy : -uy; cF += CY[n] > 0 ? F[1] : -F[1]; }
-            if (CZ[n]) { cu += CZ[n] > 0 ? uz : -uz; cF += CZ[n] > 0 ? F[2] : -F[2]; }
-            const float w = wq(n);
-            const float deq = w * (drho + rho * cu * (3.f + 4.5f * cu) - rq);
-            const float Sg = (a.guo * w) * (3.f * cF - uF3 + 9.f * cu * cF);
-            const float out = keep * d[n] + a.tau_inv * deq + Sg;
+        auto push = [&](int n, float out) {
             int dstc = q.c;
             if (CX[n]) dstc += ox[CX[n] > 0 ? 0 : 1];
             if (CY[n]) dstc += oy[CY[n] > 0 ? 0 : 1];
             if (CZ[n]) dstc += oz[CZ[n] > 0 ? 0 : 1];
             a.dst[(long long)n * a.NP + dstc] = out;
+        };
+        // rest population, then each direction n with its opposite n + 1 (the order of
+        // include/lb3d.h pairs them) from the even and odd parts in c of d_eq and of the source
+        const float base = drho - rq;
+        push(0, keep * d[0] + a.tau_inv * (wq(0) * base) + (a.guo * wq(0)) * (-uF3));
+#pragma unroll
+        for (int n = 1; n < NQ; n += 2) {
+            float cu = 0.f, cF = 0.f;
+            if (CX[n]) { cu += CX[n] > 0 ? ux : -ux; cF += CX[n] > 0 ? F[0] : -F[0]; }
+            if (CY[n]) { cu += CY[n] > 0 ? uy : -uy; cF += CY[n] > 0 ? F[1] : -F[1]; }
+            if (CZ[n]) { cu += CZ[n] > 0 ? uz : -uz; cF += CZ[n] > 0 ? F[2] : -F[2]; }
+            const float w = wq(n), gw = a.guo * w;
+            const float ev = a.tau_inv * (w * (base + 4.5f * rho * cu * cu));     // even part of d_eq / tau
+            const float od = a.tau_inv * (w * (3.f * rho * cu));                   // odd part
+            const float Sev = gw * (9.f * cu * cF - uF3), Sod = gw * (3.f * cF);
+            push(n, keep * d[n] + (ev + od) + (Sev + Sod));
+            push(n + 1, keep * d[n + 1] + (ev - od) + (Sev - Sod));
         }
         if (a.readout) {
             acc[0] = drho;
