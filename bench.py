@@ -16,9 +16,10 @@ roofline  fused lattice kernel (the node step runs in its tail; --separate-nodes
           the same steps), against the measured HBM copy bandwidth.
 e2e       the same metric through the C ABI with host buffers: per step the whole stored state is
           uploaded from pinned host memory in one copy, ten steps run, and the newest readout row
-          is copied back (lb_series_latest); the next step's upload runs on a copy stream while the
-          current step computes (lb_stage_state / lb_commit_state).  serial_value: the same with
-          the upload in line (lb_write_state).
+          is copied back; the next step's upload runs on a copy stream while the current step
+          computes (lb_stage_state / lb_commit_state) and the row comes back while the next step
+          runs (lb_series_latest_async / lb_series_wait).  serial_value: the same with the upload
+          in line (lb_write_state) and a synchronous row read (lb_series_latest).
 cpu_baseline         the FP64 oracle on one host core, one LB step of the 1024 x 1024 workload;
 cpu_baseline_openmp  the same oracle source with OpenMP on all host cores (bitwise the same).
 forms     the 4096^2 sixteen-ring workload in FP32, in the FP16/BF16 storage form and with the
@@ -1008,15 +1009,17 @@ def main():
 
     # end to end through the C ABI with host buffers: every bench step takes a whole stored state
     # uploaded from pinned host memory in one copy, runs the 10 LB steps on it and reads the
-    # newest readout row back (lb_series_latest).  The upload of step k + 1's state runs on the
-    # handle's copy stream while step k computes (lb_stage_state), and each step starts by making
-    # its uploaded state current (lb_commit_state); e2e_serial is the same loop with the upload
-    # in line (lb_write_state), the copy and the steps one after the other.
+    # newest readout row back.  The upload of step k + 1's state runs on the handle's copy stream
+    # while step k computes (lb_stage_state), each step starts by making its uploaded state
+    # current (lb_commit_state), and step k's row comes back while step k + 1 runs
+    # (lb_series_latest_async / lb_series_wait); e2e_serial is the same loop with the upload in
+    # line (lb_write_state) and a synchronous row read (lb_series_latest).
     nbytes = s.state_bytes
     pinned = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
     s.read_state(pinned)
     e2e_steps = max(3, min(args.steps, 10))
     d2h = 0
+    rows_pin = [torch.empty(lb.lib().lb_series_row_len(s.h), dtype=torch.float64).pin_memory() for _ in range(2)]
 
     def e2e_run(overlap):
         nonlocal d2h
@@ -1029,18 +1032,26 @@ def main():
                 s.commit_state()
                 if k + 1 < e2e_steps:
                     s.stage_state(pinned)
+                s.step(LB_STEPS_PER_STEP)
+                if k > 0:
+                    s.series_wait()          # step k - 1's row, while step k runs
+                s.series_latest_async(rows_pin[k % 2], 1)
+                d2h = rows_pin[k % 2].numel() * 8
             else:
                 s.write_state(pinned)
-            s.step(LB_STEPS_PER_STEP)
-            row = s.series_latest(1)
-            d2h = row.nbytes
+                s.step(LB_STEPS_PER_STEP)
+                row = s.series_latest(1)
+                d2h = row.nbytes
+        if overlap:
+            s.series_wait()
         barrier()
         return cells * LB_STEPS_PER_STEP * e2e_steps * world / (time.perf_counter() - t0) / 1e6
 
     e2e_serial = e2e_run(False)
     e2e = {"value": e2e_run(True), "unit": "MLUPS",
            "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(d2h),
-           "steps": e2e_steps, "upload": "overlapped with the previous step (lb_stage_state)",
+           "steps": e2e_steps,
+           "pipeline": "upload of the next state and read-back of the previous row overlap the steps",
            "serial_value": e2e_serial}
 
     rc = lb.lib().lb_sync(s.h)

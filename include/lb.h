@@ -204,6 +204,14 @@ int32_t lb_series_row_len(const lb_handle* h);
  * [n][row length]; *rows_written gets the number copied (fewer while fewer are recorded).
  * Synchronises the stream. */
 int lb_series_latest(lb_handle* h, double* dst, int32_t n, int32_t* rows_written);
+/* lb_series_latest without the synchronisation (the paper has no counterpart; this serves callers
+ * that keep the GPU busy with the next steps while the rows come back): the copies of the newest
+ * n rows, as of the steps enqueued so far, are enqueued on the handle's stream behind those steps,
+ * and the call returns.  dst must stay valid until lb_series_wait returns (pinned host memory for
+ * a copy that does not block the caller).  lb_series_wait blocks until the copies of the last
+ * lb_series_latest_async are done (at once if none is pending).  LB_EINVAL / LB_ECUDA. */
+int lb_series_latest_async(lb_handle* h, double* dst, int32_t n, int32_t* rows_written);
+int lb_series_wait(lb_handle* h);
 
 /*
  * Bulk transfer of the stored state (the paper has no counterpart; it exists so that a caller

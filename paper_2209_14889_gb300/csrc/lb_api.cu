@@ -749,6 +749,33 @@ int lb_series_latest(lb_handle* h, double* dst, int32_t n, int32_t* rows_written
     return LB_OK;
 }
 
+int lb_series_latest_async(lb_handle* h, double* dst, int32_t n, int32_t* rows_written)
+{
+    if (!h || !dst || n < 0) return fail(h, LB_EINVAL, "bad argument");
+    if (!h->ev_series) CK(h, cudaEventCreateWithFlags(&h->ev_series, cudaEventDisableTiming));
+    const long long every = h->p.readout_every;
+    const long long recorded = (h->t + every - 1) / every;
+    const int rows = std::min(series_rows(h), n);
+    for (int r = 0; r < rows; ++r) {
+        const long long k = recorded - rows + r;
+        CK(h, cudaMemcpyAsync(dst + (size_t)r * h->row_len, h->series + (size_t)(k % h->series_cap) * h->row_len,
+                              sizeof(double) * h->row_len, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaEventRecord(h->ev_series, h->stream));
+    h->series_pending = true;
+    if (rows_written) *rows_written = rows;
+    return LB_OK;
+}
+
+int lb_series_wait(lb_handle* h)
+{
+    if (!h) return fail(nullptr, LB_EINVAL, "null handle");
+    if (!h->series_pending) return LB_OK;
+    CK(h, cudaEventSynchronize(h->ev_series));
+    h->series_pending = false;
+    return LB_OK;
+}
+
 int64_t lb_state_bytes(const lb_handle* h) { return h ? (int64_t)N_PLANES * h->plane * h->esz : 0; }
 
 int lb_read_state(lb_handle* h, void* dst, size_t bytes, int32_t dst_is_device)
@@ -1003,6 +1030,7 @@ void lb_destroy(lb_handle* h)
         cudaStreamDestroy(h->copy_stream);
     }
     if (h->ev_staged) cudaEventDestroy(h->ev_staged);
+    if (h->ev_series) cudaEventDestroy(h->ev_series);
     if (h->ev_release) cudaEventDestroy(h->ev_release);
     dfree(h->stage_buf);
     for (auto e : h->ev_fused) cudaEventDestroy(e);

@@ -67,6 +67,8 @@ struct lb_handle {
     cudaEvent_t ev_staged = nullptr;        // the upload into stage_buf is complete
     cudaEvent_t ev_release = nullptr;       // the handle's stream has read stage_buf
     bool staged = false, release_pending = false;
+    cudaEvent_t ev_series = nullptr;        // lb_series_latest_async: its copies are done
+    bool series_pending = false;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_fused, ev_nodes;

@@ -90,6 +90,8 @@ def lib():
             "lb_series": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
             "lb_series_row_len": (i32, [_H]),
             "lb_series_latest": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
+            "lb_series_latest_async": (ctypes.c_int, [_H, vp, i32, ctypes.POINTER(i32)]),
+            "lb_series_wait": (ctypes.c_int, [_H]),
             "lb_state_bytes": (i64, [_H]),
             "lb_read_state": (ctypes.c_int, [_H, vp, sz, i32]),
             "lb_write_state": (ctypes.c_int, [_H, vp, sz, i32]),
@@ -314,6 +316,19 @@ class Solver:
         k = ctypes.c_int32(0)
         _check(self.h, L.lb_series_latest(self.h, buf.ctypes.data, int(n), ctypes.byref(k)))
         return buf[:k.value].copy()
+
+    def series_latest_async(self, out, n: int = 1) -> int:
+        """Enqueue the copy of the most recent n readout rows into `out` (a pinned host torch
+        tensor or a numpy array of FP64 [n][row length]) behind the steps enqueued so far and
+        return the number of rows it will hold (lb_series_latest_async); series_wait() blocks
+        until they are there."""
+        k = ctypes.c_int32(0)
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else ctypes.c_void_p(out.data_ptr())
+        _check(self.h, lib().lb_series_latest_async(self.h, ptr, int(n), ctypes.byref(k)))
+        return k.value
+
+    def series_wait(self):
+        _check(self.h, lib().lb_series_wait(self.h))
 
     @property
     def state_bytes(self) -> int:

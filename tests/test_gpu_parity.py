@@ -793,3 +793,29 @@ def test_staged_state_upload_overlaps_and_matches_write_state():
     for x, y in zip(runs[0][2], runs[1][2]):
         assert np.array_equal(x, y)
     a.close()
+
+
+def test_async_readout_rows_match_synchronous_rows():
+    # lb_series_latest_async copies the same rows as lb_series_latest, in stream order behind the
+    # steps enqueued before it, while later steps are already queued; lb_series_wait with nothing
+    # pending returns at once
+    lb = _gpu()
+    import torch
+    w = W.small(96, 64, steps=0)
+    s = lb.Solver.from_workload(w)
+    s.series_wait()
+    L = lb.lib().lb_series_row_len(s.h)
+    bufs = [torch.zeros((2, L), dtype=torch.float64).pin_memory() for _ in range(3)]
+    got = []
+    for k in range(3):
+        s.step(10)
+        n = s.series_latest_async(bufs[k], 2)
+        s.step(7)                                   # queued before the rows are waited for
+        s.series_wait()
+        got.append(bufs[k][:n].numpy().copy())
+    rows = s.series()
+    s.close()
+    # after 10, 27, 44 steps: readouts at t = 0, 10, 20, 30, 40, ...
+    assert np.array_equal(got[0], rows[0:1])
+    assert np.array_equal(got[1], rows[1:3])
+    assert np.array_equal(got[2], rows[3:5])
