@@ -51,12 +51,9 @@ struct TileGeo {
     static constexpr int OFF_M = OFF_H + 2 * R3;                  // drho, ux, uy [3][R2]
     static constexpr int OFF_R = OFF_M + 3 * R2;                  // RHS(y)   [5][R0] | f_IB [2][R2]
     static constexpr int SZ_R = cmax(5 * R0, 2 * R2);
-    // the gather's node staging (nodes [NT] float4 (cell, frac), forces [NT] float2) lives in the
-    // moments region, which is dead until phase C writes it, where that region is large enough
-    static constexpr bool NODES_IN_M = 3 * R2 >= 6 * NT && OFF_M % 4 == 0;
-    static constexpr int OFF_N = NODES_IN_M ? OFF_M : al4(OFF_R + SZ_R);
+    static constexpr int OFF_N = al4(OFF_R + SZ_R);               // nodes    [NT] float4 (cell, frac)
     static constexpr int OFF_NF = OFF_N + 4 * NT;                 // node forces [NT] float2
-    static constexpr int OFF_XI = NODES_IN_M ? OFF_R + SZ_R : OFF_NF + 2 * NT;   // wrapped x index [R4W] (int)
+    static constexpr int OFF_XI = OFF_NF + 2 * NT;                // wrapped x index [R4W] (int)
     static constexpr int OFF_YI = OFF_XI + R4W;                   // wrapped y index [R4H] (int)
     static constexpr int OFF_SC = OFF_YI + R4H;                   // scan scratch [NT/32 + 1] (int),
                                                                   // then the tile's ring masks [2]
