@@ -59,6 +59,20 @@ def test_create_without_gpu_fails_cleanly():
     assert not h.value
 
 
+def test_transfer_entry_points_reject_null_arguments_without_gpu():
+    # The staged upload and the asynchronous readout rows check their arguments before touching
+    # the device: a null handle or a null buffer is LB_EINVAL, with no CUDA call made.
+    from paper_2209_14889_gb300 import lb
+    L = lb.lib()
+    buf = (ctypes.c_double * 64)()
+    k = ctypes.c_int32(-1)
+    assert L.lb_stage_state(None, buf, 8, 0) == lb.LB_EINVAL
+    assert L.lb_commit_state(None) == lb.LB_EINVAL
+    assert L.lb_series_latest_async(None, buf, 1, ctypes.byref(k)) == lb.LB_EINVAL
+    assert L.lb_series_wait(None) == lb.LB_EINVAL
+    assert k.value == -1
+
+
 def test_parameter_validation_without_gpu():
     from paper_2209_14889_gb300 import lb
     L = lb.lib()
