@@ -760,7 +760,7 @@ def measure_learned_curve(args, lb, torch, budgets=(45.0, 180.0, 540.0)):
 
 
 PROFILE_CASES = ("tile_fp32", "tile_lp", "tile_scalar", "strip_fp32", "strip_lp", "strip_scalar", "sweep_fp32",
-                 "diffuse_fp32", "batch", "cube3d_128", "cube3d_192", "cube3d_256")
+                 "diffuse_fp32", "batch", "batch_cfg4", "cube3d_128", "cube3d_192", "cube3d_256")
 
 
 def run_case(args):
@@ -768,7 +768,9 @@ def run_case(args):
     profiles/ capture these): tile_* and sweep_fp32 on cfg3 at 2048^2 with 4 rings, strip_* on
     cfg3 at 4096^2 with 16 rings (FP32, FP16/BF16 storage, scalar model), diffuse_fp32 on the
     2048^2 lattice with D_p = 0.6 in 3 sub-steps, batch: 64 lattices of 256^2 (cfg4 recipe,
-    D_p = 0.05, no sub-steps) in one batch with the 32 x 16 tile shape, cube3d_N: the
+    D_p = 0.05, no sub-steps) in one batch with the 32 x 16 tile shape, batch_cfg4: the batched
+    workload of the bench (256 lattices, sides 128-512, stress diffusion with sub-steps) with the
+    warp-strip shape for every instance (the autotuner's choice), cube3d_N: the
     three-dimensional step on an N^3 periodic box of the default three-dimensional physics."""
     import torch
     from paper_2209_14889_gb300 import lb, workloads as W
@@ -783,6 +785,18 @@ def run_case(args):
         s3.sync()
         print(json.dumps({"case": case, "cells": n ** 3, "steps": args.steps}))
         s3.close()
+        return
+    if case == "batch_cfg4":
+        ws = W.cfg4()
+        ss = [lb.Solver.from_workload(w) for w in ws]
+        b = lb.Batch(ss)
+        b.set_shape(4)
+        b.step(args.steps)
+        b.sync()
+        print(json.dumps({"case": case, "cells": sum(w["nx"] * w["ny"] for w in ws), "steps": args.steps}))
+        b.close()
+        for s_ in ss:
+            s_.close()
         return
     if case == "batch":
         ws = W.cfg4(n_instances=64, sides=(256,))
