@@ -235,9 +235,11 @@ int lb_write_state(lb_handle* h, const void* src, size_t bytes, int32_t src_is_d
  * on the current one (the paper has no counterpart; this serves callers that feed a new state
  * every few steps).  lb_stage_state enqueues the copy of a whole stored state (layout and size as
  * for lb_write_state) into a staging buffer of the handle on a copy stream of its own and returns;
- * lb_commit_state makes the handle's stream wait for that upload and copy the staged state over
- * the current one (a device-to-device copy on the handle's stream), in stream order with the steps
- * before and after it.  The staging buffer (one state) and the copy stream are created on the
+ * lb_commit_state makes the handle's stream wait for that upload and makes the staged state
+ * current, in stream order with the steps before and after it: the handle takes the staging
+ * buffer as its current state buffer and keeps its former current buffer for the next stage (no
+ * copy), or, while the handle belongs to a batch (whose captured launches hold its buffers),
+ * copies the staged state device to device into its current buffer.  The staging buffer (one state) and the copy stream are created on the
  * first lb_stage_state.  A second lb_stage_state before a commit replaces the staged state; a
  * stage after a commit waits on the GPU until that commit's copy has read the buffer.  src must
  * stay unchanged until the upload is done (pinned host memory overlaps; host memory that is not

@@ -583,7 +583,10 @@ int lb_step(lb_handle* h, int64_t n)
         const bool strip = uses_strip(h);
         // consecutive kernels overlap by programmatic dependent launch, except when per-kernel
         // timing brackets each launch with events
-        const bool pdl = !h->timing;
+        // no programmatic early start for the first launch after lb_commit_state (it must not
+        // begin before the upload it waits for on the copy stream)
+        const bool pdl = !h->timing && !h->no_pdl_once;
+        h->no_pdl_once = false;
         // the tile kernels run the node step in their tail: one launch per step
         const bool tail = h->node_tail && !sweep && !strip;
         if (sweep) {
@@ -824,9 +827,17 @@ int lb_commit_state(lb_handle* h)
     if (!h) return fail(nullptr, LB_EINVAL, "null handle");
     if (!h->staged) return fail(h, LB_ESTATE, "lb_commit_state: no state staged (lb_stage_state)");
     CK(h, cudaStreamWaitEvent(h->stream, h->ev_staged, 0));
-    CK(h, cudaMemcpyAsync(h->state[h->cur], h->stage_buf, (size_t)lb_state_bytes(h), cudaMemcpyDeviceToDevice,
-                          h->stream));
+    if (h->batch_refs == 0) {
+        // the staging buffer becomes the current state and the former current buffer the
+        // staging buffer (the next stage waits until the work queued so far has read it)
+        std::swap(h->state[h->cur], h->stage_buf);
+    } else {
+        // a batch's graphs hold the handle's buffers: copy into them instead
+        CK(h, cudaMemcpyAsync(h->state[h->cur], h->stage_buf, (size_t)lb_state_bytes(h), cudaMemcpyDeviceToDevice,
+                              h->stream));
+    }
     CK(h, cudaEventRecord(h->ev_release, h->stream));
+    h->no_pdl_once = true;
     h->staged = false;
     h->release_pending = true;
     return LB_OK;

@@ -591,6 +591,7 @@ int lb_batch_create(lb_handle* const* handles, int32_t n, lb_batch** out)
     }
     lb_batch* b = new lb_batch();
     b->h.assign(handles, handles + n);
+    for (lb_handle* h : b->h) ++h->batch_refs;   // its graphs hold the handles' state buffers
     b->user = handles[0]->stream;
     b->chunk = std::max(1, handles[0]->p.readout_every);
     b->shape.assign(n, 0);
@@ -900,6 +901,7 @@ const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err.c_str() :
 void lb_batch_destroy(lb_batch* b)
 {
     if (!b) return;
+    for (lb_handle* h : b->h) --h->batch_refs;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->ev_in) cudaEventDestroy(b->ev_in);

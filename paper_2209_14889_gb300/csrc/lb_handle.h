@@ -67,6 +67,8 @@ struct lb_handle {
     cudaEvent_t ev_staged = nullptr;        // the upload into stage_buf is complete
     cudaEvent_t ev_release = nullptr;       // the handle's stream has read stage_buf
     bool staged = false, release_pending = false;
+    int batch_refs = 0;                     // live batches holding this handle's buffers
+    bool no_pdl_once = false;               // the next lattice launch starts without PDL
     cudaEvent_t ev_series = nullptr;        // lb_series_latest_async: its copies are done
     bool series_pending = false;
     // timing

@@ -819,3 +819,44 @@ def test_async_readout_rows_match_synchronous_rows():
     assert np.array_equal(got[0], rows[0:1])
     assert np.array_equal(got[1], rows[1:3])
     assert np.array_equal(got[2], rows[3:5])
+
+
+def test_staged_state_commit_into_a_batch_member():
+    # while a handle belongs to a batch (whose graphs hold its buffers) lb_commit_state copies the
+    # staged state into the handle's current buffer: the batch then steps from it exactly as after
+    # lb_write_state; after the batch is gone the commit takes over the staging buffer again
+    lb = _gpu()
+    import torch
+    w = W.small(96, 64, steps=0)
+    a = lb.Solver.from_workload(w)
+    a.step(12)
+    a.sync()
+    st = torch.empty(a.state_bytes, dtype=torch.uint8).pin_memory()
+    a.read_state(st)
+    a.close()
+    out = []
+    for mode in ("write", "stage"):
+        x = lb.Solver.from_workload(w)
+        y = lb.Solver.from_workload(W.small(64, 64, steps=0, seed=3))
+        b = lb.Batch([x, y])
+        if mode == "write":
+            x.write_state(st)
+        else:
+            x.stage_state(st)
+            x.commit_state()
+        b.step(10)
+        b.sync()
+        b.close()
+        if mode == "stage":                 # no batch now: the commit swaps buffers
+            x.stage_state(st)
+            x.commit_state()
+        else:
+            x.write_state(st)
+        x.step(5)
+        x.sync()
+        out.append(({f: x.readout(f, device=False) for f in ("ux", "sxx", "Py", "pop3")}, x.nodes()))
+        x.close()
+        y.close()
+    for f in out[0][0]:
+        assert np.array_equal(out[0][0][f], out[1][0][f]), f
+    assert np.array_equal(out[0][1], out[1][1])
