@@ -18,7 +18,9 @@
  *   orc_phi / spread / interp  pinned (partition of unity, adjointness, force equality)
  *   orc_node_forces       pinned (finite differences of Eq. Const)
  *   orc_step              pinned piecewise (Taylor-Green, Kolmogorov, Poiseuille, stress decay,
- *                         stress diffusion, P relaxation, objectivity, conservation, mirror symmetry);
+ *                         stress diffusion, P relaxation, objectivity, conservation, mirror symmetry,
+ *                         the restoring-force readout of a uniform and of a linear polymer force,
+ *                         the Heun node advance in a rigid rotation);
  *                         the whole coupled run has no closed form: parity unpinned beyond
  *                         those invariants.
  */
